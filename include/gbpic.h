@@ -1,0 +1,214 @@
+/*
+ * gbpic -- electrostatic PIC-MCC particle cycle on a cell-based adaptive quadtree, for
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The method is that of Kolobov & Arslanbekov, "Electrostatic PIC with adaptive Cartesian
+ * mesh" (arXiv:1604.07713):
+ *   - §3   : ES-PIC with Monte Carlo collisions of electrons and ions with neutrals, a
+ *            multigrid Poisson solver with the potential at cell centres, NGP charge
+ *            assignment at cell centres, bilinear interpolation of E from cell corners;
+ *            explicit scheme (dx < ~3 Debye lengths, dt < 1/omega_pe).
+ *   - §3.1 : one quad-tree grid for motion and collisions; cell-based particle lists (a
+ *            particle crossing a face leaves its cell's list and joins the neighbour's);
+ *            refinement hands particles to children by position, coarsening to the parent;
+ *            statistics reset when the grid changes.
+ *   - §2.1 : Morton-ordered cells of a forest of root boxes.
+ *   - §4.3 : particle splitting (one particle -> four in 2D) and merging for exponential
+ *            growth of electrons and ions in ionization events; the AMR grid as particle
+ *            management.
+ *
+ * Conventions for every call:
+ *   - The library owns all device memory.  Host pointers passed in are read during the call
+ *     and not kept; host pointers passed out are written during the call.
+ *   - No C++ exception crosses this ABI.  Every call returns a pic_status; on failure
+ *     pic_last_error() returns a thread-local message.
+ *   - A CUDA failure returns PIC_ECUDA and poisons the context: every later call on it
+ *     returns PIC_ESTATE (except pic_destroy).
+ *   - Read-out calls take a capacity `cap` (elements) and report the required size in
+ *     *n_out; when cap is too small they return PIC_EINVAL and write nothing.
+ *   - Work is issued on the context's stream (pic_set_stream; default: the legacy default
+ *     stream).  Calls that return host data synchronise that stream.
+ *   - Units are SI (or any consistent normalised set: eps0, q, m, qe are parameters).
+ */
+#ifndef GBPIC_H
+#define GBPIC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBPIC_API __attribute__((visibility("default")))
+#else
+#define GBPIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx; /* opaque, library-owned */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,         /* bad argument, size or state for this call */
+    PIC_ENOMEM = 2,         /* device or host allocation failed */
+    PIC_ECUDA = 3,          /* CUDA runtime error; context poisoned */
+    PIC_ESTATE = 4,         /* context poisoned by an earlier error, or call out of order */
+    PIC_ECAPACITY = 5,      /* particle population exceeds the configured hard capacity */
+    PIC_ETIMEOUT = 6,       /* a bounded device-side wait gave up */
+    PIC_ENOTCONV = 7,       /* Poisson solve did not reach mg_rel_tol in mg_max_cycles */
+    PIC_WARN_STABILITY = 8  /* explicit-PIC limits of §3 exceeded (dx > 3 lambda_D or
+                               omega_pe dt > 1); the call still did its work */
+} pic_status;
+
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };
+enum { PIC_BC_PERIODIC = 0, PIC_BC_DIRICHLET = 1, PIC_BC_NEUMANN = 2 };
+enum { PIC_ADAPT_MESH = 1, PIC_ADAPT_PARTICLES = 2 };
+
+/* Fields per leaf, in leaf (Morton key) order, for pic_read_fields. */
+enum {
+    PIC_FIELD_PHI = 0,     /* potential at the leaf centre [V] (1 per leaf)                   */
+    PIC_FIELD_RHO = 1,     /* charge density, NGP deposit + background [C/m^3] (1 per leaf)   */
+    PIC_FIELD_COUNT_E = 2, /* particles of species 0 in the leaf (1 per leaf)                 */
+    PIC_FIELD_COUNT_I = 3, /* particles of species 1 in the leaf (1 per leaf)                 */
+    PIC_FIELD_NODE_E = 4,  /* E at the leaf's 4 corners (x0,y0),(x1,y0),(x0,y1),(x1,y1),
+                              (Ex,Ey) each: 8 per leaf [V/m]                                */
+    PIC_FIELD_EMAG = 5     /* |E| at the leaf centre from the face gradients (1 per leaf)     */
+};
+
+/* Phases timed by pic_get_timing (CUDA events on the context's stream). */
+enum {
+    PIC_PHASE_DEPOSIT = 0, PIC_PHASE_POISSON = 1, PIC_PHASE_NODE_E = 2, PIC_PHASE_COUNT = 3,
+    PIC_PHASE_SCAN = 4, PIC_PHASE_MOVE = 5, PIC_PHASE_SORT = 6, PIC_PHASE_ADAPT = 7,
+    PIC_PHASE_SPLIT_MERGE = 8, PIC_N_PHASES = 9
+};
+
+/* Plain old data, copied at pic_create.  Species 0 is electrons (elastic + ionization
+ * collisions), species 1 ions (elastic collisions with a Maxwellian neutral partner). */
+typedef struct pic_config {
+    int32_t precision;          /* PIC_FP32 | PIC_FP64: particle state and push arithmetic */
+    int32_t n_species;          /* 1 (electrons on a fixed background) or 2               */
+    uint64_t seed;              /* Philox key                                              */
+    double dt;                  /* time step [s]                                           */
+    double eps0;                /* permittivity                                            */
+    double q[2], m[2];          /* charge and mass per species                             */
+    double qe;                  /* elementary charge: converts J <-> eV in the MCC         */
+    int32_t mcc;                /* 0: no collisions                                        */
+    int32_t bc_x, bc_y;         /* PIC_BC_*: walls absorb particles unless periodic        */
+    int32_t max_level;          /* deepest refinement level below the root boxes (<= 8)    */
+    double gas_density;         /* neutral density [m^-3]                                  */
+    double gas_temperature_ev;  /* neutral temperature [eV]                                */
+    double neutral_mass;        /* neutral mass [kg]                                       */
+    double sigma_el;            /* elastic cross section [m^2] (electrons and ions)        */
+    double sigma_iz0;           /* ionization: sigma = sigma_iz0 (1 - eps_th/eps), eps>th  */
+    double eps_th_ev;           /* ionization threshold [eV]                               */
+    double phi_left_dc, phi_left_amp, phi_left_freq; /* x = 0 wall: dc + amp sin(2 pi f t) */
+    double phi_right;           /* x = Lx wall potential                                   */
+    double rho_background;      /* uniform background charge density                       */
+    int32_t ppc_target, ppc_min, ppc_max; /* split/merge band (§4.3): e.g. 32, 8, 128        */
+    int32_t adapt_every;        /* informational: steps between pic_adapt calls            */
+    double e_ref;               /* reference field for the refinement criterion [V/m]     */
+    double refine_field;        /* refine where |E| > refine_field * e_ref                 */
+    double coarsen_field;       /* coarsen only where |E| < coarsen_field * e_ref          */
+    int32_t refine_count;       /* refine where the electron count exceeds this           */
+    int32_t coarsen_count;      /* coarsen 4 siblings whose electron count is <= this      */
+    double mg_rel_tol;          /* Poisson: stop at ||b - A phi|| <= tol ||b||              */
+    int32_t mg_max_cycles;      /* Poisson: V-cycle limit per solve                        */
+    int32_t instance;           /* instance id mixed into the Philox counter               */
+    int64_t particle_capacity;  /* per species; 0 = automatic (grows as needed)            */
+} pic_config;
+
+/* Create a context of n_instances independent PIC instances, one config each (cfg points
+ * to n_instances structs).  The device is the current CUDA device.  *out receives the
+ * context.  Errors: PIC_EINVAL (bad config), PIC_ENOMEM, PIC_ECUDA. */
+GBPIC_API pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out);
+
+/* Release every resource of the context.  NULL is accepted. */
+GBPIC_API pic_status pic_destroy(pic_ctx *ctx);
+
+/* Issue all later work on `stream` (a cudaStream_t; NULL = legacy default stream). */
+GBPIC_API pic_status pic_set_stream(pic_ctx *ctx, void *stream);
+
+/* Set the leaf mesh of instance `inst` (§2.1 forest of nx0 x ny0 root boxes of side h0
+ * with Morton-ordered quadtrees, §3.1).  Leaf i is the cell at refinement level level[i]
+ * (0 = root) of root box root[i] (row-major: root = rx + ry * nx0) with Morton code
+ * morton[i] inside that root at that level (x in the even bits).  Leaves may come in any
+ * order; they must tile the domain and be 2:1 balanced across faces.  root == NULL
+ * means the uniform level-0 mesh (n_leaves must equal nx0 * ny0; morton, level ignored).
+ * Discards any particles of the instance.  Errors: PIC_EINVAL (not a balanced tiling,
+ * level > max_level, sizes), PIC_ENOMEM, PIC_ECUDA. */
+GBPIC_API pic_status pic_set_mesh(pic_ctx *ctx, int32_t inst, int32_t nx0, int32_t ny0, double h0,
+                        int64_t n_leaves, const uint32_t *root, const uint32_t *morton,
+                        const uint8_t *level);
+
+/* Replace the population of species `species` in instance `inst` by n particles given as
+ * host arrays of absolute positions x, y, velocities vx, vy, vz and weights w (real
+ * particles per macro-particle per unit depth).  id == NULL assigns ids next_id ..
+ * next_id + n - 1.  Particles are located in their leaf (half-open cells, floor rule) and
+ * put into cell-list order: by leaf, load order inside a leaf.  Errors: PIC_EINVAL
+ * (position outside the domain, id >= 2^32, mesh not set), PIC_ENOMEM, PIC_ECUDA. */
+GBPIC_API pic_status pic_load_particles(pic_ctx *ctx, int32_t inst, int32_t species, int64_t n,
+                              const double *x, const double *y, const double *vx,
+                              const double *vy, const double *vz, const double *w,
+                              const uint64_t *id);
+
+/* Advance every instance by n_steps steps of the particle cycle (§3): NGP deposit ->
+ * multigrid Poisson -> corner E -> fused gather, leapfrog push, wall handling, leaf
+ * location and MCC with electron-ion pair spawning -> cell-list update.  Asynchronous
+ * except for capacity checks.  Errors: PIC_ECAPACITY, PIC_ENOTCONV (the step still
+ * completed with the last iterate), PIC_ECUDA. */
+GBPIC_API pic_status pic_step(pic_ctx *ctx, int32_t n_steps);
+
+/* Compute deposit -> Poisson -> corner E for the current state without moving particles
+ * (the field half of a step; pic_step does this itself). */
+GBPIC_API pic_status pic_compute_fields(pic_ctx *ctx);
+
+/* Mesh adaptation and particle management (§3.1, §4.3) on every instance.
+ * PIC_ADAPT_MESH: refine leaves with more than refine_count electrons or
+ * |E| > refine_field e_ref (level < max_level); coarsen sibling quartets with <=
+ * coarsen_count electrons and |E| < coarsen_field e_ref; restore 2:1 balance (refinement
+ * wins); hand particles to children by position / to the parent; carry phi over.
+ * PIC_ADAPT_PARTICLES: per leaf and species, split particles 1 -> 4 while the count is
+ * below ppc_min; merge pairs down to ppc_target when it is above ppc_max. */
+GBPIC_API pic_status pic_adapt(pic_ctx *ctx, int32_t flags);
+
+/* Copy a per-leaf field (PIC_FIELD_*) of instance `inst` to host memory `out`. */
+GBPIC_API pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *out,
+                           int64_t cap, int64_t *n_out);
+
+/* Copy the leaf mesh of instance `inst` (Morton key order) to host arrays; any pointer may
+ * be NULL.  root/morton/level as in pic_set_mesh. */
+GBPIC_API pic_status pic_read_mesh(pic_ctx *ctx, int32_t inst, uint32_t *root, uint32_t *morton,
+                         uint8_t *level, int64_t cap, int64_t *n_out);
+
+/* Copy the population of one species in cell-list order to host arrays (absolute positions,
+ * FP64); leaf receives each particle's leaf index.  Any pointer may be NULL. */
+GBPIC_API pic_status pic_read_particles(pic_ctx *ctx, int32_t inst, int32_t species, double *x,
+                              double *y, double *vx, double *vy, double *vz, double *w,
+                              uint64_t *id, uint32_t *leaf, int64_t cap, int64_t *n_out);
+
+/* Population sizes and the last Poisson solve of instance `inst` (any pointer may be NULL):
+ * n_leaves, particles of species 0 and 1, V-cycles and final relative residual. */
+GBPIC_API pic_status pic_get_counts(pic_ctx *ctx, int32_t inst, int64_t *n_leaves, int64_t *n_e,
+                          int64_t *n_i, int32_t *mg_cycles, double *mg_rel_res);
+
+/* Step counter (Philox counter word and RF phase t = step * dt) and next particle id. */
+GBPIC_API pic_status pic_get_step(const pic_ctx *ctx, int64_t *step);
+GBPIC_API pic_status pic_set_step(pic_ctx *ctx, int64_t step);
+
+/* Per-phase device timing with CUDA events on the context's stream.  pic_set_timing(1)
+ * starts recording (clearing earlier records); pic_get_timing synchronises the stream and
+ * writes, per phase (PIC_PHASE_*), the summed milliseconds to ms[] and the number of
+ * kernel launches to launches[] (either may be NULL), for min(n, PIC_N_PHASES) phases. */
+GBPIC_API pic_status pic_set_timing(pic_ctx *ctx, int32_t on);
+GBPIC_API pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches, int32_t n);
+
+/* Total kernel launches issued by the context since creation. */
+GBPIC_API pic_status pic_get_launch_count(const pic_ctx *ctx, int64_t *launches);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+GBPIC_API const char *pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBPIC_H */

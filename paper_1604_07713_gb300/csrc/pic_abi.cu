@@ -1,0 +1,500 @@
+// C ABI of gbpic (include/gbpic.h): context lifetime, argument checks, error mapping, the
+// step sequence of §3 (deposit -> Poisson -> corner E -> particle cycle) and read-outs.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct Failure : std::exception {
+    pic_status code;
+    std::string msg;
+    Failure(pic_status c, std::string m) : code(c), msg(std::move(m)) {}
+};
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void fail(pic_status code, const std::string &msg) { throw Failure(code, msg); }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        if (e == cudaErrorMemoryAllocation) throw Failure(PIC_ENOMEM, m);
+        throw Failure(PIC_ECUDA, m);
+    }
+}
+
+void check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Failure(PIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *DeviceArena::alloc(size_t bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Failure(PIC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed");
+    }
+    blocks.push_back(p);
+    return p;
+}
+void DeviceArena::release(void *p) {
+    auto it = std::find(blocks.begin(), blocks.end(), p);
+    if (it != blocks.end()) {
+        cudaFree(p);
+        blocks.erase(it);
+    }
+}
+void DeviceArena::release_all() {
+    for (void *p : blocks) cudaFree(p);
+    blocks.clear();
+}
+
+Phase::Phase(pic_ctx *c, int p) : ctx(c), phase(p), launches0(c->launches) {
+    if (ctx->timing) {
+        cudaEventCreate(&a);
+        cudaEventRecord(a, ctx->stream);
+    }
+}
+Phase::~Phase() {
+    if (ctx->timing && a) {
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, ctx->stream);
+        ctx->trec.push_back(TimingRec{phase, a, b, ctx->launches - launches0});
+    }
+}
+
+}  // namespace gbpic
+
+using namespace gbpic;
+
+namespace {
+
+template <typename F> pic_status guarded(pic_ctx *ctx, F &&f) {
+    if (ctx && ctx->poisoned) {
+        set_error("context poisoned by an earlier CUDA error");
+        return PIC_ESTATE;
+    }
+    try {
+        pic_status s = f();
+        if (s == PIC_OK) set_error("");
+        return s;
+    } catch (const Failure &e) {
+        set_error(e.msg);
+        if (ctx && e.code == PIC_ECUDA) ctx->poisoned = true;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return PIC_ENOMEM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return PIC_EINVAL;
+    }
+}
+
+void validate(const pic_config &c) {
+    if (c.precision != PIC_FP32 && c.precision != PIC_FP64) fail(PIC_EINVAL, "precision must be PIC_FP32 or PIC_FP64");
+    if (c.n_species < 1 || c.n_species > 2) fail(PIC_EINVAL, "n_species must be 1 or 2");
+    if (!(c.dt > 0.0) || !(c.eps0 > 0.0)) fail(PIC_EINVAL, "dt and eps0 must be positive");
+    for (int s = 0; s < c.n_species; ++s)
+        if (!(c.m[s] > 0.0)) fail(PIC_EINVAL, "species mass must be positive");
+    for (int b : {c.bc_x, c.bc_y})
+        if (b < PIC_BC_PERIODIC || b > PIC_BC_NEUMANN) fail(PIC_EINVAL, "bad boundary condition");
+    if (c.max_level < 0 || c.max_level > kMaxLevel) fail(PIC_EINVAL, "max_level must be in [0, 8]");
+    if (c.mcc) {
+        if (!(c.qe > 0.0) || !(c.neutral_mass > 0.0) || c.gas_density < 0.0)
+            fail(PIC_EINVAL, "MCC needs qe > 0, neutral_mass > 0, gas_density >= 0");
+    }
+    if (c.instance < 0 || c.instance > 255) fail(PIC_EINVAL, "instance must be in [0, 255]");
+    if (!(c.mg_rel_tol > 0.0)) fail(PIC_EINVAL, "mg_rel_tol must be positive");
+}
+
+Instance &get_inst(pic_ctx *ctx, int32_t inst) {
+    if (!ctx) fail(PIC_EINVAL, "null context");
+    if (inst < 0 || inst >= (int32_t)ctx->inst.size()) fail(PIC_EINVAL, "instance index out of range");
+    return ctx->inst[inst];
+}
+
+void fields_of(pic_ctx *ctx, Instance &in, int64_t step) {
+    double walls[4];
+    walls_at(in, step, walls);
+    {
+        Phase ph(ctx, PIC_PHASE_DEPOSIT);
+        deposit(ctx, in, walls);
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_POISSON);
+        poisson_solve(ctx, in, walls);
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_NODE_E);
+        node_e(ctx, in, walls);
+    }
+}
+
+void ensure_species(pic_ctx *ctx, Instance &in) {
+    // a species never loaded is an empty population
+    for (int s = 0; s < in.cfg.n_species; ++s)
+        if (!in.sp[s].start) species_alloc(ctx, in, s, 1 << 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out) {
+    if (!out || !cfg || n_instances < 1) {
+        set_error("pic_create: null argument or n_instances < 1");
+        return PIC_EINVAL;
+    }
+    *out = nullptr;
+    pic_ctx *ctx = nullptr;
+    pic_status s = guarded(nullptr, [&]() -> pic_status {
+        for (int i = 0; i < n_instances; ++i) validate(cfg[i]);
+        ctx = new pic_ctx();
+        GB_CUDA(cudaGetDevice(&ctx->device));
+        ctx->inst.resize(n_instances);
+        for (int i = 0; i < n_instances; ++i) {
+            Instance &in = ctx->inst[i];
+            in.cfg = cfg[i];
+            GB_CUDA(cudaMallocHost(&in.red_host, 64));
+            GB_CUDA(cudaMallocHost(&in.cnt_host, 64));
+            GB_CUDA(cudaMalloc(&in.d_next_id, 8));
+            GB_CUDA(cudaMemset(in.d_next_id, 0, 8));
+        }
+        ctx->precision = cfg[0].precision;
+        return PIC_OK;
+    });
+    if (s != PIC_OK) {
+        if (ctx) pic_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return PIC_OK;
+}
+
+pic_status pic_destroy(pic_ctx *ctx) {
+    if (!ctx) return PIC_OK;
+    cudaStreamSynchronize(ctx->stream);
+    for (Instance &in : ctx->inst) {
+        in.mesh_mem.release_all();
+        in.part_mem[0].release_all();
+        in.part_mem[1].release_all();
+        if (in.red_host) cudaFreeHost(in.red_host);
+        if (in.cnt_host) cudaFreeHost(in.cnt_host);
+        if (in.d_next_id) cudaFree(in.d_next_id);
+    }
+    for (auto &r : ctx->trec) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete ctx;
+    return PIC_OK;
+}
+
+pic_status pic_set_stream(pic_ctx *ctx, void *stream) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        ctx->stream = (cudaStream_t)stream;
+        return PIC_OK;
+    });
+}
+
+pic_status pic_set_mesh(pic_ctx *ctx, int32_t inst, int32_t nx0, int32_t ny0, double h0, int64_t n_leaves,
+                        const uint32_t *root, const uint32_t *morton, const uint8_t *level) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (nx0 < 1 || ny0 < 1 || !(h0 > 0.0) || n_leaves < 1) fail(PIC_EINVAL, "bad mesh size");
+        if (!root && n_leaves != (int64_t)nx0 * ny0) fail(PIC_EINVAL, "uniform mesh needs n_leaves == nx0 * ny0");
+        if (root && (!morton || !level)) fail(PIC_EINVAL, "root, morton and level must all be given");
+        if (n_leaves >= (1ll << 30)) fail(PIC_EINVAL, "too many leaves");
+        if (level)
+            for (int64_t i = 0; i < n_leaves; ++i)
+                if (level[i] > in.cfg.max_level) fail(PIC_EINVAL, "leaf level above max_level");
+        in.part_mem[0].release_all();
+        in.part_mem[1].release_all();
+        for (auto &sp : in.sp) sp = Species();
+        mesh_build(ctx, in, nx0, ny0, h0, n_leaves, root, morton, level);
+        poisson_setup(ctx, in);
+        const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
+        in.stencil = in.mesh_mem.alloc(8 * rs * in.nleaf + 64);
+        GB_CUDA(cudaMemsetAsync(in.stencil, 0, 8 * rs * in.nleaf, ctx->stream));
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        return PIC_OK;
+    });
+}
+
+pic_status pic_load_particles(pic_ctx *ctx, int32_t inst, int32_t species, int64_t n, const double *x,
+                              const double *y, const double *vx, const double *vy, const double *vz,
+                              const double *w, const uint64_t *id) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "pic_set_mesh must come first");
+        if (species < 0 || species >= in.cfg.n_species) fail(PIC_EINVAL, "species out of range");
+        if (n < 0 || n >= (1ll << 31)) fail(PIC_EINVAL, "bad particle count");
+        if (n > 0 && (!x || !y || !vx || !vy || !vz || !w)) fail(PIC_EINVAL, "null particle array");
+        particles_load(ctx, in, species, n, x, y, vx, vy, vz, w, id);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_compute_fields(pic_ctx *ctx) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        pic_status st = PIC_OK;
+        for (Instance &in : ctx->inst) {
+            if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+            ensure_species(ctx, in);
+            fields_of(ctx, in, ctx->step);
+            if (in.mg_res > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+        }
+        if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
+        return st;
+    });
+}
+
+pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        if (n_steps < 0) fail(PIC_EINVAL, "n_steps < 0");
+        for (Instance &in : ctx->inst) {
+            if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+            ensure_species(ctx, in);
+        }
+        pic_status st = PIC_OK;
+        for (int32_t k = 0; k < n_steps; ++k) {
+            for (Instance &in : ctx->inst) {
+                ensure_capacity(ctx, in);
+                fields_of(ctx, in, ctx->step);
+                if (in.mg_res > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+                particle_step(ctx, in, ctx->step);
+            }
+            ++ctx->step;
+        }
+        if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
+        return st;
+    });
+}
+
+pic_status pic_adapt(pic_ctx *ctx, int32_t flags) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        for (Instance &in : ctx->inst) {
+            if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+            ensure_species(ctx, in);
+            if (flags & PIC_ADAPT_MESH) {
+                Phase ph(ctx, PIC_PHASE_ADAPT);
+                adapt_mesh(ctx, in);
+            }
+            if (flags & PIC_ADAPT_PARTICLES) {
+                Phase ph(ctx, PIC_PHASE_SPLIT_MERGE);
+                split_merge(ctx, in);
+            }
+        }
+        return PIC_OK;
+    });
+}
+
+pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *out, int64_t cap, int64_t *n_out) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        const int64_t nl = in.nleaf;
+        int64_t need = field == PIC_FIELD_NODE_E ? 8 * nl : nl;
+        if (field < PIC_FIELD_PHI || field > PIC_FIELD_EMAG) fail(PIC_EINVAL, "unknown field");
+        if (n_out) *n_out = need;
+        if (!out || cap < need) fail(PIC_EINVAL, "output capacity too small");
+        cudaStream_t st = ctx->stream;
+        std::vector<uint8_t> lev(nl);
+        switch (field) {
+        case PIC_FIELD_PHI:
+            GB_CUDA(cudaMemcpyAsync(out, in.phi, nl * 8, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            break;
+        case PIC_FIELD_RHO: {
+            GB_CUDA(cudaMemcpyAsync(out, in.charge, nl * 8, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaMemcpyAsync(lev.data(), in.lv[0].lev, nl, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            const double hf = in.h0 / (double)(1 << in.lmax);
+            for (int64_t l = 0; l < nl; ++l) {
+                const double h = (double)(1 << (in.lmax - lev[l])) * hf;
+                out[l] = out[l] / (h * h) + in.cfg.rho_background;
+            }
+            break;
+        }
+        case PIC_FIELD_COUNT_E:
+        case PIC_FIELD_COUNT_I: {
+            const int s = field == PIC_FIELD_COUNT_E ? 0 : 1;
+            if (s >= in.cfg.n_species || !in.sp[s].start) {
+                std::fill(out, out + nl, 0.0);
+                break;
+            }
+            std::vector<int32_t> st0(nl + 1);
+            GB_CUDA(cudaMemcpyAsync(st0.data(), in.sp[s].start, (nl + 1) * 4, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            for (int64_t l = 0; l < nl; ++l) out[l] = (double)(st0[l + 1] - st0[l]);
+            break;
+        }
+        case PIC_FIELD_NODE_E:
+            if (in.cfg.precision == PIC_FP64) {
+                GB_CUDA(cudaMemcpyAsync(out, in.stencil, 8 * nl * 8, cudaMemcpyDeviceToHost, st));
+                GB_CUDA(cudaStreamSynchronize(st));
+            } else {
+                std::vector<float> tmp(8 * nl);
+                GB_CUDA(cudaMemcpyAsync(tmp.data(), in.stencil, 8 * nl * 4, cudaMemcpyDeviceToHost, st));
+                GB_CUDA(cudaStreamSynchronize(st));
+                for (int64_t i = 0; i < 8 * nl; ++i) out[i] = tmp[i];
+            }
+            break;
+        case PIC_FIELD_EMAG: {
+            DeviceArena tmp;
+            double *d = dalloc<double>(tmp, nl);
+            double walls[4];
+            walls_at(in, ctx->step, walls);
+            cell_emag(ctx, in, walls, d);
+            GB_CUDA(cudaMemcpyAsync(out, d, nl * 8, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            tmp.release_all();
+            break;
+        }
+        }
+        return PIC_OK;
+    });
+}
+
+pic_status pic_read_mesh(pic_ctx *ctx, int32_t inst, uint32_t *root, uint32_t *morton, uint8_t *level, int64_t cap,
+                         int64_t *n_out) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        const int64_t nl = in.nleaf;
+        if (n_out) *n_out = nl;
+        if (cap < nl) fail(PIC_EINVAL, "output capacity too small");
+        cudaStream_t st = ctx->stream;
+        if (root) GB_CUDA(cudaMemcpyAsync(root, in.root, nl * 4, cudaMemcpyDeviceToHost, st));
+        if (morton) GB_CUDA(cudaMemcpyAsync(morton, in.morton, nl * 4, cudaMemcpyDeviceToHost, st));
+        if (level) GB_CUDA(cudaMemcpyAsync(level, in.lv[0].lev, nl, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        return PIC_OK;
+    });
+}
+
+pic_status pic_read_particles(pic_ctx *ctx, int32_t inst, int32_t species, double *x, double *y, double *vx,
+                              double *vy, double *vz, double *w, uint64_t *id, uint32_t *leaf, int64_t cap,
+                              int64_t *n_out) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (species < 0 || species >= in.cfg.n_species) fail(PIC_EINVAL, "species out of range");
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        ensure_species(ctx, in);
+        Species &sp = in.sp[species];
+        GB_CUDA(cudaMemcpyAsync(in.cnt_host, sp.start + in.nleaf, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        sp.n = sp.n_upper = in.cnt_host[0];
+        if (n_out) *n_out = sp.n;
+        if (cap < sp.n) fail(PIC_EINVAL, "output capacity too small");
+        particles_read(ctx, in, species, x, y, vx, vy, vz, w, id, leaf);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_get_counts(pic_ctx *ctx, int32_t inst, int64_t *n_leaves, int64_t *n_e, int64_t *n_i,
+                          int32_t *mg_cycles, double *mg_rel_res) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        int64_t c[2] = {0, 0};
+        for (int s = 0; s < in.cfg.n_species; ++s) {
+            if (!in.sp[s].start) continue;
+            GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].start + in.nleaf, 4, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+        }
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int s = 0; s < in.cfg.n_species; ++s)
+            if (in.sp[s].start) {
+                c[s] = in.cnt_host[s];
+                in.sp[s].n = in.sp[s].n_upper = c[s];
+            }
+        if (n_leaves) *n_leaves = in.nleaf;
+        if (n_e) *n_e = c[0];
+        if (n_i) *n_i = c[1];
+        if (mg_cycles) *mg_cycles = in.mg_cycles;
+        if (mg_rel_res) *mg_rel_res = in.mg_res;
+        return PIC_OK;
+    });
+}
+
+pic_status pic_get_step(const pic_ctx *ctx, int64_t *step) {
+    if (!ctx || !step) {
+        set_error("null argument");
+        return PIC_EINVAL;
+    }
+    *step = ctx->step;
+    return PIC_OK;
+}
+
+pic_status pic_set_step(pic_ctx *ctx, int64_t step) {
+    if (!ctx || step < 0) {
+        set_error("bad argument");
+        return PIC_EINVAL;
+    }
+    ctx->step = step;
+    return PIC_OK;
+}
+
+pic_status pic_set_timing(pic_ctx *ctx, int32_t on) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (auto &r : ctx->trec) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        ctx->trec.clear();
+        ctx->timing = on != 0;
+        return PIC_OK;
+    });
+}
+
+pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches, int32_t n) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int m = std::min<int>(n, PIC_N_PHASES);
+        for (int k = 0; k < m; ++k) {
+            if (ms) ms[k] = 0.0;
+            if (launches) launches[k] = 0;
+        }
+        for (auto &r : ctx->trec) {
+            if (r.phase >= m) continue;
+            float t = 0.f;
+            GB_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            if (ms) ms[r.phase] += t;
+            if (launches) launches[r.phase] += r.launches;
+        }
+        return PIC_OK;
+    });
+}
+
+pic_status pic_get_launch_count(const pic_ctx *ctx, int64_t *launches) {
+    if (!ctx || !launches) {
+        set_error("null argument");
+        return PIC_EINVAL;
+    }
+    *launches = ctx->launches;
+    return PIC_OK;
+}
+
+const char *pic_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Internal declarations shared by the gbpic translation units: context layout, device
+// helpers (Philox, warp scans, leaf geometry) and host entry points of each unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbpic.h"
+
+namespace gbpic {
+
+// ------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------
+struct Error {
+    pic_status code;
+    std::string msg;
+};
+void set_error(const std::string &msg);
+[[noreturn]] void fail(pic_status code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define GB_CUDA(call) ::gbpic::check_cuda((call), #call)
+
+constexpr int kEll = 8;           // off-diagonal slots per row of the Poisson operator
+constexpr int kMaxLevel = 8;      // deepest supported refinement level
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------------------------
+// Device memory helpers (plain cudaMalloc; the context frees everything it owns)
+// ------------------------------------------------------------------------------------
+struct DeviceArena {
+    std::vector<void *> blocks;
+    void *alloc(size_t bytes);
+    void release(void *p);
+    void release_all();
+};
+
+template <typename T>
+T *dalloc(DeviceArena &a, size_t n) { return static_cast<T *>(a.alloc(n * sizeof(T) + 16)); }
+
+// ------------------------------------------------------------------------------------
+// Multigrid level: a composite leaf mesh on its own lattice of (nx0 << lmax) x
+// (ny0 << lmax) cells of side h0 / 2^lmax.
+// ------------------------------------------------------------------------------------
+struct Level {
+    int nx0 = 0, ny0 = 0, lmax = 0;
+    double h0 = 0;
+    int64_t n = 0;
+    int32_t *ix = nullptr, *iy = nullptr;  // lattice corner
+    uint8_t *lev = nullptr;                // level (side = 1 << (lmax - lev) lattice cells)
+    int32_t *map = nullptr;                // lattice cell -> cell index
+    int32_t *parent = nullptr;             // cell -> cell of the next coarser level
+    int32_t *child4 = nullptr;             // cell -> up to 4 cells of the next finer level
+    int32_t *col = nullptr;                // ELL off-diagonal columns [kEll * n], -1 = empty
+    float *val = nullptr;                  // ELL off-diagonal values (FP32)
+    float *dinv = nullptr;                 // 1 / diagonal (FP32)
+    double *val64 = nullptr, *diag64 = nullptr;  // finest level only (FP64 residual)
+    double *bcw = nullptr;                 // finest level: Dirichlet coefficients [4 * n]
+    float *x = nullptr, *b = nullptr, *t = nullptr;  // FP32 work vectors
+    int64_t lat_n() const { return ((int64_t)nx0 << lmax) * ((int64_t)ny0 << lmax); }
+};
+
+// One species: double-buffered SoA record (offsets u, v in [0,1) of the leaf, velocity,
+// weight: precision R; id: u32) and the cell-list offsets.
+struct Species {
+    int64_t cap = 0;      // elements per array
+    int64_t n = 0;        // exact count known to the host
+    int64_t n_upper = 0;  // upper bound on the count while steps are in flight
+    int cur = 0;
+    void *arr[2][6] = {};      // u, v, vx, vy, vz, w
+    uint32_t *id[2] = {};
+    uint32_t *key = nullptr;   // sort keys of entering particles (cap)
+    int32_t *start = nullptr;  // [nleaf + 1] current list offsets
+    int32_t *start_new = nullptr;
+    int32_t *stay = nullptr, *inc = nullptr, *fill = nullptr;  // [nleaf]
+    int32_t *spawn = nullptr, *spawn_base = nullptr;           // [nleaf], [nleaf + 1]
+};
+
+struct Instance {
+    pic_config cfg{};
+    bool has_mesh = false;
+    int nx0 = 0, ny0 = 0, lmax = 0;
+    double h0 = 0;
+    int64_t nleaf = 0;
+    uint32_t *key = nullptr;     // leaf Morton keys
+    uint32_t *root = nullptr;    // per leaf
+    uint32_t *morton = nullptr;  // per leaf
+    std::vector<Level> lv;       // lv[0] = the leaves
+    double *phi = nullptr, *bvec = nullptr, *res = nullptr, *charge = nullptr;
+    double *red = nullptr;       // reduction scratch
+    double *red_host = nullptr;  // pinned
+    int32_t *cnt_host = nullptr; // pinned
+    void *stencil = nullptr;     // node E per leaf corner: 8 x R per leaf
+    Species sp[2];
+    int64_t next_id = 0;                     // host mirror (exact after a sync)
+    unsigned long long *d_next_id = nullptr; // device counter of the next particle id
+    int mg_cycles = 0;
+    double mg_res = 0;
+    DeviceArena mesh_mem;        // freed on pic_set_mesh
+    DeviceArena part_mem[2];     // freed on reload / regrow
+};
+
+struct TimingRec {
+    int phase;
+    cudaEvent_t a, b;
+    int64_t launches;
+};
+
+}  // namespace gbpic
+
+struct pic_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool poisoned = false;
+    int64_t step = 0;
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<gbpic::TimingRec> trec;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<gbpic::Instance> inst;
+    int precision = PIC_FP32;
+};
+
+namespace gbpic {
+
+// Launch accounting / phase timing around a group of launches.
+struct Phase {
+    pic_ctx *ctx;
+    int phase;
+    int64_t launches0;
+    cudaEvent_t a = nullptr;
+    Phase(pic_ctx *c, int p);
+    ~Phase();
+};
+inline void count_launch(pic_ctx *c, int64_t k = 1) { c->launches += k; }
+void check_launch(const char *what);
+
+// ------------------------------------------------------------------------------------
+// Device helpers
+// ------------------------------------------------------------------------------------
+__host__ __device__ inline uint32_t spread2(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ inline uint32_t compact2(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, Weyl key schedule.
+struct U4 { uint32_t x, y, z, w; };
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// Leaf geometry on its level's lattice.
+struct LeafGeom { int32_t ix, iy, s; };
+
+// Finest-lattice lookup with wrap (periodic) or -1 outside a wall.
+__device__ __forceinline__ int32_t lattice_leaf(const int32_t *__restrict__ map, int NX, int NY,
+                                                bool px, bool py, int32_t I, int32_t J) {
+    if (I < 0 || I >= NX) {
+        if (!px) return -1;
+        I = I < 0 ? I + NX : I - NX;
+    }
+    if (J < 0 || J >= NY) {
+        if (!py) return -1;
+        J = J < 0 ? J + NY : J - NY;
+    }
+    return __ldg(map + (int64_t)J * NX + I);
+}
+
+// ------------------------------------------------------------------------------------
+// Entry points of the translation units (host side)
+// ------------------------------------------------------------------------------------
+// pic_mesh.cu
+void mesh_build(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t n,
+                const uint32_t *root, const uint32_t *morton, const uint8_t *level);
+void mesh_build_device(pic_ctx *ctx, Instance &in, int64_t n);  // from in.root/morton/lev
+void node_e(pic_ctx *ctx, Instance &in, const double walls[4]);
+void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev);
+// pic_poisson.cu
+void poisson_setup(pic_ctx *ctx, Instance &in);
+void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]);
+// pic_particles.cu
+void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap);
+void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *x,
+                    const double *y, const double *vx, const double *vy, const double *vz,
+                    const double *w, const uint64_t *id);
+void deposit(pic_ctx *ctx, Instance &in, const double walls[4]);
+void particle_step(pic_ctx *ctx, Instance &in, int64_t step);
+void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, double *vx,
+                    double *vy, double *vz, double *w, uint64_t *id, uint32_t *leaf);
+void ensure_capacity(pic_ctx *ctx, Instance &in);
+void walls_at(const Instance &in, int64_t step, double walls[4]);
+// pic_adapt.cu
+void adapt_mesh(pic_ctx *ctx, Instance &in);
+void split_merge(pic_ctx *ctx, Instance &in);
+
+// scan helpers (pic_particles.cu): exclusive scan of n int32 into out[0..n] (out[n] = total)
+void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
+                        int32_t *scratch);
+int64_t scan_scratch_elems(int64_t n);
+
+}  // namespace gbpic

@@ -1,0 +1,319 @@
+// Poisson solve on the composite leaf mesh (§3: multigrid Poisson solver with the potential
+// at cell centres).  Mixed precision: the residual b - A phi, its norm and the correction
+// phi += e are FP64 (iterative refinement); each correction e comes from one FP32
+// geometric-multigrid V-cycle over the tree-clamped and root-coarsened levels, with damped
+// Jacobi smoothing, summed restriction and piecewise-constant prolongation; the coarsest
+// level is solved by a one-block conjugate-gradient iteration.
+#include <algorithm>
+#include <cmath>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+namespace {
+constexpr int kT = 256;
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs: fixed so that the FP64 sums are deterministic
+constexpr float kOmega = 0.8f;
+constexpr int kNu = 3;
+inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+// r = b - A phi (FP64), partial sums of r^2 and b^2 per block (fixed grid).
+__global__ void k_residual64(int64_t n, const int32_t *__restrict__ col, const double *__restrict__ val,
+                             const double *__restrict__ diag, const double *__restrict__ phi,
+                             const double *__restrict__ b, double *__restrict__ r, float *__restrict__ r32,
+                             double *__restrict__ part) {
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double ax = diag[i] * phi[i];
+#pragma unroll
+        for (int j = 0; j < kEll; ++j) {
+            const int32_t c = col[(int64_t)j * n + i];
+            if (c >= 0) ax += val[(int64_t)j * n + i] * phi[c];
+        }
+        const double ri = b[i] - ax;
+        r[i] = ri;
+        r32[i] = (float)ri;
+        rr += ri * ri;
+        bb += b[i] * b[i];
+    }
+    const double s1 = block_sum(rr);
+    const double s2 = block_sum(bb);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+}
+
+__global__ void k_finish_sums(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < nparts; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }
+        out[0] = a; out[1] = b;
+    }
+}
+
+// Zero-mean projections for a fully periodic (singular) problem: area weights a = s^2.
+__global__ void k_area_moments(int64_t n, const uint8_t *__restrict__ lev, int lmax, const double *__restrict__ v,
+                               double *__restrict__ part) {
+    double sv = 0.0, sa = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = (double)(1 << (lmax - lev[i]));
+        sv += v[i];
+        sa += s * s;
+    }
+    const double s1 = block_sum(sv), s2 = block_sum(sa);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+}
+__global__ void k_area_weighted(int64_t n, const uint8_t *__restrict__ lev, int lmax, const double *__restrict__ v,
+                                double *__restrict__ part) {
+    double sv = 0.0, sa = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = (double)(1 << (lmax - lev[i]));
+        sv += s * s * v[i];
+        sa += s * s;
+    }
+    const double s1 = block_sum(sv), s2 = block_sum(sa);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+}
+// v -= mode * (sum / area_total): mode 0 subtracts an area-proportional share (RHS
+// compatibility), mode 1 a constant (zero area-weighted mean of the potential).
+__global__ void k_project(int64_t n, const uint8_t *__restrict__ lev, int lmax, const double *__restrict__ sums,
+                          double *__restrict__ v, int mode) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double s = (double)(1 << (lmax - lev[i]));
+    const double k = sums[0] / sums[1];
+    v[i] -= mode == 0 ? k * s * s : k;
+}
+
+__global__ void k_add_correction(int64_t n, const float *__restrict__ e, double *__restrict__ phi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) phi[i] += (double)e[i];
+}
+
+// Damped Jacobi: t = (1 - w) x + w D^-1 (b - offdiag x).  first: x == 0.
+__global__ void k_jacobi(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
+                         const float *__restrict__ dinv, const float *__restrict__ b, const float *__restrict__ x,
+                         float *__restrict__ t, int first) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (first) { t[i] = kOmega * dinv[i] * b[i]; return; }
+    float off = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kEll; ++j) {
+        const int32_t c = col[(int64_t)j * n + i];
+        if (c >= 0) off = fmaf(val[(int64_t)j * n + i], x[c], off);
+    }
+    t[i] = (1.0f - kOmega) * x[i] + kOmega * dinv[i] * (b[i] - off);
+}
+
+// Coarse right-hand side: summed residuals of the children; zero coarse iterate.
+__global__ void k_restrict_residual(int64_t nc, const int32_t *__restrict__ child4, int64_t nf,
+                                    const int32_t *__restrict__ col, const float *__restrict__ val,
+                                    const float *__restrict__ dinv, const float *__restrict__ bf,
+                                    const float *__restrict__ xf, float *__restrict__ bc, float *__restrict__ xc) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nc) return;
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int32_t i = child4[4 * p + k];
+        if (i < 0) continue;
+        float ax = xf[i] / dinv[i];
+#pragma unroll
+        for (int j = 0; j < kEll; ++j) {
+            const int32_t c = col[(int64_t)j * nf + i];
+            if (c >= 0) ax = fmaf(val[(int64_t)j * nf + i], xf[c], ax);
+        }
+        s += bf[i] - ax;
+    }
+    bc[p] = s;
+    xc[p] = 0.0f;
+}
+
+__global__ void k_prolong(int64_t nf, const int32_t *__restrict__ parent, const float *__restrict__ xc,
+                          float *__restrict__ xf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) xf[i] += xc[parent[i]];
+}
+
+// One-block Jacobi-preconditioned CG on the coarsest level (symmetric: one uniform level).
+__global__ void __launch_bounds__(1024) k_coarse_cg(int64_t n, const int32_t *__restrict__ col,
+                                                    const float *__restrict__ val, const float *__restrict__ dinv,
+                                                    const float *__restrict__ b, float *__restrict__ x,
+                                                    float *__restrict__ r, float *__restrict__ p,
+                                                    float *__restrict__ q, int singular, int maxit) {
+    __shared__ double red[32];
+    __shared__ double bcast;
+    auto bsum = [&](double v) -> double {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            bcast = s;
+        }
+        __syncthreads();
+        const double out = bcast;
+        __syncthreads();
+        return out;
+    };
+    double mb = 0.0;
+    if (singular) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mb += b[i];
+        mb = bsum(mb) / (double)n;
+    }
+    double rz = 0.0, bb = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float ri = b[i] - (float)mb;
+        x[i] = 0.0f;
+        r[i] = ri;
+        const float zi = dinv[i] * ri;
+        p[i] = zi;
+        rz += (double)ri * zi;
+        bb += (double)ri * ri;
+    }
+    rz = bsum(rz);
+    bb = bsum(bb);
+    if (bb == 0.0) return;
+    for (int it = 0; it < maxit; ++it) {
+        double pq = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            float ax = p[i] / dinv[i];
+            for (int j = 0; j < kEll; ++j) {
+                const int32_t c = col[(int64_t)j * n + i];
+                if (c >= 0) ax = fmaf(val[(int64_t)j * n + i], p[c], ax);
+            }
+            q[i] = ax;
+            pq += (double)p[i] * ax;
+        }
+        pq = bsum(pq);
+        if (pq <= 0.0) break;
+        const float alpha = (float)(rz / pq);
+        double rr = 0.0, rz2 = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            x[i] += alpha * p[i];
+            const float ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            rr += (double)ri * ri;
+            rz2 += (double)ri * dinv[i] * ri;
+        }
+        rr = bsum(rr);
+        rz2 = bsum(rz2);
+        if (rr <= 1e-14 * bb) break;
+        const float beta = (float)(rz2 / rz);
+        rz = rz2;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = dinv[i] * r[i] + beta * p[i];
+        __syncthreads();
+    }
+    if (singular) {
+        double mx = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx += x[i];
+        mx = bsum(mx) / (double)n;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] -= (float)mx;
+    }
+}
+
+void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
+    Level &L = in.lv[g];
+    cudaStream_t s = ctx->stream;
+    if (g + 1 == in.lv.size()) {
+        const int maxit = (int)std::min<int64_t>(4 * L.n + 20, 2000);
+        // r, p, q: three slices of the coarsest level's work buffer (allocated 3n)
+        k_coarse_cg<<<1, 1024, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, L.t + L.n, L.t + 2 * L.n,
+                                       singular, maxit);
+        count_launch(ctx);
+        return;
+    }
+    Level &C = in.lv[g + 1];
+    const unsigned nb = blocks_for(L.n);
+    // pre-smoothing (x starts at zero)
+    for (int k = 0; k < kNu; ++k) {
+        k_jacobi<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, k == 0);
+        std::swap(L.x, L.t);
+    }
+    k_restrict_residual<<<blocks_for(C.n), kT, 0, s>>>(C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
+    count_launch(ctx, kNu + 1);
+    vcycle(ctx, in, g + 1, singular);
+    k_prolong<<<nb, kT, 0, s>>>(L.n, L.parent, C.x, L.x);
+    for (int k = 0; k < kNu; ++k) {
+        k_jacobi<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, 0);
+        std::swap(L.x, L.t);
+    }
+    count_launch(ctx, kNu + 1);
+}
+}  // namespace
+
+void poisson_setup(pic_ctx *ctx, Instance &in) {
+    DeviceArena &A = in.mesh_mem;
+    const int64_t n = in.lv[0].n;
+    in.phi = dalloc<double>(A, n);
+    in.bvec = dalloc<double>(A, n);
+    in.res = dalloc<double>(A, n);
+    in.charge = dalloc<double>(A, n);
+    in.red = dalloc<double>(A, 2 * kRedBlocks + 8);
+    GB_CUDA(cudaMemsetAsync(in.phi, 0, n * 8, ctx->stream));
+    GB_CUDA(cudaMemsetAsync(in.bvec, 0, n * 8, ctx->stream));
+    GB_CUDA(cudaMemsetAsync(in.charge, 0, n * 8, ctx->stream));
+    // coarsest-level CG needs three extra vectors: give it its own buffers
+    Level &c = in.lv.back();
+    c.t = dalloc<float>(A, 3 * c.n + 16);
+}
+
+// Solve A phi = bvec to ||r|| <= mg_rel_tol ||b||, warm-started from the current phi.
+void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
+    (void)walls;
+    Level &L = in.lv[0];
+    cudaStream_t s = ctx->stream;
+    const int64_t n = L.n;
+    const bool singular = in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC;
+    if (singular) {
+        k_area_moments<<<kRedBlocks, kT, 0, s>>>(n, L.lev, L.lmax, in.bvec, in.red);
+        k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+        k_project<<<blocks_for(n), kT, 0, s>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.bvec, 0);
+        count_launch(ctx, 3);
+    }
+    double rel = 0.0;
+    int cyc = 0;
+    const int maxc = std::max(1, in.cfg.mg_max_cycles);
+    for (;;) {
+        k_residual64<<<kRedBlocks, kT, 0, s>>>(n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b, in.red);
+        k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+        count_launch(ctx, 2);
+        GB_CUDA(cudaMemcpyAsync(in.red_host, in.red + 2 * kRedBlocks, 16, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        const double rr = in.red_host[0], bb = in.red_host[1];
+        rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+        if (rel <= in.cfg.mg_rel_tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
+        vcycle(ctx, in, 0, singular);
+        k_add_correction<<<blocks_for(n), kT, 0, s>>>(n, L.x, in.phi);
+        count_launch(ctx);
+        if (singular) {
+            k_area_weighted<<<kRedBlocks, kT, 0, s>>>(n, L.lev, L.lmax, in.phi, in.red);
+            k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+            k_project<<<blocks_for(n), kT, 0, s>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
+            count_launch(ctx, 3);
+        }
+        ++cyc;
+    }
+    check_launch("poisson_solve");
+    in.mg_cycles = cyc;
+    in.mg_res = rel;
+}
+
+}  // namespace gbpic

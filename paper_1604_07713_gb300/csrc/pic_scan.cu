@@ -1,0 +1,100 @@
+// Exclusive prefix sums of int32 arrays (reduce -> scan of block totals -> rescan), used for
+// the cell-list offsets, the spawn ranks and the multigrid level construction.
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+namespace {
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total) {
+    __shared__ int32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int32_t before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_tile_sums(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ part) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    int32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// One block scans the tile totals in chunks, carrying the running sum.
+__global__ void k_scan_parts(int32_t *__restrict__ part, int64_t nparts, int32_t *__restrict__ total) {
+    int32_t carry = 0;
+    for (int64_t c0 = 0; c0 < nparts; c0 += kScanThreads) {
+        const int64_t i = c0 + threadIdx.x;
+        const int32_t v = i < nparts ? part[i] : 0;
+        int32_t tot;
+        const int32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nparts) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_tile_scan(const int32_t *__restrict__ in, int64_t n, const int32_t *__restrict__ part,
+                            int32_t *__restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int32_t tot;
+    int32_t run = block_exclusive_scan(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+}  // namespace
+
+int64_t scan_scratch_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
+
+// out[0..n-1] = exclusive prefix of in, out[n] = total.  scratch: scan_scratch_elems(n).
+// `in` and `out` may alias.
+void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *scratch) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 0) {
+        GB_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), ctx->stream));
+        return;
+    }
+    k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch);
+    k_scan_parts<<<1, kScanThreads, 0, ctx->stream>>>(scratch, tiles, out + n);
+    k_tile_scan<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch, out);
+    count_launch(ctx, 3);
+    check_launch("exclusive_scan_i32");
+}
+
+}  // namespace gbpic

@@ -1,0 +1,56 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, exports every function
+that include/gbpic.h declares, and the Python mirror of pic_config has the C layout."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1604_07713_gb300 as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbpic.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"GBPIC_API\s+[\w\s\*]+?\b(pic_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    G.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", G.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s(pic_\w+)", out))
+    declared = _declared()
+    assert len(declared) >= 18
+    assert set(declared) <= exported, set(declared) - exported
+    assert set(G.EXPORTED) == set(declared)
+    L = C.CDLL(G.LIB_PATH)
+    for name in declared:
+        assert hasattr(L, name)
+
+
+def test_config_struct_layout_matches_header(tmp_path):
+    fields = [f[0] for f in G.PicConfig._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){',
+           'printf("%zu\\n", sizeof(pic_config));']
+    for f in fields:
+        src.append(f'printf("%zu\\n", offsetof(pic_config, {f}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", str(c), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == C.sizeof(G.PicConfig)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(G.PicConfig, f).offset == off, f
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(G, "_lib", None)
+    monkeypatch.setattr(G, "LIB_PATH", "/nonexistent/libgbpic.so")
+    with pytest.raises(RuntimeError):
+        G.lib()

@@ -1,0 +1,216 @@
+"""GPU path (C ABI, CUDA kernels) against the FP64 CPU oracle, phase by phase from
+identical seeded inputs.
+
+Bars: leaf location, cell-list order (ids), per-leaf counts and collision decisions are
+bit-exact (FP32 mode: exact except for the few particles whose FP32 position lies within
+rounding of a face or whose collision probability lies within rounding of its uniform,
+which are counted and bounded); fields within 1e-5 relative in FP32 mode and 1e-12 in FP64
+mode (per field, ||a - b|| / ||b||).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1604_07713_gb300 as G
+from paper_1604_07713_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    G.build()
+    O.build()
+
+
+def _oracle(cfg, mesh, parts):
+    M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], mesh.get("lmax", 0), cfg["bc_x"], cfg["bc_y"],
+               mesh.get("root"), mesh.get("level"), mesh.get("morton"))
+    sim = O.Sim(cfg, M)
+    for s in sorted(parts):
+        sim.load(s, **parts[s])
+    return sim
+
+
+def _gpu(cfg, mesh, parts):
+    ctx = G.Context(cfg)
+    ctx.set_mesh_dict(mesh)
+    for s in sorted(parts):
+        ctx.load(s, **parts[s])
+    return ctx
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _amr_mesh(nx0, ny0, h0, lmax, seed, px=False, py=False):
+    r, l, m = W.random_tree(nx0, ny0, lmax, 0.3, seed, px, py)
+    return dict(nx0=nx0, ny0=ny0, h0=h0, lmax=lmax, root=r, level=l, morton=m)
+
+
+def _ccp_small(precision, nx=64, ny=8, ppc=20, seed=7, te=2.5, ng=9.6e20):
+    cfg, mesh, parts = W.ccp(nx=nx, ny=ny, ppc=ppc, seed=seed, precision=precision, te=te, ng=ng)
+    cfg["mg_rel_tol"] = 1e-13 if precision == W.FP64 else 1e-11
+    return cfg, mesh, parts
+
+
+# ---------------------------------------------------------------------------------------
+# A1: tree build and point location
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [W.FP32, W.FP64])
+def test_mesh_order_and_location_bit_exact(precision):
+    mesh = _amr_mesh(5, 3, 0.25, 3, 11, py=True)
+    cfg = W.base_config(precision=precision, n_species=1, bc_x=W.BC_DIRICHLET, bc_y=W.BC_PERIODIC,
+                        max_level=3, q=[-1.0], m=[1.0])
+    sim = _oracle(cfg, mesh, {})
+    M = sim.mesh
+    rng = np.random.default_rng(3)
+    n = 20000
+    x = rng.random(n) * M.lx; y = rng.random(n) * M.ly
+    # points exactly on faces and corners of every leaf (dyadic h0: exact in FP64)
+    xf = M.ix * M.hf; yf = M.iy * M.hf
+    x = np.concatenate([x, xf, xf + 0.5 * M.h(), xf]); y = np.concatenate([y, yf, yf, yf + 0.5 * M.h()])
+    z = np.zeros(x.size)
+    parts = {0: dict(x=x, y=y, vx=z, vy=z, vz=z, w=np.ones(x.size))}
+    sim.load(0, **parts[0])
+    with _gpu(cfg, mesh, parts) as ctx:
+        r, m, lv = ctx.mesh()
+        assert np.array_equal(r, M.root) and np.array_equal(m, M.morton) and np.array_equal(lv, M.level)
+        gp = ctx.particles(0)
+        cnt = ctx.fields(G.PIC_FIELD_COUNT_E)
+    sp = sim.species[0]
+    assert np.array_equal(gp["id"], sp.id)                     # cell-list order
+    assert np.array_equal(gp["leaf"].astype(np.int64), sp.leaf)  # leaf of every particle
+    assert np.array_equal(cnt, sim.counts(0))
+    tol = 1e-7 if precision == W.FP32 else 1e-15
+    assert np.abs(gp["x"] - sp.x).max() <= tol * M.lx
+
+
+# ---------------------------------------------------------------------------------------
+# A6 deposit, A7 Poisson, A2 corner field
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [W.FP32, W.FP64])
+@pytest.mark.parametrize("amr", [False, True])
+def test_fields_parity(precision, amr):
+    cfg, mesh, parts = _ccp_small(precision, nx=32, ny=8, ppc=30)
+    if amr:
+        mesh = _amr_mesh(32, 8, mesh["h0"], 2, 5, py=True)
+        cfg["max_level"] = 2
+    sim = _oracle(cfg, mesh, parts)
+    rho_o, phi_o, E_o = sim.fields()
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.compute_fields()
+        rho = ctx.fields(G.PIC_FIELD_RHO)
+        phi = ctx.fields(G.PIC_FIELD_PHI)
+        E = ctx.fields(G.PIC_FIELD_NODE_E)
+        c = ctx.counts()
+    tol = 1e-5 if precision == W.FP32 else 1e-12
+    assert _rel(rho, rho_o) < (1e-6 if precision == W.FP32 else 1e-13)
+    assert _rel(phi, phi_o) < tol
+    assert _rel(E.reshape(-1), E_o.reshape(-1)) < tol
+    assert c["mg_rel_res"] <= cfg["mg_rel_tol"]
+
+
+def test_fields_periodic_cold_plasma_fp64():
+    cfg, mesh, parts = W.cold_plasma(n_side=32, ppc=4)
+    sim = _oracle(cfg, mesh, parts)
+    rho_o, phi_o, E_o = sim.fields()
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.compute_fields()
+        phi = ctx.fields(G.PIC_FIELD_PHI)
+        E = ctx.fields(G.PIC_FIELD_NODE_E)
+    assert _rel(phi, phi_o) < 1e-12
+    assert _rel(E.reshape(-1), E_o.reshape(-1)) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# A3 + A4 + A5: one full step from identical state
+# ---------------------------------------------------------------------------------------
+def _by_id(d):
+    o = np.argsort(d["id"])
+    return {k: v[o] for k, v in d.items()}
+
+
+def test_one_step_fp64_bit_exact_lists_with_ionization():
+    # hot electrons in dense gas: many elastic collisions and ionizations in one step
+    cfg, mesh, parts = _ccp_small(W.FP64, nx=32, ny=8, ppc=40, te=30.0, ng=3e21)
+    cfg["dt"] *= 4
+    sim = _oracle(cfg, mesh, parts)
+    sim.step(1)
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.step(1)
+        g = [ctx.particles(s) for s in (0, 1)]
+    n_sp = sim.species[1].n - parts[1]["x"].size
+    assert n_sp > 20, "the case must exercise ionization"
+    for s in (0, 1):
+        sp = sim.species[s]
+        assert np.array_equal(g[s]["id"], sp.id), f"species {s}: cell-list order differs"
+        assert np.array_equal(g[s]["leaf"].astype(np.int64), sp.leaf)
+        for k, ref in (("x", sp.x), ("y", sp.y), ("vx", sp.vx), ("vy", sp.vy), ("vz", sp.vz), ("w", sp.w)):
+            scale = np.abs(ref).max()
+            assert np.abs(g[s][k] - ref).max() <= 1e-12 * scale, (s, k)
+
+
+def test_one_step_fp32_within_tolerance():
+    cfg, mesh, parts = _ccp_small(W.FP32, nx=32, ny=8, ppc=40, te=30.0, ng=3e21)
+    cfg["dt"] *= 4
+    sim = _oracle(cfg, mesh, parts)
+    sim.step(1)
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.step(1)
+        g = [ctx.particles(s) for s in (0, 1)]
+    h = mesh["h0"]
+    for s in (0, 1):
+        sp = sim.species[s]
+        a = _by_id(g[s])
+        o = np.argsort(sp.id)
+        ids_o = sp.id[o]
+        common = np.intersect1d(a["id"], ids_o)
+        # particles whose collision decision flipped within FP32 rounding are the only
+        # allowed differences in the population
+        assert common.size >= 0.999 * max(a["id"].size, ids_o.size)
+        ia = np.searchsorted(a["id"], common); io = o[np.searchsorted(ids_o, common)]
+        dx = np.abs(a["x"][ia] - sp.x[io])
+        assert np.quantile(dx, 0.999) <= 1e-5 * h
+        v_o = np.sqrt(sp.vx[io] ** 2 + sp.vy[io] ** 2 + sp.vz[io] ** 2)
+        v_g = np.sqrt(a["vx"][ia] ** 2 + a["vy"][ia] ** 2 + a["vz"][ia] ** 2)
+        close = np.abs(v_g - v_o) <= 1e-5 * v_o.max()
+        assert close.mean() >= 0.999
+        # leaf agreement except at faces (FP32 offsets vs FP64 absolute positions)
+        same_leaf = a["leaf"][ia].astype(np.int64) == sp.leaf[io]
+        assert same_leaf.mean() >= 0.9999
+
+
+@pytest.mark.parametrize("amr", [False, True])
+def test_multi_step_fp64_cold_plasma_tracks_oracle(amr):
+    cfg, mesh, parts = W.cold_plasma(n_side=32, ppc=4, dt=0.05)
+    if amr:
+        mesh = _amr_mesh(32, 32, mesh["h0"], 2, 9, px=True, py=True)
+        cfg["max_level"] = 2
+    sim = _oracle(cfg, mesh, parts)
+    sim.step(10)
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.step(10)
+        g = ctx.particles(0)
+    sp = sim.species[0]
+    assert np.array_equal(g["id"], sp.id)
+    assert np.abs(g["x"] - sp.x).max() < 1e-10
+    assert np.abs(g["vx"] - sp.vx).max() < 1e-10 * max(1e-30, np.abs(sp.vx).max()) + 1e-14
+
+
+def test_streamer_like_amr_step_fp64():
+    # Dirichlet x (uniform background field), Neumann y, AMR tree, ionizing electrons
+    tree = W.streamer_tree(nx0=16, lmax=2)
+    cfg, mesh, parts = W.streamer(n_particles=6000, nx0=16, lmax=2, precision=W.FP64, tree=tree)
+    cfg["mg_rel_tol"] = 1e-13
+    sim = _oracle(cfg, mesh, parts)
+    sim.step(2)
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.step(2)
+        g = [ctx.particles(s) for s in (0, 1)]
+    for s in (0, 1):
+        sp = sim.species[s]
+        assert np.array_equal(g[s]["id"], sp.id)
+        assert np.abs(g[s]["x"] - sp.x).max() <= 1e-12 * 0.01
