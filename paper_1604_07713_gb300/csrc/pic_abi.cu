@@ -172,6 +172,8 @@ pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out)
             GB_CUDA(cudaMallocHost(&in.cnt_host, 64));
             GB_CUDA(cudaMalloc(&in.d_next_id, 8));
             GB_CUDA(cudaMemset(in.d_next_id, 0, 8));
+            GB_CUDA(cudaMalloc(&in.d_err, 4));
+            GB_CUDA(cudaMemset(in.d_err, 0, 4));
         }
         ctx->precision = cfg[0].precision;
         return PIC_OK;
@@ -194,6 +196,7 @@ pic_status pic_destroy(pic_ctx *ctx) {
         if (in.red_host) cudaFreeHost(in.red_host);
         if (in.cnt_host) cudaFreeHost(in.cnt_host);
         if (in.d_next_id) cudaFree(in.d_next_id);
+        if (in.d_err) cudaFree(in.d_err);
     }
     for (auto &r : ctx->trec) {
         cudaEventDestroy(r.a);
@@ -281,6 +284,14 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
                 particle_step(ctx, in, ctx->step);
             }
             ++ctx->step;
+        }
+        for (Instance &in : ctx->inst) {
+            GB_CUDA(cudaMemcpyAsync(in.cnt_host + 8, in.d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GB_CUDA(cudaStreamSynchronize(ctx->stream));
+            if (in.cnt_host[8] != 0) {
+                ctx->poisoned = true;
+                fail(PIC_ESTATE, "particle bookkeeping mismatch between count and move passes");
+            }
         }
         if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
         return st;

@@ -97,6 +97,7 @@ struct Instance {
     Species sp[2];
     int64_t next_id = 0;                     // host mirror (exact after a sync)
     unsigned long long *d_next_id = nullptr; // device counter of the next particle id
+    int32_t *d_err = nullptr;                // device-side consistency flag (0 = fine)
     int mg_cycles = 0;
     double mg_res = 0;
     DeviceArena mesh_mem;        // freed on pic_set_mesh

@@ -146,6 +146,8 @@ template <typename R> struct PushArgs {
     uint32_t *ion_key;
     const int32_t *ion_start_new, *ion_stay, *ion_start_old;
     int32_t *ion_fill;
+    int32_t cap, ion_cap;  // record capacity of the output buffers
+    int32_t *err;          // set when a write would fall outside them (count/move mismatch)
     // collisions
     int mcc, species;
     R ng_dt, sig_el, sig_iz0, eps_th, half_m_over_qe, two_qe_over_m, two_m_over_mn;
@@ -325,28 +327,39 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
                     } else {
                         const int32_t slot = atomicAdd(a.fill + nl, 1);
                         dst = a.start_new[nl] + a.stay_new[nl] + slot;
-                        a.key_out[dst] = (uint32_t)p;
+                        if (dst >= 0 && dst < a.cap) a.key_out[dst] = (uint32_t)p;
                     }
+                    if (dst < 0 || dst >= a.cap) { atomicExch(a.err, 1); dst = -1; }
+                    if (dst >= 0) {
                     a.out.u[dst] = u; a.out.v[dst] = v;
                     a.out.vx[dst] = vx; a.out.vy[dst] = vy; a.out.vz[dst] = vz;
                     a.out.w[dst] = w; a.out.id[dst] = id;
+                    }
                 }
                 if (spawns) {
                     const int32_t rank = sbase + spawn_run + __popc(spawn_mask & lanemask_lt());
                     const unsigned long long base = *a.next_id + 2ull * (unsigned long long)rank;
                     const int32_t slot = atomicAdd(a.fill + nl, 1);
                     const int32_t dst = a.start_new[nl] + a.stay_new[nl] + slot;
-                    a.key_out[dst] = (uint32_t)(n_old + p);
-                    a.out.u[dst] = u; a.out.v[dst] = v;
-                    a.out.vx[dst] = sv[0]; a.out.vy[dst] = sv[1]; a.out.vz[dst] = sv[2];
-                    a.out.w[dst] = w; a.out.id[dst] = (uint32_t)base;
+                    if (dst < 0 || dst >= a.cap) {
+                        atomicExch(a.err, 1);
+                    } else {
+                        a.key_out[dst] = (uint32_t)(n_old + p);
+                        a.out.u[dst] = u; a.out.v[dst] = v;
+                        a.out.vx[dst] = sv[0]; a.out.vy[dst] = sv[1]; a.out.vz[dst] = sv[2];
+                        a.out.w[dst] = w; a.out.id[dst] = (uint32_t)base;
+                    }
                     if (a.ion_fill) {
                         const int32_t islot = atomicAdd(a.ion_fill + nl, 1);
                         const int32_t idst = a.ion_start_new[nl] + a.ion_stay[nl] + islot;
+                        if (idst < 0 || idst >= a.ion_cap) {
+                            atomicExch(a.err, 1);
+                        } else {
                         a.ion_key[idst] = (uint32_t)(a.ion_start_old[a.nleaf] + p);
                         a.ion_out.u[idst] = u; a.ion_out.v[idst] = v;
                         a.ion_out.vx[idst] = si[0]; a.ion_out.vy[idst] = si[1]; a.ion_out.vz[idst] = si[2];
                         a.ion_out.w[idst] = w; a.ion_out.id[idst] = (uint32_t)(base + 1);
+                        }
                     }
                 }
                 stay_run += __popc(stay_mask);
@@ -530,6 +543,9 @@ template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, i
     a.k0 = (uint32_t)(c.seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(c.seed >> 32);
     a.inst_word = (uint32_t)c.instance << 24;
+    a.cap = (int32_t)sp.cap;
+    a.ion_cap = in.cfg.n_species > 1 ? (int32_t)in.sp[1].cap : 0;
+    a.err = in.d_err;
     a.step = (uint32_t)step;
     (void)ctx;
     return a;
