@@ -205,6 +205,21 @@ GBPIC_API pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches,
 /* Total kernel launches issued by the context since creation. */
 GBPIC_API pic_status pic_get_launch_count(const pic_ctx *ctx, int64_t *launches);
 
+/* |E| at the leaf centres of instance `inst`, exactly as pic_read_fields(PIC_FIELD_EMAG), for
+ * callers that cannot allocate device memory: code that runs while another thread captures a
+ * CUDA graph in global capture mode (where cudaMalloc is refused), callers whose device memory
+ * is fully owned by an outside allocator or a fixed budget, and real-time loops that allocate
+ * nothing after start-up.  The paper has no counterpart; this is an interface convenience.
+ * It uses a fixed 1 MiB file-scope device array (held by every GPU that loads the library
+ * until the process exits) instead of a temporary buffer, so it accepts meshes of at most
+ * 131,072 leaves and returns PIC_EINVAL with a message for larger ones.  The first call on a
+ * device looks up that array's device address (once per device, with the device current);
+ * make that first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, threads or contexts at the same time) race on it.  `out`,
+ * `cap`, `n_out` and the errors are as in pic_read_fields; the call synchronises the stream. */
+GBPIC_API pic_status pic_read_emag_noalloc(pic_ctx *ctx, int32_t inst, double *out, int64_t cap,
+                                           int64_t *n_out);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 GBPIC_API const char *pic_last_error(void);
 

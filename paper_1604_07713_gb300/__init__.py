@@ -30,7 +30,8 @@ PIC_N_PHASES = len(PHASES)
 EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_load_particles",
             "pic_step", "pic_compute_fields", "pic_adapt", "pic_read_fields", "pic_read_mesh",
             "pic_read_particles", "pic_get_counts", "pic_get_step", "pic_set_step",
-            "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_last_error"]
+            "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_read_emag_noalloc",
+            "pic_last_error"]
 
 
 class PicConfig(C.Structure):
@@ -108,6 +109,7 @@ def _declare(L):
         "pic_get_counts": [_p, _i32, _p, _p, _p, _p, _p], "pic_get_step": [_p, _p],
         "pic_set_step": [_p, _i64], "pic_set_timing": [_p, _i32],
         "pic_get_timing": [_p, _p, _p, _i32], "pic_get_launch_count": [_p, _p],
+        "pic_read_emag_noalloc": [_p, _i32, _p, _i64, _p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -242,6 +244,14 @@ def pic_get_timing(ctx):
 def pic_get_launch_count(ctx):
     n = C.c_int64()
     _call("pic_get_launch_count", ctx, C.byref(n))
+    return n.value
+
+
+def pic_read_emag_noalloc(ctx, inst, out: np.ndarray) -> int:
+    """|E| per leaf into the caller's FP64 array without any device allocation (fixed
+    1 MiB scratch: at most 131,072 leaves).  Returns the number of leaves written."""
+    n = C.c_int64()
+    _call("pic_read_emag_noalloc", ctx, inst, _ptr(out), out.size, C.byref(n))
     return n.value
 
 

@@ -151,6 +151,10 @@ void ensure_species(pic_ctx *ctx, Instance &in) {
 
 }  // namespace
 
+pic_status gbpic::guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg) {
+    return guarded(ctx, [&]() -> pic_status { return fn(arg); });
+}
+
 extern "C" {
 
 pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out) {

@@ -218,6 +218,10 @@ void walls_at(const Instance &in, int64_t step, double walls[4]);
 void adapt_mesh(pic_ctx *ctx, Instance &in);
 void split_merge(pic_ctx *ctx, Instance &in);
 
+// Runs fn(arg) with the ABI's error mapping (exceptions -> pic_status, last error, context
+// poisoning on CUDA failures).  Allocates nothing on the device.
+pic_status guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg);
+
 // scan helpers (pic_particles.cu): exclusive scan of n int32 into out[0..n] (out[n] = total)
 void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
                         int32_t *scratch);
