@@ -143,6 +143,21 @@ void fields_of(pic_ctx *ctx, Instance &in, int64_t step) {
     }
 }
 
+void reset_solver_stats(pic_ctx *ctx, Instance &in) {
+    in.mg_res_max = 0.0;
+    if (in.mg_stats) GB_CUDA(cudaMemsetAsync(in.mg_stats + 2, 0, 8, ctx->stream));
+}
+
+// Worst relative residual of the solves since the last reset (synchronises the stream).
+double collect_solver_stats(pic_ctx *ctx, Instance &in) {
+    if (!in.mg_on_device || !in.mg_stats) return in.mg_res_max;
+    GB_CUDA(cudaMemcpyAsync(in.red_host + 4, in.mg_stats, 3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    in.mg_cycles = (int)in.red_host[4];
+    in.mg_res = in.red_host[5];
+    return std::max(in.mg_res_max, in.red_host[6]);
+}
+
 void ensure_species(pic_ctx *ctx, Instance &in) {
     // a species never loaded is an empty population
     for (int s = 0; s < in.cfg.n_species; ++s)
@@ -263,8 +278,9 @@ pic_status pic_compute_fields(pic_ctx *ctx) {
         for (Instance &in : ctx->inst) {
             if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
             ensure_species(ctx, in);
+            reset_solver_stats(ctx, in);
             fields_of(ctx, in, ctx->step);
-            if (in.mg_res > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
         }
         if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
         return st;
@@ -278,18 +294,19 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
         for (Instance &in : ctx->inst) {
             if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
             ensure_species(ctx, in);
+            reset_solver_stats(ctx, in);
         }
         pic_status st = PIC_OK;
         for (int32_t k = 0; k < n_steps; ++k) {
             for (Instance &in : ctx->inst) {
                 ensure_capacity(ctx, in);
                 fields_of(ctx, in, ctx->step);
-                if (in.mg_res > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
                 particle_step(ctx, in, ctx->step);
             }
             ++ctx->step;
         }
         for (Instance &in : ctx->inst) {
+            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
             GB_CUDA(cudaMemcpyAsync(in.cnt_host + 8, in.d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
             GB_CUDA(cudaStreamSynchronize(ctx->stream));
             if (in.cnt_host[8] != 0) {
@@ -440,6 +457,7 @@ pic_status pic_get_counts(pic_ctx *ctx, int32_t inst, int64_t *n_leaves, int64_t
                 c[s] = in.cnt_host[s];
                 in.sp[s].n = in.sp[s].n_upper = c[s];
             }
+        collect_solver_stats(ctx, in);
         if (n_leaves) *n_leaves = in.nleaf;
         if (n_e) *n_e = c[0];
         if (n_i) *n_i = c[1];

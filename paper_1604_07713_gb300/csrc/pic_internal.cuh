@@ -100,6 +100,9 @@ struct Instance {
     int32_t *d_err = nullptr;                // device-side consistency flag (0 = fine)
     int mg_cycles = 0;
     double mg_res = 0;
+    double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
+    bool mg_on_device = false;     // last solve ran its loop on the device (stats below)
+    double *mg_stats = nullptr;    // device: [cycles, rel. residual, max rel. since reset]
     DeviceArena mesh_mem;        // freed on pic_set_mesh
     DeviceArena part_mem[2];     // freed on reload / regrow
 };

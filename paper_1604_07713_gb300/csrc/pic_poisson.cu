@@ -16,6 +16,7 @@ constexpr int kT = 256;
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs: fixed so that the FP64 sums are deterministic
 constexpr float kOmega = 0.8f;
 constexpr int kNu = 3;
+constexpr double kCoarseTol2 = 1e-10;  // coarsest solve: ||r|| <= 1e-5 ||b|| (FP32 reachable)
 inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(int64_t n, const int32_t *__
         }
         rr = bsum(rr);
         rz2 = bsum(rz2);
-        if (rr <= 1e-14 * bb) break;
+        if (rr <= kCoarseTol2 * bb) break;
         const float beta = (float)(rz2 / rz);
         rz = rz2;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = dinv[i] * r[i] + beta * p[i];
@@ -229,11 +230,371 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(int64_t n, const int32_t *__
     }
 }
 
+// ---- levels held in shared memory by one block (n <= kSmallN cells each) ----------------
+constexpr int kSmallN = 8192;          // 8 cells per thread of a 1024-thread block
+constexpr int kMaxSmallLevels = 16;
+constexpr int kSmallSmemCap = 200 * 1024;
+
+struct SmallLevel {
+    int32_t n;
+    const int32_t *col;
+    const float *val, *dinv;
+    const int32_t *child4;  // children (in the finer level) of this level's cells
+    const int32_t *parent;  // this level's cells -> cells of the next coarser level
+    int32_t off;            // smem offset (floats) of x; b follows at off + n
+};
+struct SmallDesc {
+    int nlev;  // levels g0 .. g0 + nlev - 1 live in shared memory
+    SmallLevel lv[kMaxSmallLevels];
+    int32_t off_cg;  // smem offset of the coarsest CG vectors r, p, q (3 n)
+    int32_t smem_floats;
+};
+
+__device__ void sm_jacobi(const SmallLevel &L, float *x, const float *b, bool first) {
+    float t[kSmallN / 1024];
+    int k = 0;
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x, ++k) {
+        if (first) {
+            t[k] = kOmega * L.dinv[i] * b[i];
+        } else {
+            float off = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kEll; ++j) {
+                const int32_t c = L.col[(int64_t)j * L.n + i];
+                if (c >= 0) off = fmaf(L.val[(int64_t)j * L.n + i], x[c], off);
+            }
+            t[k] = (1.0f - kOmega) * x[i] + kOmega * L.dinv[i] * (b[i] - off);
+        }
+    }
+    __syncthreads();
+    k = 0;
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x, ++k) x[i] = t[k];
+    __syncthreads();
+}
+
+__device__ double sm_block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        red[32] = s;
+    }
+    __syncthreads();
+    const double out = red[32];
+    __syncthreads();
+    return out;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Coarsest level: Jacobi-preconditioned CG in shared memory (one uniform level: symmetric).
+// Up to 256 cells it runs on the first warp alone (shuffle reductions, no block barriers).
+__device__ void sm_coarse_cg(const SmallLevel &L, float *x, const float *b, float *r, float *p, float *q,
+                             bool singular, double *red) {
+    const int n = L.n;
+    const int maxit = min(2 * n + 10, 500);
+    if (n <= 256) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double mb = 0.0;
+            if (singular) {
+                for (int i = lane; i < n; i += 32) mb += b[i];
+                mb = warp_sum(mb) / (double)n;
+            }
+            double rz = 0.0, bb = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const float ri = b[i] - (float)mb;
+                x[i] = 0.0f;
+                r[i] = ri;
+                const float zi = L.dinv[i] * ri;
+                p[i] = zi;
+                rz += (double)ri * zi;
+                bb += (double)ri * ri;
+            }
+            rz = warp_sum(rz);
+            bb = warp_sum(bb);
+            __syncwarp();
+            if (bb > 0.0) {
+                for (int it = 0; it < maxit; ++it) {
+                    double pq = 0.0;
+                    for (int i = lane; i < n; i += 32) {
+                        float ax = p[i] / L.dinv[i];
+                        for (int j = 0; j < kEll; ++j) {
+                            const int32_t c = L.col[(int64_t)j * n + i];
+                            if (c >= 0) ax = fmaf(L.val[(int64_t)j * n + i], p[c], ax);
+                        }
+                        q[i] = ax;
+                        pq += (double)p[i] * ax;
+                    }
+                    pq = warp_sum(pq);
+                    if (pq <= 0.0) break;
+                    const float alpha = (float)(rz / pq);
+                    double rr = 0.0, rz2 = 0.0;
+                    for (int i = lane; i < n; i += 32) {
+                        x[i] += alpha * p[i];
+                        const float ri = r[i] - alpha * q[i];
+                        r[i] = ri;
+                        rr += (double)ri * ri;
+                        rz2 += (double)ri * L.dinv[i] * ri;
+                    }
+                    rr = warp_sum(rr);
+                    rz2 = warp_sum(rz2);
+                    if (rr <= kCoarseTol2 * bb) break;
+                    const float beta = (float)(rz2 / rz);
+                    rz = rz2;
+                    __syncwarp();
+                    for (int i = lane; i < n; i += 32) p[i] = L.dinv[i] * r[i] + beta * p[i];
+                    __syncwarp();
+                }
+            }
+            if (singular) {
+                double mx = 0.0;
+                for (int i = lane; i < n; i += 32) mx += x[i];
+                mx = warp_sum(mx) / (double)n;
+                for (int i = lane; i < n; i += 32) x[i] -= (float)mx;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    double mb = 0.0;
+    if (singular) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) mb += b[i];
+        mb = sm_block_sum(mb, red) / (double)n;
+    }
+    double rz = 0.0, bb = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float ri = b[i] - (float)mb;
+        x[i] = 0.0f;
+        r[i] = ri;
+        const float zi = L.dinv[i] * ri;
+        p[i] = zi;
+        rz += (double)ri * zi;
+        bb += (double)ri * ri;
+    }
+    rz = sm_block_sum(rz, red);
+    bb = sm_block_sum(bb, red);
+    if (bb > 0.0) {
+        for (int it = 0; it < maxit; ++it) {
+            double pq = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                float ax = p[i] / L.dinv[i];
+                for (int j = 0; j < kEll; ++j) {
+                    const int32_t c = L.col[(int64_t)j * n + i];
+                    if (c >= 0) ax = fmaf(L.val[(int64_t)j * n + i], p[c], ax);
+                }
+                q[i] = ax;
+                pq += (double)p[i] * ax;
+            }
+            pq = sm_block_sum(pq, red);
+            if (pq <= 0.0) break;
+            const float alpha = (float)(rz / pq);
+            double rr = 0.0, rz2 = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                x[i] += alpha * p[i];
+                const float ri = r[i] - alpha * q[i];
+                r[i] = ri;
+                rr += (double)ri * ri;
+                rz2 += (double)ri * L.dinv[i] * ri;
+            }
+            rr = sm_block_sum(rr, red);
+            rz2 = sm_block_sum(rz2, red);
+            if (rr <= kCoarseTol2 * bb) break;
+            const float beta = (float)(rz2 / rz);
+            rz = rz2;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = L.dinv[i] * r[i] + beta * p[i];
+            __syncthreads();
+        }
+    }
+    if (singular) {
+        double mx = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) mx += x[i];
+        mx = sm_block_sum(mx, red) / (double)n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= (float)mx;
+    }
+    __syncthreads();
+}
+
+// V-cycle over the shared-memory levels; b of the first level must be in place, x of the
+// first level holds the correction on return.
+__device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, double *red) {
+    const int last = D.nlev - 1;
+    for (int g = 0; g < last; ++g) {
+        const SmallLevel &L = D.lv[g], &Cc = D.lv[g + 1];
+        float *x = sm + L.off, *b = x + L.n;
+        for (int k = 0; k < kNu; ++k) sm_jacobi(L, x, b, k == 0);
+        float *bc = sm + Cc.off + Cc.n;
+        for (int p = threadIdx.x; p < Cc.n; p += blockDim.x) {
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t i = Cc.child4[4 * p + k];
+                if (i < 0) continue;
+                float ax = x[i] / L.dinv[i];
+#pragma unroll
+                for (int j = 0; j < kEll; ++j) {
+                    const int32_t c = L.col[(int64_t)j * L.n + i];
+                    if (c >= 0) ax = fmaf(L.val[(int64_t)j * L.n + i], x[c], ax);
+                }
+                s += b[i] - ax;
+            }
+            bc[p] = s;
+        }
+        __syncthreads();
+    }
+    {
+        const SmallLevel &L = D.lv[last];
+        float *x = sm + L.off, *b = x + L.n;
+        float *r = sm + D.off_cg;
+        sm_coarse_cg(L, x, b, r, r + L.n, r + 2 * L.n, singular, red);
+    }
+    for (int g = last - 1; g >= 0; --g) {
+        const SmallLevel &L = D.lv[g], &Cc = D.lv[g + 1];
+        float *x = sm + L.off, *b = x + L.n;
+        const float *xc = sm + Cc.off;
+        for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += xc[L.parent[i]];
+        __syncthreads();
+        for (int k = 0; k < kNu; ++k) sm_jacobi(L, x, b, false);
+    }
+}
+
+// Tail of a V-cycle started by the multi-block levels: b from global, x back to global.
+__global__ void __launch_bounds__(1024) k_tail_vcycle(SmallDesc D, const float *__restrict__ gb,
+                                                       float *__restrict__ gx, int singular) {
+    extern __shared__ float sm[];
+    __shared__ double red[33];
+    const SmallLevel &L = D.lv[0];
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) sm[L.off + L.n + i] = gb[i];
+    __syncthreads();
+    sm_vcycle(D, sm, singular != 0, red);
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) gx[i] = sm[L.off + i];
+}
+
+// Whole solve for a mesh whose every level fits: FP64 residual and correction, FP32 V-cycles
+// in shared memory, convergence test on the device.  stats: [cycles, rel. residual, max rel.]
+__global__ void __launch_bounds__(1024) k_small_solve(SmallDesc D, const double *__restrict__ diag64,
+                                                       const double *__restrict__ val64, double *__restrict__ phi,
+                                                       double *__restrict__ bvec, const uint8_t *__restrict__ lev,
+                                                       int lmax, int singular, double tol, int maxc,
+                                                       double *__restrict__ stats) {
+    extern __shared__ float sm[];
+    __shared__ double red[33];
+    const SmallLevel &L = D.lv[0];
+    const int n = L.n;
+    if (singular) {  // right-hand side compatibility: remove an area-proportional share
+        double sb = 0.0, sa = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double s = (double)(1 << (lmax - lev[i]));
+            sb += bvec[i];
+            sa += s * s;
+        }
+        sb = sm_block_sum(sb, red);
+        sa = sm_block_sum(sa, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double s = (double)(1 << (lmax - lev[i]));
+            bvec[i] -= sb / sa * s * s;
+        }
+        __syncthreads();
+    }
+    double bb = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bb += bvec[i] * bvec[i];
+    bb = sm_block_sum(bb, red);
+    float *b0 = sm + L.off + n, *x0 = sm + L.off;
+    int cyc = 0;
+    double rel = 0.0;
+    for (;;) {
+        double rr = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double ax = diag64[i] * phi[i];
+#pragma unroll
+            for (int j = 0; j < kEll; ++j) {
+                const int32_t c = L.col[(int64_t)j * n + i];
+                if (c >= 0) ax += val64[(int64_t)j * n + i] * phi[c];
+            }
+            const double ri = bvec[i] - ax;
+            b0[i] = (float)ri;
+            rr += ri * ri;
+        }
+        rr = sm_block_sum(rr, red);
+        rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        if (rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
+        sm_vcycle(D, sm, singular != 0, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) phi[i] += (double)x0[i];
+        __syncthreads();
+        if (singular) {
+            double sv = 0.0, sa = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double s = (double)(1 << (lmax - lev[i]));
+                sv += s * s * phi[i];
+                sa += s * s;
+            }
+            sv = sm_block_sum(sv, red);
+            sa = sm_block_sum(sa, red);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) phi[i] -= sv / sa;
+            __syncthreads();
+        }
+        ++cyc;
+    }
+    if (threadIdx.x == 0) {
+        stats[0] = (double)cyc;
+        stats[1] = rel;
+        stats[2] = fmax(stats[2], rel);
+    }
+}
+
+// Which suffix of the level list fits one block's shared memory.
+int small_from(const Instance &in) {
+    int g0 = (int)in.lv.size();
+    int64_t floats = 0;
+    for (int g = (int)in.lv.size() - 1; g >= 0; --g) {
+        const Level &L = in.lv[g];
+        const int64_t add = 2 * L.n + (g == (int)in.lv.size() - 1 ? 3 * L.n + 8 : 0);
+        if (L.n > kSmallN || (int)in.lv.size() - g > kMaxSmallLevels || (floats + add) * 4 > kSmallSmemCap) break;
+        floats += add;
+        g0 = g;
+    }
+    return g0;
+}
+
+SmallDesc small_desc(const Instance &in, int g0) {
+    SmallDesc D{};
+    D.nlev = (int)in.lv.size() - g0;
+    int32_t off = 0;
+    for (int k = 0; k < D.nlev; ++k) {
+        const Level &L = in.lv[g0 + k];
+        SmallLevel &S = D.lv[k];
+        S.n = (int32_t)L.n; S.col = L.col; S.val = L.val; S.dinv = L.dinv;
+        S.child4 = L.child4; S.parent = L.parent; S.off = off;
+        off += 2 * (int32_t)L.n;
+    }
+    D.off_cg = off;
+    off += 3 * (int32_t)in.lv.back().n + 8;
+    D.smem_floats = off;
+    return D;
+}
+
 void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     Level &L = in.lv[g];
     cudaStream_t s = ctx->stream;
+    const int g0 = small_from(in);
+    if ((int)g >= g0) {
+        const SmallDesc D = small_desc(in, (int)g);
+        const size_t bytes = (size_t)D.smem_floats * 4;
+        GB_CUDA(cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
+        k_tail_vcycle<<<1, 1024, bytes, s>>>(D, L.b, L.x, singular);
+        count_launch(ctx);
+        return;
+    }
     if (g + 1 == in.lv.size()) {
-        const int maxit = (int)std::min<int64_t>(4 * L.n + 20, 2000);
+        const int maxit = (int)std::min<int64_t>(2 * L.n + 10, 500);
         // r, p, q: three slices of the coarsest level's work buffer (allocated 3n)
         k_coarse_cg<<<1, 1024, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, L.t + L.n, L.t + 2 * L.n,
                                        singular, maxit);
@@ -267,6 +628,8 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     in.res = dalloc<double>(A, n);
     in.charge = dalloc<double>(A, n);
     in.red = dalloc<double>(A, 2 * kRedBlocks + 8);
+    in.mg_stats = dalloc<double>(A, 4);
+    GB_CUDA(cudaMemsetAsync(in.mg_stats, 0, 4 * 8, ctx->stream));
     GB_CUDA(cudaMemsetAsync(in.phi, 0, n * 8, ctx->stream));
     GB_CUDA(cudaMemsetAsync(in.bvec, 0, n * 8, ctx->stream));
     GB_CUDA(cudaMemsetAsync(in.charge, 0, n * 8, ctx->stream));
@@ -282,6 +645,18 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     cudaStream_t s = ctx->stream;
     const int64_t n = L.n;
     const bool singular = in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC;
+    if (small_from(in) == 0) {
+        const SmallDesc D = small_desc(in, 0);
+        GB_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
+        k_small_solve<<<1, 1024, (size_t)D.smem_floats * 4, s>>>(D, L.diag64, L.val64, in.phi, in.bvec, L.lev, L.lmax,
+                                                                 singular ? 1 : 0, in.cfg.mg_rel_tol,
+                                                                 std::max(1, in.cfg.mg_max_cycles), in.mg_stats);
+        count_launch(ctx);
+        check_launch("poisson_solve");
+        in.mg_on_device = true;
+        return;
+    }
+    in.mg_on_device = false;
     if (singular) {
         k_area_moments<<<kRedBlocks, kT, 0, s>>>(n, L.lev, L.lmax, in.bvec, in.red);
         k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
@@ -314,6 +689,7 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     check_launch("poisson_solve");
     in.mg_cycles = cyc;
     in.mg_res = rel;
+    in.mg_res_max = std::max(in.mg_res_max, rel);
 }
 
 }  // namespace gbpic
