@@ -103,18 +103,6 @@ def _declare(L):
     L.or_push_mcc.argtypes = [C.POINTER(_Mesh), C.POINTER(_PushParams), _p, _i64, _p, _p, _p,
                               _p, _p, _p, _p, _p, _p, _p, _p]
     L.or_push_mcc.restype = _i64
-    if hasattr(L, "or_adapt_flags"):
-        _declare_adapt(L)
-
-
-def _declare_adapt(L):
-    L.or_adapt_flags.argtypes = [C.POINTER(_Mesh), _p, _p, C.c_double, C.c_double, _i32,
-                                 _i32, _i32, _p]
-    L.or_adapt_flags.restype = _i64
-    L.or_split_merge_leaf.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, C.c_double,
-                                      C.c_double, C.c_double, C.c_double, _i32, _i32, _i32,
-                                      _i32, _p, _p, _p, _p, _p, _p, _p, _p, _p]
-    L.or_split_merge_leaf.restype = _i64
 
 
 def _ptr(a):
@@ -311,6 +299,7 @@ class Sim:
         self.next_id = 0
         self.species: list[Species | None] = [None] * len(self.cfg["q"])
         self.phi = np.zeros(mesh.nleaf)
+        self.last_walls = None
         self.last_rho = None
         self.last_node_e = None
 
@@ -360,8 +349,18 @@ class Sim:
         walls = self.walls()
         phi = self.mesh.solve_poisson(b, walls)
         E = self.mesh.node_e(phi, walls)
-        self.phi, self.last_rho, self.last_node_e = phi, rho, E
+        self.phi, self.last_rho, self.last_node_e, self.last_walls = phi, rho, E, walls
         return rho, phi, E
+
+    # -- §3.1 / §4.3 adaptation and particle management (oracle/adapt.py) ----------------
+    def adapt(self, mesh=True, particles=True):
+        from .adapt import adapt_mesh, split_merge
+        out = {}
+        if mesh:
+            out["mesh"] = adapt_mesh(self)
+        if particles:
+            out["particles"] = split_merge(self)
+        return out
 
     def push_params(self, s):
         c = self.cfg

@@ -57,6 +57,7 @@ struct Level {
     int32_t *col = nullptr;                // ELL off-diagonal columns [kEll * n], -1 = empty
     float *val = nullptr;                  // ELL off-diagonal values (FP32)
     float *dinv = nullptr;                 // 1 / diagonal (FP32)
+    uint8_t *color = nullptr;              // red-black colour of the cell on its own scale
     double *val64 = nullptr, *diag64 = nullptr;  // finest level only (FP64 residual)
     double *bcw = nullptr;                 // finest level: Dirichlet coefficients [4 * n]
     float *x = nullptr, *b = nullptr, *t = nullptr;  // FP32 work vectors
@@ -90,6 +91,8 @@ struct Instance {
     uint32_t *morton = nullptr;  // per leaf
     std::vector<Level> lv;       // lv[0] = the leaves
     double *phi = nullptr, *bvec = nullptr, *res = nullptr, *charge = nullptr;
+    double *phi_prev = nullptr;  // previous solution: the next solve starts from 2 phi - phi_prev
+    int n_solves = 0;            // solves since the mesh was set (extrapolation needs two)
     double *red = nullptr;       // reduction scratch
     double *red_host = nullptr;  // pinned
     int32_t *cnt_host = nullptr; // pinned

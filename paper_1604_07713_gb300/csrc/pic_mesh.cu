@@ -143,9 +143,14 @@ __global__ void k_check_balance(int64_t n, LatView L, int32_t *__restrict__ err)
 //   Dirichlet wall: 2 toward the wall value; Neumann: nothing.
 __global__ void k_assemble(int64_t n, LatView L, int bcx, int bcy, int32_t *__restrict__ col,
                            float *__restrict__ val, float *__restrict__ dinv, double *__restrict__ val64,
-                           double *__restrict__ diag64, double *__restrict__ bcw, int32_t *__restrict__ err) {
+                           double *__restrict__ diag64, double *__restrict__ bcw, uint8_t *__restrict__ color,
+                           int32_t *__restrict__ err) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
+    {
+        const int sh = L.lmax - L.lev[c];
+        color[c] = (uint8_t)(((L.ix[c] >> sh) + (L.iy[c] >> sh)) & 1);
+    }
     double diag = 0.0;
     int k = 0;
     int32_t cc[kEll];
@@ -364,6 +369,7 @@ void assemble_level(pic_ctx *ctx, Instance &in, Level &g, bool finest, int32_t *
     g.col = dalloc<int32_t>(A, kEll * g.n);
     g.val = dalloc<float>(A, kEll * g.n);
     g.dinv = dalloc<float>(A, g.n);
+    g.color = dalloc<uint8_t>(A, g.n);
     if (finest) {
         g.val64 = dalloc<double>(A, kEll * g.n);
         g.diag64 = dalloc<double>(A, g.n);
@@ -373,7 +379,7 @@ void assemble_level(pic_ctx *ctx, Instance &in, Level &g, bool finest, int32_t *
     g.b = dalloc<float>(A, g.n);
     g.t = dalloc<float>(A, g.n);
     k_assemble<<<blocks_for(g.n), kT, 0, ctx->stream>>>(g.n, view_of(in, g), in.cfg.bc_x, in.cfg.bc_y, g.col,
-                                                        g.val, g.dinv, g.val64, g.diag64, g.bcw, d_err);
+                                                        g.val, g.dinv, g.val64, g.diag64, g.bcw, g.color, d_err);
     count_launch(ctx);
 }
 

@@ -153,6 +153,7 @@ template <typename R> struct PushArgs {
     R ng_dt, sig_el, sig_iz0, eps_th, half_m_over_qe, two_qe_over_m, two_m_over_mn;
     R vt_gas;       // neutral thermal speed sqrt(T qe / M)
     R red_a, red_m, red_mn;  // ions: M / (m + M), m / (m + M), M / (m + M)
+    R g_partner_max, g_pad;  // ions: bound on the partner speed (8.2 v_t), rounding margin
     uint32_t k0, k1, inst_word, step;
 };
 
@@ -282,7 +283,11 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
                                 vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
                             }
                         }
-                    } else {
+                    } else if (U0 < -m_expm1(-a.ng_dt * a.sig_el * a.g_pad *
+                                             (m_sqrt(vx * vx + vy * vy + vz * vz) + a.g_partner_max))) {
+                        // The Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms), so
+                        // U0 above the probability at |v| + that bound already means no collision;
+                        // below it, the partner is drawn and the exact test decides.
                         const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
                         R nn[3];
                         normals3<R>(r2, nn);
@@ -540,6 +545,8 @@ template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, i
     a.red_a = (R)(c.neutral_mass / mt);
     a.red_m = (R)(c.m[s] / mt);
     a.red_mn = (R)(c.neutral_mass / mt);
+    a.g_partner_max = (R)(8.2 * std::sqrt(c.gas_temperature_ev * c.qe / c.neutral_mass));
+    a.g_pad = (R)1.001;
     a.k0 = (uint32_t)(c.seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(c.seed >> 32);
     a.inst_word = (uint32_t)c.instance << 24;

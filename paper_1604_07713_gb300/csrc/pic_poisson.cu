@@ -1,9 +1,11 @@
 // Poisson solve on the composite leaf mesh (§3: multigrid Poisson solver with the potential
 // at cell centres).  Mixed precision: the residual b - A phi, its norm and the correction
 // phi += e are FP64 (iterative refinement); each correction e comes from one FP32
-// geometric-multigrid V-cycle over the tree-clamped and root-coarsened levels, with damped
-// Jacobi smoothing, summed restriction and piecewise-constant prolongation; the coarsest
-// level is solved by a one-block conjugate-gradient iteration.
+// geometric-multigrid V-cycle over the tree-clamped and root-coarsened levels, with two
+// red-black Gauss-Seidel sweeps before and after the coarse correction, summed restriction
+// and piecewise-constant prolongation; the coarsest level is solved by conjugate gradients.
+// Levels of at most 8192 cells live in one block's shared memory; when every level does, the
+// whole solve (FP64 residual, V-cycles, convergence test) is a single launch.
 #include <algorithm>
 #include <cmath>
 
@@ -14,9 +16,9 @@ namespace gbpic {
 namespace {
 constexpr int kT = 256;
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs: fixed so that the FP64 sums are deterministic
-constexpr float kOmega = 0.8f;
-constexpr int kNu = 3;
-constexpr double kCoarseTol2 = 1e-10;  // coarsest solve: ||r|| <= 1e-5 ||b|| (FP32 reachable)
+constexpr int kNu = 2;          // red-black Gauss-Seidel sweeps before and after the coarse correction
+constexpr double kCoarseTol2 = 1e-10;  // coarsest solve (multi-block path): ||r|| <= 1e-5 ||b||
+constexpr float kSmCoarseTol2 = 1e-6f; // coarsest solve inside a V-cycle in shared memory: 1e-3
 inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -99,25 +101,43 @@ __global__ void k_project(int64_t n, const uint8_t *__restrict__ lev, int lmax, 
     v[i] -= mode == 0 ? k * s * s : k;
 }
 
+// Initial guess of a solve: phi <- 2 phi - phi_prev (linear extrapolation in time of the last
+// two solutions), phi_prev <- phi.  With only one earlier solve: phi_prev <- phi.
+__global__ void k_extrapolate(int64_t n, double *__restrict__ phi, double *__restrict__ prev, int both) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p = phi[i];
+    if (both) phi[i] = 2.0 * p - prev[i];
+    prev[i] = p;
+}
+
 __global__ void k_add_correction(int64_t n, const float *__restrict__ e, double *__restrict__ phi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) phi[i] += (double)e[i];
 }
 
-// Damped Jacobi: t = (1 - w) x + w D^-1 (b - offdiag x).  first: x == 0.
-__global__ void k_jacobi(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
-                         const float *__restrict__ dinv, const float *__restrict__ b, const float *__restrict__ x,
-                         float *__restrict__ t, int first) {
+// One colour of a red-black Gauss-Seidel sweep, written out of place so that the result does
+// not depend on thread order (cells of the same colour can touch on a non-uniform mesh):
+// colour-c cells get D^-1 (b - offdiag x_in), others copy x_in.  zero_in: x_in is zero.
+__global__ void k_rbgs_half(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
+                            const float *__restrict__ dinv, const uint8_t *__restrict__ color, int c,
+                            const float *__restrict__ b, const float *__restrict__ xin, float *__restrict__ xout,
+                            int zero_in) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (first) { t[i] = kOmega * dinv[i] * b[i]; return; }
-    float off = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kEll; ++j) {
-        const int32_t c = col[(int64_t)j * n + i];
-        if (c >= 0) off = fmaf(val[(int64_t)j * n + i], x[c], off);
+    if (color[i] != c) {
+        xout[i] = zero_in ? 0.0f : xin[i];
+        return;
     }
-    t[i] = (1.0f - kOmega) * x[i] + kOmega * dinv[i] * (b[i] - off);
+    float off = 0.0f;
+    if (!zero_in) {
+#pragma unroll
+        for (int j = 0; j < kEll; ++j) {
+            const int32_t cc = col[(int64_t)j * n + i];
+            if (cc >= 0) off = fmaf(val[(int64_t)j * n + i], xin[cc], off);
+        }
+    }
+    xout[i] = dinv[i] * (b[i] - off);
 }
 
 // Coarse right-hand side: summed residuals of the children; zero coarse iterate.
@@ -239,37 +259,130 @@ struct SmallLevel {
     int32_t n;
     const int32_t *col;
     const float *val, *dinv;
+    const uint8_t *color;
     const int32_t *child4;  // children (in the finer level) of this level's cells
     const int32_t *parent;  // this level's cells -> cells of the next coarser level
     int32_t off;            // smem offset (floats) of x; b follows at off + n
+    // A level of root boxes only (no refinement) is a row-major nx x ny grid whose operator
+    // is the 5-point stencil; it is applied from the cell index, without the ELL arrays.
+    int32_t uniform, nx, ny;
+    uint32_t nx_magic;   // floor(i / nx) == __umulhi(i, nx_magic) for every cell index i < n
+    uint32_t nxh_magic;  // the same for nx / 2 (uniform levels with even nx)
 };
 struct SmallDesc {
     int nlev;  // levels g0 .. g0 + nlev - 1 live in shared memory
+    int bcx, bcy;
     SmallLevel lv[kMaxSmallLevels];
     int32_t off_cg;  // smem offset of the coarsest CG vectors r, p, q (3 n)
     int32_t smem_floats;
 };
 
-__device__ void sm_jacobi(const SmallLevel &L, float *x, const float *b, bool first) {
-    float t[kSmallN / 1024];
-    int k = 0;
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x, ++k) {
-        if (first) {
-            t[k] = kOmega * L.dinv[i] * b[i];
-        } else {
-            float off = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kEll; ++j) {
-                const int32_t c = L.col[(int64_t)j * L.n + i];
-                if (c >= 0) off = fmaf(L.val[(int64_t)j * L.n + i], x[c], off);
-            }
-            t[k] = (1.0f - kOmega) * x[i] + kOmega * L.dinv[i] * (b[i] - off);
-        }
+// Neighbour sum s and diagonal d of row i, so that (A x)_i = d x_i - s.  Uniform levels:
+// face conductance 1 to each neighbour, 2 to a Dirichlet wall, none at a Neumann wall.
+template <typename T>
+__device__ __forceinline__ T uni_row(int nx, int ny, uint32_t magic, int bcx, int bcy, const T *x, int i, T &d) {
+    const int iy = (int)__umulhi((uint32_t)i, magic), ix = i - iy * nx;
+    T s = 0, dd = 0;
+    if (ix > 0) { s += x[i - 1]; dd += 1; }
+    else if (bcx == PIC_BC_PERIODIC) { s += x[i + nx - 1]; dd += 1; }
+    else if (bcx == PIC_BC_DIRICHLET) dd += 2;
+    if (ix < nx - 1) { s += x[i + 1]; dd += 1; }
+    else if (bcx == PIC_BC_PERIODIC) { s += x[i - nx + 1]; dd += 1; }
+    else if (bcx == PIC_BC_DIRICHLET) dd += 2;
+    if (iy > 0) { s += x[i - nx]; dd += 1; }
+    else if (bcy == PIC_BC_PERIODIC) { s += x[i + (ny - 1) * nx]; dd += 1; }
+    else if (bcy == PIC_BC_DIRICHLET) dd += 2;
+    if (iy < ny - 1) { s += x[i + nx]; dd += 1; }
+    else if (bcy == PIC_BC_PERIODIC) { s += x[i - (ny - 1) * nx]; dd += 1; }
+    else if (bcy == PIC_BC_DIRICHLET) dd += 2;
+    d = dd;
+    return s;
+}
+
+__device__ __forceinline__ float sm_row(const SmallDesc &D, const SmallLevel &L, const float *x, int i, float &d,
+                                        float &dinv) {
+    if (L.uniform) {
+        const float s = uni_row<float>(L.nx, L.ny, L.nx_magic, D.bcx, D.bcy, x, i, d);
+        dinv = __frcp_rn(d);
+        return s;
     }
-    __syncthreads();
-    k = 0;
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x, ++k) x[i] = t[k];
-    __syncthreads();
+    float off = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kEll; ++j) {
+        const int32_t c = L.col[(int64_t)j * L.n + i];
+        if (c >= 0) off = fmaf(L.val[(int64_t)j * L.n + i], x[c], off);
+    }
+    dinv = L.dinv[i];
+    d = __frcp_rn(dinv);
+    return -off;
+}
+__device__ __forceinline__ float sm_row(const SmallDesc &D, const SmallLevel &L, const float *x, int i, float &d) {
+    float dinv;
+    return sm_row(D, L, x, i, d, dinv);
+}
+
+__device__ __forceinline__ int sm_color(const SmallLevel &L, int i) {
+    if (!L.uniform) return L.color[i];
+    const int iy = (int)__umulhi((uint32_t)i, L.nx_magic);
+    return (i - iy * L.nx + iy) & 1;
+}
+
+// Red-black Gauss-Seidel sweep in shared memory; each colour's new values are computed from
+// the current vector before any is written (deterministic on non-uniform meshes).  The block
+// has 1024 threads; thread t owns cells t + 1024 k, k < 8, so the new values stay in registers.
+constexpr int kPerThread = kSmallN / 1024;
+__device__ void sm_smooth(const SmallDesc &D, const SmallLevel &L, float *x, const float *b, bool first) {
+    if (first) {
+        for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] = 0.0f;
+        __syncthreads();
+    }
+    if (L.uniform && (L.nx & 1) == 0) {
+        // colour c of an even-width grid: in row iy the cells ix = 2m + ((c + iy) & 1)
+        const int half = L.n >> 1, nxh = L.nx >> 1;
+        for (int c = 0; c < 2; ++c) {
+            float t[kPerThread / 2];
+            int cell[kPerThread / 2];
+#pragma unroll
+            for (int k = 0; k < kPerThread / 2; ++k) {
+                const int j = threadIdx.x + 1024 * k;
+                cell[k] = -1;
+                if (j < half) {
+                    const int iy = (int)__umulhi((uint32_t)j, L.nxh_magic), m = j - iy * nxh;
+                    const int i = iy * L.nx + 2 * m + ((c + iy) & 1);
+                    float d, dinv;
+                    const float sn = sm_row(D, L, x, i, d, dinv);
+                    t[k] = (b[i] + sn) * dinv;
+                    cell[k] = i;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPerThread / 2; ++k)
+                if (cell[k] >= 0) x[cell[k]] = t[k];
+            __syncthreads();
+        }
+        return;
+    }
+    for (int c = 0; c < 2; ++c) {
+        float t[kPerThread];
+        bool mine[kPerThread];
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int i = threadIdx.x + 1024 * k;
+            mine[k] = i < L.n && sm_color(L, i) == c;
+            t[k] = 0.0f;
+            if (mine[k]) {
+                float d, dinv;
+                const float sn = sm_row(D, L, x, i, d, dinv);
+                t[k] = (b[i] + sn) * dinv;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k)
+            if (mine[k]) x[threadIdx.x + 1024 * k] = t[k];
+        __syncthreads();
+    }
 }
 
 __device__ double sm_block_sum(double v, double *red) {
@@ -289,162 +402,138 @@ __device__ double sm_block_sum(double v, double *red) {
     return out;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+
+__device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
 }
+__device__ float sm_block_sumf(float v, float *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sumf(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        red[32] = s;
+    }
+    __syncthreads();
+    const float out = red[32];
+    __syncthreads();
+    return out;
+}
 
-// Coarsest level: Jacobi-preconditioned CG in shared memory (one uniform level: symmetric).
-// Up to 256 cells it runs on the first warp alone (shuffle reductions, no block barriers).
-__device__ void sm_coarse_cg(const SmallLevel &L, float *x, const float *b, float *r, float *p, float *q,
-                             bool singular, double *red) {
+// Coarsest level: Jacobi-preconditioned CG in shared memory (one uniform level: symmetric),
+// all in FP32 (GB300's FP64 rate is a small fraction of FP32), to 1e-3 relative residual,
+// which is all a coarse-grid correction needs.  Up to 256 cells it runs on the first warp.
+__device__ void sm_coarse_cg(const SmallDesc &D, const SmallLevel &L, float *x, const float *b, float *r, float *p,
+                             float *q, bool singular, float *red) {
     const int n = L.n;
     const int maxit = min(2 * n + 10, 500);
-    if (n <= 256) {
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            double mb = 0.0;
-            if (singular) {
-                for (int i = lane; i < n; i += 32) mb += b[i];
-                mb = warp_sum(mb) / (double)n;
-            }
-            double rz = 0.0, bb = 0.0;
-            for (int i = lane; i < n; i += 32) {
-                const float ri = b[i] - (float)mb;
-                x[i] = 0.0f;
-                r[i] = ri;
-                const float zi = L.dinv[i] * ri;
-                p[i] = zi;
-                rz += (double)ri * zi;
-                bb += (double)ri * ri;
-            }
-            rz = warp_sum(rz);
-            bb = warp_sum(bb);
-            __syncwarp();
-            if (bb > 0.0) {
-                for (int it = 0; it < maxit; ++it) {
-                    double pq = 0.0;
-                    for (int i = lane; i < n; i += 32) {
-                        float ax = p[i] / L.dinv[i];
-                        for (int j = 0; j < kEll; ++j) {
-                            const int32_t c = L.col[(int64_t)j * n + i];
-                            if (c >= 0) ax = fmaf(L.val[(int64_t)j * n + i], p[c], ax);
-                        }
-                        q[i] = ax;
-                        pq += (double)p[i] * ax;
-                    }
-                    pq = warp_sum(pq);
-                    if (pq <= 0.0) break;
-                    const float alpha = (float)(rz / pq);
-                    double rr = 0.0, rz2 = 0.0;
-                    for (int i = lane; i < n; i += 32) {
-                        x[i] += alpha * p[i];
-                        const float ri = r[i] - alpha * q[i];
-                        r[i] = ri;
-                        rr += (double)ri * ri;
-                        rz2 += (double)ri * L.dinv[i] * ri;
-                    }
-                    rr = warp_sum(rr);
-                    rz2 = warp_sum(rz2);
-                    if (rr <= kCoarseTol2 * bb) break;
-                    const float beta = (float)(rz2 / rz);
-                    rz = rz2;
-                    __syncwarp();
-                    for (int i = lane; i < n; i += 32) p[i] = L.dinv[i] * r[i] + beta * p[i];
-                    __syncwarp();
-                }
-            }
-            if (singular) {
-                double mx = 0.0;
-                for (int i = lane; i < n; i += 32) mx += x[i];
-                mx = warp_sum(mx) / (double)n;
-                for (int i = lane; i < n; i += 32) x[i] -= (float)mx;
-            }
-        }
+    const bool warp_only = n <= 256;
+    if (warp_only && threadIdx.x >= 32) {
         __syncthreads();
         return;
     }
-    double mb = 0.0;
+    const int stride = warp_only ? 32 : blockDim.x;
+    auto sum = [&](float v) -> float { return warp_only ? warp_sumf(v) : sm_block_sumf(v, red); };
+    auto sync = [&]() { if (warp_only) __syncwarp(); else __syncthreads(); };
+    float mb = 0.0f;
     if (singular) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) mb += b[i];
-        mb = sm_block_sum(mb, red) / (double)n;
+        for (int i = threadIdx.x; i < n; i += stride) mb += b[i];
+        mb = sum(mb) / (float)n;
     }
-    double rz = 0.0, bb = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float ri = b[i] - (float)mb;
+    float rz = 0.0f, bb = 0.0f;
+    for (int i = threadIdx.x; i < n; i += stride) {
+        float d, dinv;
+        sm_row(D, L, b, i, d, dinv);  // diagonal only
+        const float ri = b[i] - mb;
         x[i] = 0.0f;
         r[i] = ri;
-        const float zi = L.dinv[i] * ri;
+        const float zi = ri * dinv;
         p[i] = zi;
-        rz += (double)ri * zi;
-        bb += (double)ri * ri;
+        rz += ri * zi;
+        bb += ri * ri;
     }
-    rz = sm_block_sum(rz, red);
-    bb = sm_block_sum(bb, red);
-    if (bb > 0.0) {
+    rz = sum(rz);
+    bb = sum(bb);
+    sync();
+    if (bb > 0.0f) {
         for (int it = 0; it < maxit; ++it) {
-            double pq = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                float ax = p[i] / L.dinv[i];
-                for (int j = 0; j < kEll; ++j) {
-                    const int32_t c = L.col[(int64_t)j * n + i];
-                    if (c >= 0) ax = fmaf(L.val[(int64_t)j * n + i], p[c], ax);
-                }
+            float pq = 0.0f;
+            for (int i = threadIdx.x; i < n; i += stride) {
+                float d;
+                const float sn = sm_row(D, L, p, i, d);
+                const float ax = d * p[i] - sn;
                 q[i] = ax;
-                pq += (double)p[i] * ax;
+                pq += p[i] * ax;
             }
-            pq = sm_block_sum(pq, red);
-            if (pq <= 0.0) break;
-            const float alpha = (float)(rz / pq);
-            double rr = 0.0, rz2 = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            pq = sum(pq);
+            if (!(pq > 0.0f)) break;
+            const float alpha = rz / pq;
+            float rr = 0.0f, rz2 = 0.0f;
+            for (int i = threadIdx.x; i < n; i += stride) {
+                float d, dinv;
+                sm_row(D, L, p, i, d, dinv);
                 x[i] += alpha * p[i];
                 const float ri = r[i] - alpha * q[i];
                 r[i] = ri;
-                rr += (double)ri * ri;
-                rz2 += (double)ri * L.dinv[i] * ri;
+                rr += ri * ri;
+                rz2 += ri * ri * dinv;
             }
-            rr = sm_block_sum(rr, red);
-            rz2 = sm_block_sum(rz2, red);
-            if (rr <= kCoarseTol2 * bb) break;
-            const float beta = (float)(rz2 / rz);
+            rr = sum(rr);
+            rz2 = sum(rz2);
+            if (rr <= kSmCoarseTol2 * bb) break;
+            const float beta = rz2 / rz;
             rz = rz2;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = L.dinv[i] * r[i] + beta * p[i];
-            __syncthreads();
+            sync();
+            for (int i = threadIdx.x; i < n; i += stride) {
+                float d, dinv;
+                sm_row(D, L, p, i, d, dinv);
+                p[i] = r[i] * dinv + beta * p[i];
+            }
+            sync();
         }
     }
     if (singular) {
-        double mx = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) mx += x[i];
-        mx = sm_block_sum(mx, red) / (double)n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= (float)mx;
+        float mx = 0.0f;
+        for (int i = threadIdx.x; i < n; i += stride) mx += x[i];
+        mx = sum(mx) / (float)n;
+        for (int i = threadIdx.x; i < n; i += stride) x[i] -= mx;
     }
     __syncthreads();
 }
 
 // V-cycle over the shared-memory levels; b of the first level must be in place, x of the
 // first level holds the correction on return.
-__device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, double *red) {
+__device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *red) {
     const int last = D.nlev - 1;
     for (int g = 0; g < last; ++g) {
         const SmallLevel &L = D.lv[g], &Cc = D.lv[g + 1];
         float *x = sm + L.off, *b = x + L.n;
-        for (int k = 0; k < kNu; ++k) sm_jacobi(L, x, b, k == 0);
+        for (int k = 0; k < kNu; ++k) sm_smooth(D, L, x, b, k == 0);
         float *bc = sm + Cc.off + Cc.n;
         for (int p = threadIdx.x; p < Cc.n; p += blockDim.x) {
             float s = 0.0f;
+            if (L.uniform && Cc.uniform) {
+                const int py = (int)__umulhi((uint32_t)p, Cc.nx_magic), px = p - py * Cc.nx;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t i = Cc.child4[4 * p + k];
-                if (i < 0) continue;
-                float ax = x[i] / L.dinv[i];
-#pragma unroll
-                for (int j = 0; j < kEll; ++j) {
-                    const int32_t c = L.col[(int64_t)j * L.n + i];
-                    if (c >= 0) ax = fmaf(L.val[(int64_t)j * L.n + i], x[c], ax);
+                for (int k = 0; k < 4; ++k) {
+                    const int i = (2 * py + (k >> 1)) * L.nx + 2 * px + (k & 1);
+                    float d;
+                    const float sn = sm_row(D, L, x, i, d);
+                    s += b[i] - (d * x[i] - sn);
                 }
-                s += b[i] - ax;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t i = Cc.child4[4 * p + k];
+                    if (i < 0) continue;
+                    float d;
+                    const float sn = sm_row(D, L, x, i, d);
+                    s += b[i] - (d * x[i] - sn);
+                }
             }
             bc[p] = s;
         }
@@ -454,39 +543,47 @@ __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, double *
         const SmallLevel &L = D.lv[last];
         float *x = sm + L.off, *b = x + L.n;
         float *r = sm + D.off_cg;
-        sm_coarse_cg(L, x, b, r, r + L.n, r + 2 * L.n, singular, red);
+        sm_coarse_cg(D, L, x, b, r, r + L.n, r + 2 * L.n, singular, red);
     }
     for (int g = last - 1; g >= 0; --g) {
         const SmallLevel &L = D.lv[g], &Cc = D.lv[g + 1];
         float *x = sm + L.off, *b = x + L.n;
         const float *xc = sm + Cc.off;
-        for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += xc[L.parent[i]];
+        if (L.uniform && Cc.uniform) {
+            for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+                const int iy = (int)__umulhi((uint32_t)i, L.nx_magic), ix = i - iy * L.nx;
+                x[i] += xc[(iy >> 1) * Cc.nx + (ix >> 1)];
+            }
+        } else {
+            for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += xc[L.parent[i]];
+        }
         __syncthreads();
-        for (int k = 0; k < kNu; ++k) sm_jacobi(L, x, b, false);
+        for (int k = 0; k < kNu; ++k) sm_smooth(D, L, x, b, false);
     }
 }
 
 // Tail of a V-cycle started by the multi-block levels: b from global, x back to global.
-__global__ void __launch_bounds__(1024) k_tail_vcycle(SmallDesc D, const float *__restrict__ gb,
+__global__ void __launch_bounds__(1024, 1) k_tail_vcycle(SmallDesc D, const float *__restrict__ gb,
                                                        float *__restrict__ gx, int singular) {
     extern __shared__ float sm[];
-    __shared__ double red[33];
+    __shared__ float redf[33];
     const SmallLevel &L = D.lv[0];
     for (int i = threadIdx.x; i < L.n; i += blockDim.x) sm[L.off + L.n + i] = gb[i];
     __syncthreads();
-    sm_vcycle(D, sm, singular != 0, red);
+    sm_vcycle(D, sm, singular != 0, redf);
     for (int i = threadIdx.x; i < L.n; i += blockDim.x) gx[i] = sm[L.off + i];
 }
 
 // Whole solve for a mesh whose every level fits: FP64 residual and correction, FP32 V-cycles
 // in shared memory, convergence test on the device.  stats: [cycles, rel. residual, max rel.]
-__global__ void __launch_bounds__(1024) k_small_solve(SmallDesc D, const double *__restrict__ diag64,
+__global__ void __launch_bounds__(1024, 1) k_small_solve(SmallDesc D, const double *__restrict__ diag64,
                                                        const double *__restrict__ val64, double *__restrict__ phi,
                                                        double *__restrict__ bvec, const uint8_t *__restrict__ lev,
                                                        int lmax, int singular, double tol, int maxc,
                                                        double *__restrict__ stats) {
     extern __shared__ float sm[];
     __shared__ double red[33];
+    __shared__ float redf[33];
     const SmallLevel &L = D.lv[0];
     const int n = L.n;
     if (singular) {  // right-hand side compatibility: remove an area-proportional share
@@ -513,11 +610,18 @@ __global__ void __launch_bounds__(1024) k_small_solve(SmallDesc D, const double 
     for (;;) {
         double rr = 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double ax = diag64[i] * phi[i];
+            double ax;
+            if (L.uniform) {
+                double d;
+                const double sn = uni_row<double>(L.nx, L.ny, L.nx_magic, D.bcx, D.bcy, phi, i, d);
+                ax = d * phi[i] - sn;
+            } else {
+                ax = diag64[i] * phi[i];
 #pragma unroll
-            for (int j = 0; j < kEll; ++j) {
-                const int32_t c = L.col[(int64_t)j * n + i];
-                if (c >= 0) ax += val64[(int64_t)j * n + i] * phi[c];
+                for (int j = 0; j < kEll; ++j) {
+                    const int32_t c = L.col[(int64_t)j * n + i];
+                    if (c >= 0) ax += val64[(int64_t)j * n + i] * phi[c];
+                }
             }
             const double ri = bvec[i] - ax;
             b0[i] = (float)ri;
@@ -526,7 +630,7 @@ __global__ void __launch_bounds__(1024) k_small_solve(SmallDesc D, const double 
         rr = sm_block_sum(rr, red);
         rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         if (rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
-        sm_vcycle(D, sm, singular != 0, red);
+        sm_vcycle(D, sm, singular != 0, redf);
         for (int i = threadIdx.x; i < n; i += blockDim.x) phi[i] += (double)x0[i];
         __syncthreads();
         if (singular) {
@@ -567,12 +671,25 @@ int small_from(const Instance &in) {
 SmallDesc small_desc(const Instance &in, int g0) {
     SmallDesc D{};
     D.nlev = (int)in.lv.size() - g0;
+    D.bcx = in.cfg.bc_x;
+    D.bcy = in.cfg.bc_y;
     int32_t off = 0;
     for (int k = 0; k < D.nlev; ++k) {
         const Level &L = in.lv[g0 + k];
         SmallLevel &S = D.lv[k];
-        S.n = (int32_t)L.n; S.col = L.col; S.val = L.val; S.dinv = L.dinv;
+        S.n = (int32_t)L.n; S.col = L.col; S.val = L.val; S.dinv = L.dinv; S.color = L.color;
         S.child4 = L.child4; S.parent = L.parent; S.off = off;
+        S.uniform = L.lmax == 0 ? 1 : 0;
+        S.nx = L.nx0;
+        S.ny = L.ny0;
+        // multiply-high reciprocal: floor(i * m / 2^32) == floor(i / nx) for the i < n used here
+        S.nx_magic = 0xFFFFFFFFu / (uint32_t)L.nx0 + 1u;
+        const uint32_t nxh = std::max(1, L.nx0 / 2);
+        S.nxh_magic = 0xFFFFFFFFu / nxh + 1u;
+        for (int64_t i = 0; i < L.n; ++i)
+            if ((int64_t)(((uint64_t)i * S.nx_magic) >> 32) != i / L.nx0 ||
+                (int64_t)(((uint64_t)i * S.nxh_magic) >> 32) != i / (int64_t)nxh)
+                fail(PIC_EINVAL, "index division check failed");
         off += 2 * (int32_t)L.n;
     }
     D.off_cg = off;
@@ -604,19 +721,21 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     Level &C = in.lv[g + 1];
     const unsigned nb = blocks_for(L.n);
     // pre-smoothing (x starts at zero)
-    for (int k = 0; k < kNu; ++k) {
-        k_jacobi<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, k == 0);
-        std::swap(L.x, L.t);
-    }
+    for (int k = 0; k < kNu; ++k)
+        for (int c = 0; c < 2; ++c) {
+            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, k == 0 && c == 0);
+            std::swap(L.x, L.t);
+        }
     k_restrict_residual<<<blocks_for(C.n), kT, 0, s>>>(C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
-    count_launch(ctx, kNu + 1);
+    count_launch(ctx, 2 * kNu + 1);
     vcycle(ctx, in, g + 1, singular);
     k_prolong<<<nb, kT, 0, s>>>(L.n, L.parent, C.x, L.x);
-    for (int k = 0; k < kNu; ++k) {
-        k_jacobi<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, 0);
-        std::swap(L.x, L.t);
-    }
-    count_launch(ctx, kNu + 1);
+    for (int k = 0; k < kNu; ++k)
+        for (int c = 0; c < 2; ++c) {
+            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
+            std::swap(L.x, L.t);
+        }
+    count_launch(ctx, 2 * kNu + 1);
 }
 }  // namespace
 
@@ -624,6 +743,8 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     DeviceArena &A = in.mesh_mem;
     const int64_t n = in.lv[0].n;
     in.phi = dalloc<double>(A, n);
+    in.phi_prev = dalloc<double>(A, n);
+    in.n_solves = 0;
     in.bvec = dalloc<double>(A, n);
     in.res = dalloc<double>(A, n);
     in.charge = dalloc<double>(A, n);
@@ -645,6 +766,11 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     cudaStream_t s = ctx->stream;
     const int64_t n = L.n;
     const bool singular = in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC;
+    if (in.n_solves >= 1) {
+        k_extrapolate<<<blocks_for(n), kT, 0, s>>>(n, in.phi, in.phi_prev, in.n_solves >= 2 ? 1 : 0);
+        count_launch(ctx);
+    }
+    ++in.n_solves;
     if (small_from(in) == 0) {
         const SmallDesc D = small_desc(in, 0);
         GB_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
