@@ -93,6 +93,7 @@ struct Instance {
     double *phi = nullptr, *bvec = nullptr, *res = nullptr, *charge = nullptr;
     double *phi_prev = nullptr;  // previous solution: the next solve starts from 2 phi - phi_prev
     int n_solves = 0;            // solves since the mesh was set (extrapolation needs two)
+    double last_walls[4] = {0, 0, 0, 0};  // wall potentials of the last solve
     double *red = nullptr;       // reduction scratch
     double *red_host = nullptr;  // pinned
     int32_t *cnt_host = nullptr; // pinned

@@ -761,7 +761,7 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
 
 // Solve A phi = bvec to ||r|| <= mg_rel_tol ||b||, warm-started from the current phi.
 void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
-    (void)walls;
+    for (int k = 0; k < 4; ++k) in.last_walls[k] = walls[k];
     Level &L = in.lv[0];
     cudaStream_t s = ctx->stream;
     const int64_t n = L.n;
