@@ -20,11 +20,9 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -34,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "ccp-512x16-ppc100-fp32"
 METRIC = "particle-steps/s"
+WORKLOADS = ("ccp", "streamer")
 
 
 def _dist():
@@ -42,18 +41,30 @@ def _dist():
     return ws, rank
 
 
-def _workload(seed):
+def _workload(seed, name="ccp", n_particles=50_000_000):
     from paper_1604_07713_gb300 import workloads as W
+    if name == "streamer":
+        return W.streamer_snapshot(n_particles=n_particles, seed=seed, precision=W.FP32)
     cfg, mesh, parts = W.ccp(seed=seed, precision=W.FP32)
     cfg["mg_rel_tol"] = 1e-8
     return cfg, mesh, parts
 
 
-def _config_json(ws):
-    return {"workload": WORKLOAD, "cells": "512x16 uniform quadtree leaves", "particles_per_species": 819200,
-            "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
-            "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
-            "poisson_rel_tol": 1e-8}
+def _config_json(ws, name="ccp", extra=None):
+    if name == "streamer":
+        d = {"workload": "streamer-amr-128x128-l4-fp32", "cells": "adaptive quadtree, 128x128 roots, up to 4 levels",
+             "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
+             "adapt": "pic_adapt (mesh + split/merge) every 10 steps inside the timed region",
+             "l2": "inputs larger than L2 (particle state >> 129 MB)", "parallelism": f"replicas x{ws}",
+             "poisson_rel_tol": 1e-8}
+    else:
+        d = {"workload": WORKLOAD, "cells": "512x16 uniform quadtree leaves", "particles_per_species": 819200,
+             "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
+             "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
+             "poisson_rel_tol": 1e-8}
+    if extra:
+        d.update(extra)
+    return d
 
 
 # ---------------------------------------------------------------------------------------
@@ -107,8 +118,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # oracle (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------------------
-def _oracle_sim(seed):
+ORACLE_STREAMER_PARTICLES = 200_000
+
+
+def _oracle_sim(seed, name="ccp"):
     import oracle as O
+    if name == "streamer":
+        cfg, mesh, parts = _workload(seed, "streamer", ORACLE_STREAMER_PARTICLES)
+        M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], mesh["lmax"], cfg["bc_x"], cfg["bc_y"])
+        sim = O.Sim(cfg, M)
+        for s in sorted(parts):
+            sim.load(s, **parts[s])
+        for _ in range(mesh["lmax"] + 1):  # refine the uniform roots onto the particles
+            sim.fields()
+            sim.adapt(mesh=True, particles=False)
+        sim.fields()
+        sim.adapt()
+        return sim
     cfg, mesh, parts = _workload(seed)
     M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, cfg["bc_x"], cfg["bc_y"])
     sim = O.Sim(cfg, M)
@@ -117,40 +143,47 @@ def _oracle_sim(seed):
     return sim
 
 
-def _oracle_rate(sim, steps):
+def _oracle_rate(sim, steps, adapt_every=0):
     tot, t = 0, 0.0
-    for _ in range(steps):
+    for k in range(steps):
         n = sum(sp.n for sp in sim.species)
         t0 = time.perf_counter()
         sim.step(1)
+        if adapt_every and (k + 1) % adapt_every == 0:
+            sim.adapt()
         t += time.perf_counter() - t0
         tot += n
     return tot / t, t
 
 
-def cpu_baseline(seed, steps=12):
-    sim = _oracle_sim(seed)
+def _sample_text(name, steps, t):
+    if name == "streamer":
+        return (f"{steps} steps (adaptation every 10) of the streamer workload at {ORACLE_STREAMER_PARTICLES:,} "
+                f"particles (the GPU runs 5e7) on a mesh the oracle adapted itself, FP64, single thread, {t:.1f} s")
+    return f"{steps} steps of the full workload (2 x 819,200 particles), FP64 oracle, single thread, {t:.1f} s"
+
+
+def cpu_baseline(seed, steps=12, name="ccp"):
+    sim = _oracle_sim(seed, name)
     sim.step(1)  # warm-up (imports, first solve)
-    rate, t = _oracle_rate(sim, steps)
-    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the full workload (2 x 819,200 particles), FP64 oracle, "
-                      f"single thread, {t:.1f} s"}
+    rate, t = _oracle_rate(sim, steps, 10 if name == "streamer" else 0)
+    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": _sample_text(name, steps, t)}
 
 
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return
-    sim = _oracle_sim(args.seed)
+    sim = _oracle_sim(args.seed, args.workload)
     for _ in range(args.warmup):
         sim.step(1)
-    rate, t = _oracle_rate(sim, args.steps)
+    rate, t = _oracle_rate(sim, args.steps, 10 if args.workload == "streamer" else 0)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config_json(1),
+            "data": "synthetic", "config": _config_json(1, args.workload),
             "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps of the full workload after {args.warmup} warm-up, single thread"},
+                             "sample": _sample_text(args.workload, args.steps, t)},
             "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -158,18 +191,22 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
-def _traffic_record():
-    """DRAM traffic per launch of the move kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path))
+def _csrc_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_07713_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         h.update(open(os.path.join(csrc, f), "rb").read())
-    if rec.get("csrc_sha256") != h.hexdigest():
+    return h.hexdigest()
+
+
+def _traffic_record(name):
+    """DRAM bytes per launch of the move kernel from the committed ncu summary, if that was
+    taken on the current kernel sources and this workload (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(name)
+    if not rec or rec.get("csrc_sha256") != _csrc_hash():
         return None
     return rec
 
@@ -185,21 +222,35 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     G.build()
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    name = args.workload
+    streamer = name == "streamer"
 
     stream = torch.cuda.Stream()
-    cfg, mesh, parts = _workload(args.seed + rank)
+    cfg, mesh, parts = _workload(args.seed + rank, name, args.particles)
     ctx = G.Context(cfg, stream_handle=stream.cuda_stream)
     ctx.set_mesh_dict(mesh)
     for s in sorted(parts):
         ctx.load(s, **parts[s])
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if streamer:  # refine the uniform roots onto the particles, then manage them (setup, untimed)
+        for _ in range(mesh["lmax"] + 1):
+            ctx.compute_fields(allow_notconv=True)
+            ctx.adapt(G.PIC_ADAPT_MESH)
+        ctx.compute_fields(allow_notconv=True)
+        ctx.adapt()
+    flush = None if streamer else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    adapt_every = cfg.get("adapt_every", 0) if streamer else 0
 
-    for _ in range(args.warmup):
+    def one_step(k):
         ctx.step(1)
+        if adapt_every and (k + 1) % adapt_every == 0:
+            ctx.adapt()
+
+    for k in range(args.warmup):
+        one_step(k)
     torch.cuda.synchronize()
 
     # timed region
@@ -212,21 +263,22 @@ def run_gpu(args):
     G.pic_set_timing(ctx.ctx, True)
     t_total = 0.0
     particle_steps = 0
-    mover_particles = 0
-    for _ in range(args.steps):
+    leaf_steps = 0
+    for k in range(args.steps):
         c = ctx.counts()
         n = c["n_e"] + c["n_i"]
         with torch.cuda.stream(stream):
-            flush.zero_()
+            if flush is not None:
+                flush.zero_()
             a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-        ctx.step(1)
+        one_step(args.warmup + k)
         with torch.cuda.stream(stream):
             b.record(stream)
         b.synchronize()
         t_total += a.elapsed_time(b) * 1e-3
         particle_steps += n
-        mover_particles += n
+        leaf_steps += c["n_leaves"]
     torch.cuda.synchronize()
     phases = G.pic_get_timing(ctx.ctx)
     G.pic_set_timing(ctx.ctx, False)
@@ -243,33 +295,39 @@ def run_gpu(args):
     else:
         particle_steps_all = float(particle_steps)
     value = particle_steps_all / t_max
+    final = ctx.counts()
 
-    # roofline of the move pass (k_push in move mode, both species): algorithmic bytes per
-    # particle = 28 B record read + 28 B record written; per leaf 32 B corner field + 8 B
-    # list offsets (old and new), summed over the steps' particles
-    nl = 512 * 16
+    # Roofline of the move pass (k_push in move mode, both species): algorithmic bytes = the
+    # 28 B record (u, v, vx, vy, vz, w, id) read and written once per particle, plus per leaf
+    # the 8 corner field values and two list offsets (old, new) of each species.
+    rs = 4
     move_ms, move_launches = phases["move"]
     move_s = move_ms * 1e-3
-    alg_bytes = 56.0 * mover_particles + args.steps * 2 * nl * (32 + 8)
+    alg_bytes = 2 * 7 * rs * particle_steps + leaf_steps * (8 * rs + 2 * 2 * 4)
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
-    tr = _traffic_record()
-    roofline = {"bound": "hbm", "kernel": "k_push<float> (move pass, both species)", "achieved": achieved,
+    tr = _traffic_record(name)
+    tot_ms = sum(v[0] for v in phases.values())
+    roofline = {"bound": "hbm", "kernel": "k_push<float> move pass (both species)", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": tr["move_bytes_per_step"] if tr else None,
-                "peak_source": f"{peak_src} hbm_gbs", "alg_bytes_per_particle": 56,
-                "launch_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in phases.values())), 4)
-                                 for k, v in phases.items() if v[1]}}
+                "traffic": tr["move_dram_bytes_per_step"] if tr else None,
+                "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                "alg_bytes_per_step": alg_bytes / args.steps,
+                "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items() if v[1]}}
+    extra = {"particles_mean": int(particle_steps / args.steps),
+             "particles_end": int(final["n_e"] + final["n_i"]), "leaves_end": int(final["n_leaves"]),
+             "poisson_cycles_last": int(final["mg_cycles"])}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config_json(ws), "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
-            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
+            "config": _config_json(ws, name, extra), "roofline": roofline, "clocks": clocks,
+            "gpu_launches": int(launches),
+            "phase_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]}}
 
     # end to end through the C ABI with host buffers: load (H2D) + one step + read phi (D2H)
     if not args.no_e2e:
         host = {s: {k: np.ascontiguousarray(v) for k, v in parts[s].items()} for s in parts}
         h2d = sum(v.nbytes for s in host for v in host[s].values())
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = 3 if streamer else max(3, min(args.steps, 10))
         t_e2e = 0.0
         n_e2e = 0
         for k in range(e2e_steps + 1):
@@ -285,9 +343,9 @@ def run_gpu(args):
                 n_e2e += sum(host[s]["x"].size for s in host)
         line["e2e"] = {"value": n_e2e / t_e2e, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(phi.nbytes)}
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.seed, steps=args.cpu_steps)
     ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.seed, steps=args.cpu_steps, name=name)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -301,6 +359,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbpic", choices=["gbpic", "reference"])
     ap.add_argument("--seed", type=int, default=160407713)
+    ap.add_argument("--workload", default="ccp", choices=WORKLOADS)
+    ap.add_argument("--particles", type=int, default=50_000_000, help="streamer workload: total particles")
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

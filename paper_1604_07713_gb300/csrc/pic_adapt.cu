@@ -464,7 +464,9 @@ int32_t read_i32(pic_ctx *ctx, const int32_t *d) {
 void species_relist(pic_ctx *ctx, Instance &in, int s, int64_t nl, const int32_t *new_start) {
     Species &sp = in.sp[s];
     DeviceArena &A = in.part_mem[s];
-    int32_t *olds[7] = {sp.start, sp.start_new, sp.stay, sp.inc, sp.fill, sp.spawn, sp.spawn_base};
+    void *olds[10] = {sp.start, sp.start_new, sp.stay, sp.inc, sp.fill, sp.spawn, sp.spawn_base,
+                      sp.stay_hi, sp.stay_lo, sp.wsum};
+    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
     sp.start = dalloc<int32_t>(A, nl + 1);
     sp.start_new = dalloc<int32_t>(A, nl + 1);
     sp.stay = dalloc<int32_t>(A, nl + 1);
@@ -472,10 +474,14 @@ void species_relist(pic_ctx *ctx, Instance &in, int s, int64_t nl, const int32_t
     sp.fill = dalloc<int32_t>(A, nl + 1);
     sp.spawn = dalloc<int32_t>(A, nl + 1);
     sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
+    sp.stay_hi = A.alloc((nl + 1) * rs + 64);
+    sp.stay_lo = A.alloc((nl + 1) * rs + 64);
+    sp.wsum = dalloc<double>(A, nl + 1);
+    sp.sums_valid = false;
     GB_CUDA(cudaMemsetAsync(sp.spawn_base, 0, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4, ctx->stream));
     GB_CUDA(cudaMemcpyAsync(sp.start, new_start, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
-    for (int32_t *p : olds) A.release(p);
+    for (void *p : olds) A.release(p);
 }
 
 template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n_old, int64_t n_new,
@@ -546,6 +552,7 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
         GB_CUDA(cudaMemcpyAsync(sp.start, nstart, (nl + 1) * 4, cudaMemcpyDeviceToDevice, st));
         sp.cur ^= 1;
         sp.n = sp.n_upper = tot[0];
+        sp.sums_valid = false;
     }
     GB_CUDA(cudaMemcpyAsync(in.d_next_id, &next_id, 8, cudaMemcpyHostToDevice, st));
     GB_CUDA(cudaStreamSynchronize(st));

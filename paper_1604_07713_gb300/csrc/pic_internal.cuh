@@ -78,6 +78,10 @@ struct Species {
     int32_t *start_new = nullptr;
     int32_t *stay = nullptr, *inc = nullptr, *fill = nullptr;  // [nleaf]
     int32_t *spawn = nullptr, *spawn_base = nullptr;           // [nleaf], [nleaf + 1]
+    // per-leaf weight sums left by the last cell-list update for the next deposit
+    void *stay_hi = nullptr, *stay_lo = nullptr;               // R [nleaf]
+    double *wsum = nullptr;                                     // [nleaf]
+    bool sums_valid = false;
 };
 
 struct Instance {

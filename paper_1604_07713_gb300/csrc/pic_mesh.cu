@@ -239,59 +239,62 @@ __global__ void k_root_coarsen(int nx, int ny, int32_t *__restrict__ parent, int
 }
 
 // ---- corner electric field ---------------------------------------------------------------
-struct FieldView {
+// Corner field from the cell potentials.  Differences of the FP64 potential are taken in
+// FP64; the scaling by 1/h (exact powers of two times 1/h_finest) and the averaging run in T
+// (float in FP32 mode, double in FP64 mode), with no divisions.
+template <typename T> struct FieldView {
     LatView L;
     const double *phi;
-    double hf;  // lattice cell side
+    T inv_hf;  // 1 / (lattice cell side)
     int bcx, bcy;
     double wall[4];
 
-    __device__ double side_h(int32_t c) const { return (double)L.side(c) * hf; }
+    __device__ __forceinline__ T inv_h(int32_t c) const { return inv_hf * ((T)1 / (T)L.side(c)); }
 
     // d phi / dx across the vertical lattice line x = I at lattice row J (operator's face rule)
-    __device__ double grad_x(int32_t I, int32_t J) const {
+    __device__ T grad_x(int32_t I, int32_t J) const {
         const int32_t A = L.at(I - 1, J), B = L.at(I, J);
-        if (A < 0 && B < 0) return 0.0;
-        if (A < 0) return bcx == PIC_BC_DIRICHLET ? (phi[B] - wall[0]) / (0.5 * side_h(B)) : 0.0;
-        if (B < 0) return bcx == PIC_BC_DIRICHLET ? (wall[1] - phi[A]) / (0.5 * side_h(A)) : 0.0;
+        if (A < 0 && B < 0) return (T)0;
+        if (A < 0) return bcx == PIC_BC_DIRICHLET ? (T)(phi[B] - wall[0]) * ((T)2 * inv_h(B)) : (T)0;
+        if (B < 0) return bcx == PIC_BC_DIRICHLET ? (T)(wall[1] - phi[A]) * ((T)2 * inv_h(A)) : (T)0;
         const int32_t sA = L.side(A), sB = L.side(B);
-        if (sA == sB) return (phi[B] - phi[A]) / side_h(A);
+        if (sA == sB) return (T)(phi[B] - phi[A]) * inv_h(A);
         if (sA > sB) {
             const int32_t c1 = L.at(L.ix[A] + sA, L.iy[A]), c2 = L.at(L.ix[A] + sA, L.iy[A] + sA - 1);
-            return (0.5 * (phi[c1] + phi[c2]) - phi[A]) / (0.75 * side_h(A));
+            return (T)(0.5 * (phi[c1] + phi[c2]) - phi[A]) * (inv_h(A) * (T)(4.0 / 3.0));
         }
         const int32_t c1 = L.at(L.ix[B] - 1, L.iy[B]), c2 = L.at(L.ix[B] - 1, L.iy[B] + sB - 1);
-        return (phi[B] - 0.5 * (phi[c1] + phi[c2])) / (0.75 * side_h(B));
+        return (T)(phi[B] - 0.5 * (phi[c1] + phi[c2])) * (inv_h(B) * (T)(4.0 / 3.0));
     }
-    __device__ double grad_y(int32_t I, int32_t J) const {
+    __device__ T grad_y(int32_t I, int32_t J) const {
         const int32_t A = L.at(I, J - 1), B = L.at(I, J);
-        if (A < 0 && B < 0) return 0.0;
-        if (A < 0) return bcy == PIC_BC_DIRICHLET ? (phi[B] - wall[2]) / (0.5 * side_h(B)) : 0.0;
-        if (B < 0) return bcy == PIC_BC_DIRICHLET ? (wall[3] - phi[A]) / (0.5 * side_h(A)) : 0.0;
+        if (A < 0 && B < 0) return (T)0;
+        if (A < 0) return bcy == PIC_BC_DIRICHLET ? (T)(phi[B] - wall[2]) * ((T)2 * inv_h(B)) : (T)0;
+        if (B < 0) return bcy == PIC_BC_DIRICHLET ? (T)(wall[3] - phi[A]) * ((T)2 * inv_h(A)) : (T)0;
         const int32_t sA = L.side(A), sB = L.side(B);
-        if (sA == sB) return (phi[B] - phi[A]) / side_h(A);
+        if (sA == sB) return (T)(phi[B] - phi[A]) * inv_h(A);
         if (sA > sB) {
             const int32_t c1 = L.at(L.ix[A], L.iy[A] + sA), c2 = L.at(L.ix[A] + sA - 1, L.iy[A] + sA);
-            return (0.5 * (phi[c1] + phi[c2]) - phi[A]) / (0.75 * side_h(A));
+            return (T)(0.5 * (phi[c1] + phi[c2]) - phi[A]) * (inv_h(A) * (T)(4.0 / 3.0));
         }
         const int32_t c1 = L.at(L.ix[B], L.iy[B] - 1), c2 = L.at(L.ix[B] + sB - 1, L.iy[B] - 1);
-        return (phi[B] - 0.5 * (phi[c1] + phi[c2])) / (0.75 * side_h(B));
+        return (T)(phi[B] - 0.5 * (phi[c1] + phi[c2])) * (inv_h(B) * (T)(4.0 / 3.0));
     }
     __device__ bool in_x(int32_t I) const { return L.px || (I >= 0 && I < L.NX); }
     __device__ bool in_y(int32_t J) const { return L.py || (J >= 0 && J < L.NY); }
 
     // E at lattice node (I, J): regular nodes average the incident face gradients; a node
     // inside a coarser leaf's edge takes the mean of that edge's end nodes (recursively).
-    __device__ void node(int32_t I, int32_t J, double &ex, double &ey) const {
+    __device__ void node(int32_t I, int32_t J, T &ex, T &ey) const {
         int32_t sI[24], sJ[24];
-        double sw[24];
+        T sw[24];
         int top = 0;
-        sI[0] = I; sJ[0] = J; sw[0] = 1.0; top = 1;
-        ex = 0.0; ey = 0.0;
+        sI[0] = I; sJ[0] = J; sw[0] = (T)1; top = 1;
+        ex = (T)0; ey = (T)0;
         while (top > 0) {
             --top;
             const int32_t i = sI[top], j = sJ[top];
-            const double wt = sw[top];
+            const T wt = sw[top];
             const int32_t LL = L.at(i - 1, j - 1), LR = L.at(i, j - 1), UL = L.at(i - 1, j), UR = L.at(i, j);
             int32_t q = -1;
             bool horiz = false;
@@ -303,41 +306,41 @@ struct FieldView {
                 const int32_t s = L.side(q);
                 if (horiz) {
                     const int32_t off = (((i - L.ix[q]) % L.NX) + L.NX) % L.NX;
-                    sI[top] = i - off; sJ[top] = j; sw[top] = 0.5 * wt; ++top;
-                    sI[top] = i - off + s; sJ[top] = j; sw[top] = 0.5 * wt; ++top;
+                    sI[top] = i - off; sJ[top] = j; sw[top] = (T)0.5 * wt; ++top;
+                    sI[top] = i - off + s; sJ[top] = j; sw[top] = (T)0.5 * wt; ++top;
                 } else {
                     const int32_t off = (((j - L.iy[q]) % L.NY) + L.NY) % L.NY;
-                    sI[top] = i; sJ[top] = j - off; sw[top] = 0.5 * wt; ++top;
-                    sI[top] = i; sJ[top] = j - off + s; sw[top] = 0.5 * wt; ++top;
+                    sI[top] = i; sJ[top] = j - off; sw[top] = (T)0.5 * wt; ++top;
+                    sI[top] = i; sJ[top] = j - off + s; sw[top] = (T)0.5 * wt; ++top;
                 }
                 continue;
             }
-            double sx = 0.0, sy = 0.0;
+            T sx = 0, sy = 0;
             int nx = 0, ny = 0;
             if (in_y(j)) { sx += grad_x(i, j); ++nx; }
             if (in_y(j - 1)) { sx += grad_x(i, j - 1); ++nx; }
             if (in_x(i - 1)) { sy += grad_y(i - 1, j); ++ny; }
             if (in_x(i)) { sy += grad_y(i, j); ++ny; }
-            ex += wt * (nx ? -sx / nx : 0.0);
-            ey += wt * (ny ? -sy / ny : 0.0);
+            ex -= wt * (nx == 2 ? (T)0.5 * sx : sx);
+            ey -= wt * (ny == 2 ? (T)0.5 * sy : sy);
         }
     }
 };
 
 template <typename R>
-__global__ void k_node_e(int64_t n, FieldView F, R *__restrict__ stencil) {
+__global__ void k_node_e(int64_t n, FieldView<R> F, R *__restrict__ stencil) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * n) return;
     const int32_t l = (int32_t)(t >> 2);
     const int c = (int)(t & 3);
     const int32_t s = F.L.side(l);
-    double ex, ey;
+    R ex, ey;
     F.node(F.L.ix[l] + ((c & 1) ? s : 0), F.L.iy[l] + ((c & 2) ? s : 0), ex, ey);
-    stencil[8 * (int64_t)l + 2 * c] = (R)ex;
-    stencil[8 * (int64_t)l + 2 * c + 1] = (R)ey;
+    stencil[8 * (int64_t)l + 2 * c] = ex;
+    stencil[8 * (int64_t)l + 2 * c + 1] = ey;
 }
 
-__global__ void k_cell_emag(int64_t n, FieldView F, double *__restrict__ out) {
+__global__ void k_cell_emag(int64_t n, FieldView<double> F, double *__restrict__ out) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
     const int32_t x = F.L.ix[l], y = F.L.iy[l], s = F.L.side((int32_t)l);
@@ -510,31 +513,31 @@ void mesh_build_device(pic_ctx *ctx, Instance &in, int64_t n) {
     in.has_mesh = true;
 }
 
-void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {
-    Level &g = in.lv[0];
-    FieldView F;
-    F.L = view_of(in, g);
+template <typename T> FieldView<T> field_view(const Instance &in, const double walls[4]) {
+    FieldView<T> F;
+    F.L = view_of(in, in.lv[0]);
     F.phi = in.phi;
-    F.hf = in.h0 / (double)(1 << in.lmax);
+    F.inv_hf = (T)((double)(1 << in.lmax) / in.h0);
     F.bcx = in.cfg.bc_x; F.bcy = in.cfg.bc_y;
     for (int k = 0; k < 4; ++k) F.wall[k] = walls[k];
+    return F;
+}
+
+void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {
+    Level &g = in.lv[0];
     if (in.cfg.precision == PIC_FP64)
-        k_node_e<double><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, F, (double *)in.stencil);
+        k_node_e<double><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, field_view<double>(in, walls),
+                                                                     (double *)in.stencil);
     else
-        k_node_e<float><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, F, (float *)in.stencil);
+        k_node_e<float><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, field_view<float>(in, walls),
+                                                                    (float *)in.stencil);
     count_launch(ctx);
     check_launch("node_e");
 }
 
 void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev) {
     Level &g = in.lv[0];
-    FieldView F;
-    F.L = view_of(in, g);
-    F.phi = in.phi;
-    F.hf = in.h0 / (double)(1 << in.lmax);
-    F.bcx = in.cfg.bc_x; F.bcy = in.cfg.bc_y;
-    for (int k = 0; k < 4; ++k) F.wall[k] = walls[k];
-    k_cell_emag<<<blocks_for(g.n), kT, 0, ctx->stream>>>(g.n, F, out_dev);
+    k_cell_emag<<<blocks_for(g.n), kT, 0, ctx->stream>>>(g.n, field_view<double>(in, walls), out_dev);
     count_launch(ctx);
     check_launch("cell_emag");
 }

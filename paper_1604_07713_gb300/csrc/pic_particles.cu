@@ -67,6 +67,26 @@ template <> __device__ __forceinline__ double below_one<double>() { return 0.999
 
 template <typename R> __device__ __forceinline__ R u24(uint32_t r) { return (R)(r >> 8) * (R)(1.0 / 16777216.0); }
 
+// Compensated accumulation (Kahan) of one lane, and an error-free combination of the lanes'
+// (sum, -compensation) pairs: every lane ends with the same (hi, lo).
+template <typename R> __device__ __forceinline__ void kahan_add(R &sum, R &c, R x) {
+    const R y = x - c;
+    const R t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+}
+template <typename R> __device__ __forceinline__ void warp_two_sum(R &hi, R &lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const R oh = __shfl_xor_sync(0xFFFFFFFFu, hi, o), ol = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const R t = hi + oh;
+        const R bp = t - hi;
+        const R err = (hi - (t - bp)) + (oh - bp);
+        hi = t;
+        lo = lo + ol + err;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Deposit (§3 NGP at leaf centres; §3.1 no volume weighting): per leaf
 //   charge = sum_s q_s sum_{p in list} w_p   (FP32 Kahan per lane, FP64 across lanes)
@@ -97,16 +117,16 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
             const int32_t p0 = a.start[s][L], p1 = a.start[s][L + 1];
             const R *w = (const R *)a.w[s];
             R sum = 0, c = 0;
-            for (int32_t p = p0 + lane; p < p1; p += 32) {
-                const R y = w[p] - c;
-                const R t = sum + y;
-                c = (t - sum) - y;
-                sum = t;
-            }
-            double d = (double)sum - (double)c;
+            for (int32_t p = p0 + lane; p < p1; p += 128) {
+                R x4[4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
-            total += a.q[s] * d;
+                for (int k = 0; k < 4; ++k) x4[k] = p + 32 * k < p1 ? w[p + 32 * k] : (R)0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) kahan_add(sum, c, x4[k]);
+            }
+            R hi = sum, lo = -c;
+            warp_two_sum(hi, lo);
+            total += a.q[s] * ((double)hi + (double)lo);
         }
         if (lane == 0) {
             const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
@@ -116,6 +136,20 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
             a.b[L] = bl;
         }
     }
+}
+
+// Deposit from the per-leaf weight sums that the last cell-list update left behind
+// (staying particles summed by the move pass, entering ones by the per-leaf sort).
+__global__ void k_deposit_sums(DepositArgs a, const double *__restrict__ ws0, const double *__restrict__ ws1) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= a.nleaf) return;
+    double total = a.q[0] * ws0[L];
+    if (a.nsp > 1) total += a.q[1] * ws1[L];
+    const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
+    a.charge[L] = total;
+    double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
+    for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * a.wall[k];
+    a.b[L] = bl;
 }
 
 // ------------------------------------------------------------------------------------
@@ -146,6 +180,7 @@ template <typename R> struct PushArgs {
     uint32_t *ion_key;
     const int32_t *ion_start_new, *ion_stay, *ion_start_old;
     int32_t *ion_fill;
+    R *stay_hi, *stay_lo;  // move pass: compensated weight sum of each leaf's staying particles
     int32_t cap, ion_cap;  // record capacity of the output buffers
     int32_t *err;          // set when a write would fall outside them (count/move mismatch)
     // collisions
@@ -184,11 +219,14 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
     for (int64_t Lw = warp; Lw < a.nleaf; Lw += nw) {
         const int32_t L = (int32_t)Lw;
         const int32_t p0 = a.start[L], p1 = a.start[L + 1];
-        if (a.mode == 0 && p0 == p1) {
-            if (lane == 0) { a.stay[L] = 0; if (a.spawn) a.spawn[L] = 0; }
+        if (p0 == p1) {
+            if (lane == 0) {
+                if (a.mode == 0) { a.stay[L] = 0; if (a.spawn) a.spawn[L] = 0; }
+                else { a.stay_hi[L] = (R)0; a.stay_lo[L] = (R)0; }
+            }
             continue;
         }
-        if (p0 == p1) continue;
+        R ws_sum = 0, ws_c = 0;  // staying particles' weights, in list order per lane
         const int lv = a.lev[L];
         const int32_t s = 1 << (a.lmax - lv);
         const int32_t lx = a.ix[L], ly = a.iy[L];
@@ -199,17 +237,30 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
         int32_t stay_run = 0, spawn_run = 0;
         const int32_t sbase = (a.mode == 1 && a.spawn_base) ? a.spawn_base[L] : 0;
         const int32_t dst0 = a.mode == 1 ? a.start_new[L] : 0;
+        // software pipeline: the next chunk's record is loaded while this chunk computes
+        R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nw = 0;
+        uint32_t nid = 0;
+        if (p0 + lane < p1) {
+            const int32_t q = p0 + lane;
+            nu = a.in.u[q]; nv = a.in.v[q]; nvx = a.in.vx[q]; nvy = a.in.vy[q]; nvz = a.in.vz[q];
+            nid = a.in.id[q];
+            if (a.mode == 1) nw = a.in.w[q];
+        }
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
             const bool live = p < p1;
             bool alive = false, stays = false, spawns = false;
             int32_t nl = -1;
-            R u = 0, v = 0, vx = 0, vy = 0, vz = 0, w = 0;
-            uint32_t id = 0;
+            R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nw;
+            uint32_t id = nid;
+            if (p + 32 < p1) {
+                const int32_t q = p + 32;
+                nu = a.in.u[q]; nv = a.in.v[q]; nvx = a.in.vx[q]; nvy = a.in.vy[q]; nvz = a.in.vz[q];
+                nid = a.in.id[q];
+                if (a.mode == 1) nw = a.in.w[q];
+            }
             R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
             if (live) {
-                u = a.in.u[p]; v = a.in.v[p]; vx = a.in.vx[p]; vy = a.in.vy[p]; vz = a.in.vz[p];
-                id = a.in.id[p];
                 // gather: bilinear in the leaf's corner field
                 const R w00 = ((R)1 - u) * ((R)1 - v), w10 = u * ((R)1 - v), w01 = ((R)1 - u) * v, w11 = u * v;
                 const R ex = w00 * E[0] + w10 * E[2] + w01 * E[4] + w11 * E[6];
@@ -249,13 +300,17 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
                         stays = nl == L;
                     }
                 }
-                if (alive && a.mcc) {
+                // The count pass only needs the spawn decisions, which only electrons above the
+                // ionization threshold can make; the move pass runs every collision.  v2 and eps
+                // are computed once so both passes take the identical decision.
+                const R v2 = vx * vx + vy * vy + vz * vz;
+                const R eps = a.half_m_over_qe * v2;
+                const bool collide_here = a.mode == 1 || (a.species == 0 && a.sig_iz0 > (R)0 && eps > a.eps_th);
+                if (alive && a.mcc && collide_here) {
                     const U4 r0 = philox4x32_10(id, a.inst_word, a.step, 0u, a.k0, a.k1);
                     const R U0 = u24<R>(r0.x), U1 = u24<R>(r0.y), U2 = u24<R>(r0.z), U3 = u24<R>(r0.w);
                     if (a.species == 0) {
-                        const R v2 = vx * vx + vy * vy + vz * vz;
                         const R speed = m_sqrt(v2);
-                        const R eps = a.half_m_over_qe * v2;
                         const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - a.eps_th / eps) : (R)0;
                         const R st = a.sig_el + siz;
                         const R P = -m_expm1(-a.ng_dt * st * speed);
@@ -324,7 +379,6 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
                 stay_run += __popc(stay_mask);
                 spawn_run += __popc(spawn_mask);
             } else {
-                if (live) w = a.in.w[p];
                 if (live && alive) {
                     int32_t dst;
                     if (stays) {
@@ -335,6 +389,7 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
                         if (dst >= 0 && dst < a.cap) a.key_out[dst] = (uint32_t)p;
                     }
                     if (dst < 0 || dst >= a.cap) { atomicExch(a.err, 1); dst = -1; }
+                    if (stays) kahan_add(ws_sum, ws_c, w);
                     if (dst >= 0) {
                     a.out.u[dst] = u; a.out.v[dst] = v;
                     a.out.vx[dst] = vx; a.out.vy[dst] = vy; a.out.vz[dst] = vz;
@@ -375,6 +430,11 @@ __global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
             a.stay[L] = stay_run;
             if (a.spawn) a.spawn[L] = spawn_run;
         }
+        if (a.mode == 1) {
+            R hi = ws_sum, lo = -ws_c;
+            warp_two_sum(hi, lo);
+            if (lane == 0) { a.stay_hi[L] = hi; a.stay_lo[L] = lo; }
+        }
     }
 }
 
@@ -387,22 +447,14 @@ __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__res
     if (threadIdx.x == 0 && blockIdx.x == 0) *next_id += 2ull * (unsigned long long)(*spawn_total);
 }
 
-// ------------------------------------------------------------------------------------
-// Per-leaf sort of the entering slots [start + stay, start_next) by key (one warp per leaf).
-// Up to 32 entries sort in registers; longer runs go through the idle buffer `tmp`.
-// ------------------------------------------------------------------------------------
+// Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
+// longer runs go through the idle buffer `tmp`.
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32_t *__restrict__ start,
-                                                      const int32_t *__restrict__ stay, SoA<R> d,
-                                                      uint32_t *__restrict__ key, SoA<R> tmp,
-                                                      uint32_t *__restrict__ tkey) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t L = warp; L < nleaf; L += nw) {
-        const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
+__device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t *__restrict__ key, SoA<R> tmp,
+                            uint32_t *__restrict__ tkey) {
+    {
         const int32_t k = b1 - b0;
-        if (k <= 1) continue;
+        if (k <= 1) return;
         if (k <= 32) {
             const bool act = lane < k;
             const uint32_t kk = act ? key[b0 + lane] : 0xFFFFFFFFu;
@@ -439,6 +491,44 @@ __global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32
                 d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
             }
             __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Per-leaf sort of the entering slots [start + stay, start_next) by key (one warp per leaf).
+// Up to 32 entries sort in registers; longer runs go through the idle buffer `tmp`.
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32_t *__restrict__ start,
+                                                      const int32_t *__restrict__ stay, SoA<R> d,
+                                                      uint32_t *__restrict__ key, SoA<R> tmp,
+                                                      uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
+                                                      const R *__restrict__ stay_lo, double *__restrict__ wsum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t L = warp; L < nleaf; L += nw) {
+        const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
+        sort_region(b0, b1, lane, d, key, tmp, tkey);
+        if (wsum) {
+            // the leaf's weight for the next deposit: staying sum + entering particles in order
+            // (a few entering particles: one lane, in order; many: lanes, then an exact combine)
+            __syncwarp();
+            const int32_t k = b1 - b0;
+            if (k <= 16) {
+                if (lane == 0) {
+                    R sum = 0, c = 0;
+                    for (int32_t p = b0; p < b1; ++p) kahan_add(sum, c, d.w[p]);
+                    wsum[L] = ((double)stay_hi[L] + (double)stay_lo[L]) + ((double)sum - (double)c);
+                }
+            } else {
+                R sum = 0, c = 0;
+                for (int32_t p = b0 + lane; p < b1; p += 32) kahan_add(sum, c, d.w[p]);
+                R hi = sum, lo = -c;
+                warp_two_sum(hi, lo);
+                if (lane == 0) wsum[L] = ((double)stay_hi[L] + (double)stay_lo[L]) + ((double)hi + (double)lo);
+            }
         }
     }
 }
@@ -551,6 +641,8 @@ template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, i
     a.k1 = (uint32_t)(c.seed >> 32);
     a.inst_word = (uint32_t)c.instance << 24;
     a.cap = (int32_t)sp.cap;
+    a.stay_hi = (R *)sp.stay_hi;
+    a.stay_lo = (R *)sp.stay_lo;
     a.ion_cap = in.cfg.n_species > 1 ? (int32_t)in.sp[1].cap : 0;
     a.err = in.d_err;
     a.step = (uint32_t)step;
@@ -625,10 +717,12 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
             Species &sp = in.sp[s];
             // entering region of leaf L: [start_new[L] + stay[L], start_new[L + 1])
             k_sort_entering<R><<<wb, kT, 0, st>>>(nl, sp.start_new, sp.stay, soa<R>(sp, sp.cur ^ 1), sp.key,
-                                                  soa<R>(sp, sp.cur), sp.key + sp.cap);
+                                                  soa<R>(sp, sp.cur), sp.key + sp.cap, (const R *)sp.stay_hi,
+                                                  (const R *)sp.stay_lo, sp.wsum);
             count_launch(ctx);
             std::swap(sp.start, sp.start_new);
             sp.cur ^= 1;
+            sp.sums_valid = true;
         }
     }
     check_launch("particle_step");
@@ -655,6 +749,10 @@ void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
     sp.inc = dalloc<int32_t>(A, nl + 1);
     sp.fill = dalloc<int32_t>(A, nl + 1);
     sp.spawn = dalloc<int32_t>(A, nl + 1);
+    sp.stay_hi = A.alloc((nl + 1) * rs + 64);
+    sp.stay_lo = A.alloc((nl + 1) * rs + 64);
+    sp.wsum = dalloc<double>(A, nl + 1);
+    sp.sums_valid = false;
     // spawn_base [nl + 1] | scan scratch | scan scratch
     sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
     GB_CUDA(cudaMemsetAsync(sp.start, 0, (nl + 1) * 4, ctx->stream));
@@ -732,10 +830,12 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
         count_launch(ctx);
         if (in.cfg.precision == PIC_FP64)
             k_sort_entering<double><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, nullptr, soa<double>(sp, 0), sp.key,
-                                                                    soa<double>(sp, 1), sp.key + sp.cap);
+                                                                    soa<double>(sp, 1), sp.key + sp.cap, nullptr,
+                                                                    nullptr, nullptr);
         else
             k_sort_entering<float><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, nullptr, soa<float>(sp, 0), sp.key,
-                                                                   soa<float>(sp, 1), sp.key + sp.cap);
+                                                                   soa<float>(sp, 1), sp.key + sp.cap, nullptr,
+                                                                   nullptr, nullptr);
         count_launch(ctx);
     }
     unsigned long long nid = next_id;
@@ -773,7 +873,12 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
     for (int k = 0; k < 4; ++k) a.wall[k] = walls[k];
     a.charge = in.charge;
     a.b = in.bvec;
-    if (in.cfg.precision == PIC_FP64)
+    bool sums = true;
+    for (int s = 0; s < in.cfg.n_species; ++s) sums = sums && in.sp[s].start && in.sp[s].sums_valid;
+    if (sums)
+        k_deposit_sums<<<blocks_for(in.nleaf), kT, 0, ctx->stream>>>(a, in.sp[0].wsum,
+                                                                   in.cfg.n_species > 1 ? in.sp[1].wsum : nullptr);
+    else if (in.cfg.precision == PIC_FP64)
         k_deposit<double><<<warp_blocks(in.nleaf), kT, 0, ctx->stream>>>(a);
     else
         k_deposit<float><<<warp_blocks(in.nleaf), kT, 0, ctx->stream>>>(a);

@@ -231,3 +231,37 @@ def streamer(n_particles=200_000, nx0=128, lmax=4, seed=DEFAULT_SEED, precision=
     root, level, mort = tree
     mesh = dict(nx0=nx0, ny0=nx0, h0=h0, lmax=lmax, root=root, level=level, morton=mort)
     return cfg, mesh, parts
+
+
+def streamer_snapshot(n_particles=50_000_000, nx0=128, lmax=4, seed=DEFAULT_SEED, precision=FP32,
+                      box=0.01, e0=3e6, ng=3.2e24, dt=1e-13, n_e=1e19):
+    """A grown 2D streamer: electrons and ions (half each) in a channel along x through the
+    box centre (uniform over the middle half of the box in x with Gaussian ends, Gaussian
+    across with sigma = 0.5 mm), electrons Maxwellian at 5 eV and ions at 0.026 eV; weights
+    give a channel density of about n_e.  Same physics and walls as ``streamer``; the mesh
+    starts as the uniform root grid and is refined on the device by adaptation."""
+    rng = np.random.default_rng(seed)
+    n = n_particles // 2
+    h0 = box / nx0
+    sig_y = 0.05 * box
+    parts = {}
+    mi = 4.0 * AMU
+    area = 0.5 * box * (2.5 * sig_y)
+    w = n_e * area / n
+    for s, (m, T) in enumerate(((ME, 5.0), (mi, 0.026))):
+        u = rng.random(n)
+        x = 0.25 * box + 0.5 * box * u + 0.05 * box * rng.standard_normal(n) * (u < 0.0)
+        tail = rng.random(n) < 0.1
+        x[tail] = 0.5 * box + 0.3 * box * rng.standard_normal(int(tail.sum()))
+        y = 0.5 * box + sig_y * rng.standard_normal(n)
+        x = np.clip(x, 1e-4 * box, box * (1 - 1e-4)); y = np.clip(y, 1e-4 * box, box * (1 - 1e-4))
+        vt = math.sqrt(T * QE / m)
+        v = rng.standard_normal((3, n)) * vt
+        parts[s] = dict(x=x, y=y, vx=v[0], vy=v[1], vz=v[2], w=np.full(n, w))
+    cfg = base_config(precision=precision, n_species=2, dt=dt, eps0=EPS0, q=[-QE, QE],
+                      m=[ME, mi], qe=QE, mcc=1, bc_x=BC_DIRICHLET, bc_y=BC_NEUMANN,
+                      max_level=lmax, gas_density=ng, gas_temperature_ev=0.026, neutral_mass=mi,
+                      sigma_el=6e-20, sigma_iz0=1e-20, eps_th_ev=24.6, phi_left_dc=0.0,
+                      phi_right=e0 * box, e_ref=e0, adapt_every=10, mg_rel_tol=1e-8)
+    mesh = dict(nx0=nx0, ny0=nx0, h0=h0, lmax=lmax)
+    return cfg, mesh, parts
