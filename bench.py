@@ -2,13 +2,18 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbpic|reference]
 
-Workload: the 2D capacitively coupled discharge (512 x 16 square cells, plates at x = 0 with
-200 V at 13.56 MHz and x = 6.7 cm grounded, periodic in y, electrons and 4 amu ions, 100
-macro-particles per cell and species = 2 x 819,200, Maxwellian 2.5 eV / 0.026 eV, analytic
-elastic + ionization cross sections, dt = 1/(400 f)), FP32 particle state.  One step is the
-whole cycle: NGP deposit, multigrid Poisson, corner field, fused gather/push/locate/MCC,
-cell-list update.  Inputs are resident in HBM; L2 is flushed (256 MiB write) before every
-timed step, outside the timed events.
+Workloads (FP32 particle state):
+  streamer (default): the 2D streamer on an adaptive quadtree -- 1 cm box of 128 x 128 root
+      boxes refined up to 4 levels on the device, 5e7 electrons + ions in a channel, 3 MV/m
+      background field, ionization MCC, split/merge toward 32 per leaf (band 8-128) and mesh
+      adaptation every 10 steps inside the timed region.  State >> L2.
+  ccp: the 2D capacitively coupled discharge (512 x 16 square cells, plates at x = 0 with
+      200 V at 13.56 MHz and x = 6.7 cm grounded, periodic in y, electrons and 4 amu ions,
+      100 macro-particles per cell and species = 2 x 819,200, dt = 1/(400 f)); L2 is flushed
+      (256 MiB write) before every timed step, outside the timed events.
+One step is the whole cycle: NGP deposit, multigrid Poisson, corner field, fused
+gather/push/locate/MCC, cell-list update (plus the adaptation cadence).  Inputs are resident
+in HBM when the timed region starts.
 
 Prints one JSON line: particle-steps/s (whole job), the roofline of the dominant particle
 kernel (the move pass of the fused push), the oracle's CPU baseline on a bounded sample,
@@ -359,7 +364,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbpic", choices=["gbpic", "reference"])
     ap.add_argument("--seed", type=int, default=160407713)
-    ap.add_argument("--workload", default="ccp", choices=WORKLOADS)
+    ap.add_argument("--workload", default="streamer", choices=WORKLOADS)
     ap.add_argument("--particles", type=int, default=50_000_000, help="streamer workload: total particles")
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -1,0 +1,98 @@
+"""System behaviour of the C ABI on the GPU: batched instances equal the same instances run
+alone, runs are deterministic, capacity grows under ionization, and invalid input is
+refused with the documented status."""
+import numpy as np
+import pytest
+
+import paper_1604_07713_gb300 as G
+from paper_1604_07713_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    G.build()
+
+
+def _ccp(nx, ppc, seed, volt, ng):
+    cfg, mesh, parts = W.ccp(nx=nx, ny=8, ppc=ppc, seed=seed, precision=W.FP32, volt=volt, ng=ng, te=8.0)
+    return cfg, mesh, parts
+
+
+def _run_alone(cfg, mesh, parts, steps):
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s in sorted(parts):
+            ctx.load(s, **parts[s])
+        ctx.step(steps)
+        return [ctx.particles(s) for s in (0, 1)]
+
+
+def test_batched_instances_equal_instances_run_alone():
+    cases = [_ccp(32, 10, 1, 100.0, 3e20), _ccp(48, 20, 2, 300.0, 1e21), _ccp(64, 15, 3, 200.0, 3e21)]
+    for i, (cfg, _, _) in enumerate(cases):
+        cfg["instance"] = i
+    with G.Context([c[0] for c in cases]) as ctx:
+        for i, (cfg, mesh, parts) in enumerate(cases):
+            ctx.set_mesh_dict(mesh, inst=i)
+            for s in sorted(parts):
+                ctx.load(s, **parts[s], inst=i)
+        ctx.step(4)
+        batched = [[ctx.particles(s, inst=i) for s in (0, 1)] for i in range(len(cases))]
+    for i, (cfg, mesh, parts) in enumerate(cases):
+        alone = _run_alone(cfg, mesh, parts, 4)
+        for s in (0, 1):
+            for k in ("id", "x", "y", "vx", "vy", "vz", "w"):
+                assert np.array_equal(batched[i][s][k], alone[s][k]), (i, s, k)
+
+
+def test_two_runs_are_bitwise_identical():
+    cfg, mesh, parts = _ccp(64, 20, 5, 200.0, 3e21)
+    a = _run_alone(cfg, mesh, parts, 5)
+    b = _run_alone(cfg, mesh, parts, 5)
+    for s in (0, 1):
+        for k in a[s]:
+            assert np.array_equal(a[s][k], b[s][k])
+
+
+def test_capacity_grows_under_ionization_and_fixed_capacity_is_enforced():
+    cfg, mesh, parts = W.ccp(nx=32, ny=8, ppc=20, seed=9, precision=W.FP32, te=40.0, ng=3e21)
+    cfg["dt"] *= 4
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s in sorted(parts):
+            ctx.load(s, **parts[s])
+        n0 = ctx.counts()
+        ctx.step(6)
+        n1 = ctx.counts()
+        assert n1["n_i"] > n0["n_i"]  # ionization spawned pairs
+        ids = ctx.particles(0)["id"]
+        assert np.unique(ids).size == ids.size
+    cfg["particle_capacity"] = parts[0]["x"].size + 1
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s in sorted(parts):
+            ctx.load(s, **parts[s])
+        with pytest.raises(G.PicError) as e:
+            ctx.step(6)
+        assert e.value.status == G.PIC_ECAPACITY
+
+
+def test_invalid_input_is_refused():
+    cfg, mesh, parts = _ccp(16, 4, 1, 100.0, 1e20)
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        p = {k: v.copy() for k, v in parts[0].items()}
+        p["x"][3] = -1.0  # outside the domain
+        with pytest.raises(G.PicError) as e:
+            ctx.load(0, **p)
+        assert e.value.status == G.PIC_EINVAL and "outside" in str(e.value)
+    # a leaf set that is not 2:1 balanced across faces
+    cfg2 = W.base_config(precision=W.FP32, n_species=1, q=[-1.0], m=[1.0], bc_x=W.BC_DIRICHLET,
+                         bc_y=W.BC_NEUMANN, max_level=2)
+    root, level, morton = [0] * 16 + [1], [2] * 16 + [0], list(range(16)) + [0]
+    with G.Context(cfg2) as ctx:
+        with pytest.raises(G.PicError) as e:
+            ctx.set_mesh(0, 2, 1, 1.0, np.array(root), np.array(morton), np.array(level))
+        assert e.value.status == G.PIC_EINVAL
