@@ -209,6 +209,7 @@ pic_status pic_destroy(pic_ctx *ctx) {
     if (!ctx) return PIC_OK;
     cudaStreamSynchronize(ctx->stream);
     for (Instance &in : ctx->inst) {
+        if (in.mg_cycle) cudaGraphExecDestroy(in.mg_cycle);
         in.mesh_mem.release_all();
         in.part_mem[0].release_all();
         in.part_mem[1].release_all();

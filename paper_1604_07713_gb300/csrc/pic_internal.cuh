@@ -111,6 +111,8 @@ struct Instance {
     double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
     bool mg_on_device = false;     // last solve ran its loop on the device (stats below)
     double *mg_stats = nullptr;    // device: [cycles, rel. residual, max rel. since reset]
+    cudaGraphExec_t mg_cycle = nullptr;  // multi-block meshes: one captured cycle (V-cycle,
+    int64_t mg_cycle_nodes = 0;          // correction, residual, norm read-back) and its launches
     DeviceArena mesh_mem;        // freed on pic_set_mesh
     DeviceArena part_mem[2];     // freed on reload / regrow
 };

@@ -211,7 +211,7 @@ template <typename R> __device__ __forceinline__ void normals3(const U4 &r, R n[
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kT) k_push(PushArgs<R> a) {
+__global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -449,50 +449,80 @@ __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__res
 
 // Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
 // longer runs go through the idle buffer `tmp`.
+constexpr int kSortSmem = 512;  // per-warp shared-memory sort capacity (keys + slots)
+
+// Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
+// up to 512 by a bitonic network on (key, slot) pairs in the warp's shared memory followed by
+// a gather through the idle buffer `tmp`; longer runs rank each key against all others.
 template <typename R>
 __device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t *__restrict__ key, SoA<R> tmp,
-                            uint32_t *__restrict__ tkey) {
-    {
-        const int32_t k = b1 - b0;
-        if (k <= 1) return;
-        if (k <= 32) {
-            const bool act = lane < k;
-            const uint32_t kk = act ? key[b0 + lane] : 0xFFFFFFFFu;
-            int rank = 0;
-            for (int j = 0; j < k; ++j) {
-                const uint32_t o = __shfl_sync(0xFFFFFFFFu, kk, j);
-                rank += (o < kk) ? 1 : 0;
-            }
-            R u = 0, v = 0, vx = 0, vy = 0, vz = 0, w = 0;
-            uint32_t id = 0;
-            if (act) {
-                const int32_t p = b0 + lane;
-                u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p]; id = d.id[p];
-            }
-            __syncwarp();
-            if (act) {
-                const int32_t q = b0 + rank;
-                d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
-                key[q] = kk;
-            }
-            __syncwarp();
-        } else {
-            for (int32_t p = b0 + lane; p < b1; p += 32) {
-                tmp.u[p] = d.u[p]; tmp.v[p] = d.v[p]; tmp.vx[p] = d.vx[p]; tmp.vy[p] = d.vy[p];
-                tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
-            }
-            __syncwarp();
-            for (int32_t p = b0 + lane; p < b1; p += 32) {
-                const uint32_t kk = tkey[p];
-                int32_t rank = 0;
-                for (int32_t j = b0; j < b1; ++j) rank += (tkey[j] < kk) ? 1 : 0;
-                const int32_t q = b0 + rank;
-                d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
-                d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
-            }
-            __syncwarp();
+                            uint32_t *__restrict__ tkey, unsigned long long *wsm) {
+    const int32_t k = b1 - b0;
+    if (k <= 1) return;
+    if (k <= 32) {
+        const bool act = lane < k;
+        const uint32_t kk = act ? key[b0 + lane] : 0xFFFFFFFFu;
+        int rank = 0;
+        for (int j = 0; j < k; ++j) {
+            const uint32_t o = __shfl_sync(0xFFFFFFFFu, kk, j);
+            rank += (o < kk) ? 1 : 0;
         }
+        R u = 0, v = 0, vx = 0, vy = 0, vz = 0, w = 0;
+        uint32_t id = 0;
+        if (act) {
+            const int32_t p = b0 + lane;
+            u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p]; id = d.id[p];
+        }
+        __syncwarp();
+        if (act) {
+            const int32_t q = b0 + rank;
+            d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
+            key[q] = kk;
+        }
+        __syncwarp();
+        return;
     }
+    // copy the region to the idle buffer
+    for (int32_t p = b0 + lane; p < b1; p += 32) {
+        tmp.u[p] = d.u[p]; tmp.v[p] = d.v[p]; tmp.vx[p] = d.vx[p]; tmp.vy[p] = d.vy[p];
+        tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
+    }
+    __syncwarp();
+    if (k <= kSortSmem && wsm) {
+        int32_t np2 = 64;
+        while (np2 < k) np2 <<= 1;
+        for (int32_t i = lane; i < np2; i += 32)
+            wsm[i] = i < k ? (((unsigned long long)tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
+        __syncwarp();
+        for (int32_t kk = 2; kk <= np2; kk <<= 1) {
+            for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+                for (int32_t i = lane; i < np2; i += 32) {
+                    const int32_t ij = i ^ j;
+                    if (ij > i) {
+                        const unsigned long long x = wsm[i], y = wsm[ij];
+                        if ((x > y) == ((i & kk) == 0)) { wsm[i] = y; wsm[ij] = x; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int32_t r = lane; r < k; r += 32) {
+            const int32_t p = b0 + (int32_t)(wsm[r] & 0xFFFFFFFFull), q = b0 + r;
+            d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
+            d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = (uint32_t)(wsm[r] >> 32);
+        }
+        __syncwarp();
+        return;
+    }
+    for (int32_t p = b0 + lane; p < b1; p += 32) {
+        const uint32_t kk = tkey[p];
+        int32_t rank = 0;
+        for (int32_t j = b0; j < b1; ++j) rank += (tkey[j] < kk) ? 1 : 0;
+        const int32_t q = b0 + rank;
+        d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
+        d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------------------------
@@ -505,12 +535,13 @@ __global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32
                                                       uint32_t *__restrict__ key, SoA<R> tmp,
                                                       uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
                                                       const R *__restrict__ stay_lo, double *__restrict__ wsum) {
+    __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = warp; L < nleaf; L += nw) {
         const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
-        sort_region(b0, b1, lane, d, key, tmp, tkey);
+        sort_region(b0, b1, lane, d, key, tmp, tkey, sm_keys[threadIdx.x >> 5]);
         if (wsum) {
             // the leaf's weight for the next deposit: staying sum + entering particles in order
             // (a few entering particles: one lane, in order; many: lanes, then an exact combine)

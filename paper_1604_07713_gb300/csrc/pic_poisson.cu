@@ -705,7 +705,6 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     if ((int)g >= g0) {
         const SmallDesc D = small_desc(in, (int)g);
         const size_t bytes = (size_t)D.smem_floats * 4;
-        GB_CUDA(cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
         k_tail_vcycle<<<1, 1024, bytes, s>>>(D, L.b, L.x, singular);
         count_launch(ctx);
         return;
@@ -740,6 +739,12 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
 }  // namespace
 
 void poisson_setup(pic_ctx *ctx, Instance &in) {
+    if (in.mg_cycle) {
+        cudaGraphExecDestroy(in.mg_cycle);
+        in.mg_cycle = nullptr;
+    }
+    GB_CUDA(cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
+    GB_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
     DeviceArena &A = in.mesh_mem;
     const int64_t n = in.lv[0].n;
     in.phi = dalloc<double>(A, n);
@@ -773,7 +778,6 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     ++in.n_solves;
     if (small_from(in) == 0) {
         const SmallDesc D = small_desc(in, 0);
-        GB_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmemCap));
         k_small_solve<<<1, 1024, (size_t)D.smem_floats * 4, s>>>(D, L.diag64, L.val64, in.phi, in.bvec, L.lev, L.lmax,
                                                                  singular ? 1 : 0, in.cfg.mg_rel_tol,
                                                                  std::max(1, in.cfg.mg_max_cycles), in.mg_stats);
@@ -792,24 +796,55 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     double rel = 0.0;
     int cyc = 0;
     const int maxc = std::max(1, in.cfg.mg_max_cycles);
-    for (;;) {
-        k_residual64<<<kRedBlocks, kT, 0, s>>>(n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b, in.red);
-        k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+    // launches go to ctx->stream, which is the capture stream while the cycle is captured
+    auto issue_residual = [&]() {
+        k_residual64<<<kRedBlocks, kT, 0, ctx->stream>>>(n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b, in.red);
+        k_finish_sums<<<1, 32, 0, ctx->stream>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
         count_launch(ctx, 2);
-        GB_CUDA(cudaMemcpyAsync(in.red_host, in.red + 2 * kRedBlocks, 16, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(in.red_host, in.red + 2 * kRedBlocks, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    };
+    auto issue_cycle = [&]() {
+        vcycle(ctx, in, 0, singular);
+        k_add_correction<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.x, in.phi);
+        count_launch(ctx);
+        if (singular) {
+            k_area_weighted<<<kRedBlocks, kT, 0, ctx->stream>>>(n, L.lev, L.lmax, in.phi, in.red);
+            k_finish_sums<<<1, 32, 0, ctx->stream>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+            k_project<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
+            count_launch(ctx, 3);
+        }
+        issue_residual();
+    };
+    if (!in.mg_cycle) {
+        // capture one cycle on a private stream (the context's stream may be the legacy
+        // default stream, which cannot be captured); replay it on the context's stream
+        cudaStream_t cs;
+        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaStream_t saved = ctx->stream;
+        const int64_t l0 = ctx->launches;
+        ctx->stream = cs;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e1 == cudaSuccess) {
+            issue_cycle();
+            e1 = cudaStreamEndCapture(cs, &graph);
+        }
+        ctx->stream = saved;
+        in.mg_cycle_nodes = ctx->launches - l0;
+        ctx->launches = l0;
+        cudaStreamDestroy(cs);
+        GB_CUDA(e1);
+        GB_CUDA(cudaGraphInstantiate(&in.mg_cycle, graph, 0));
+        cudaGraphDestroy(graph);
+    }
+    issue_residual();
+    for (;;) {
         GB_CUDA(cudaStreamSynchronize(s));
         const double rr = in.red_host[0], bb = in.red_host[1];
         rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
         if (rel <= in.cfg.mg_rel_tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
-        vcycle(ctx, in, 0, singular);
-        k_add_correction<<<blocks_for(n), kT, 0, s>>>(n, L.x, in.phi);
-        count_launch(ctx);
-        if (singular) {
-            k_area_weighted<<<kRedBlocks, kT, 0, s>>>(n, L.lev, L.lmax, in.phi, in.red);
-            k_finish_sums<<<1, 32, 0, s>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
-            k_project<<<blocks_for(n), kT, 0, s>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
-            count_launch(ctx, 3);
-        }
+        GB_CUDA(cudaGraphLaunch(in.mg_cycle, s));
+        count_launch(ctx, in.mg_cycle_nodes);
         ++cyc;
     }
     check_launch("poisson_solve");
