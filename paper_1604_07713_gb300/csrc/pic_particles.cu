@@ -453,12 +453,12 @@ constexpr int kSortSmem = 512;  // per-warp shared-memory sort capacity (keys + 
 
 // Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
 // up to 512 by a bitonic network on (key, slot) pairs in the warp's shared memory followed by
-// a gather through the idle buffer `tmp`; longer runs rank each key against all others.
+// a gather through the idle buffer `tmp`; longer runs were sorted by k_sort_big already.
 template <typename R>
 __device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t *__restrict__ key, SoA<R> tmp,
                             uint32_t *__restrict__ tkey, unsigned long long *wsm) {
     const int32_t k = b1 - b0;
-    if (k <= 1) return;
+    if (k <= 1 || k > kSortSmem) return;  // longer regions: k_sort_big
     if (k <= 32) {
         const bool act = lane < k;
         const uint32_t kk = act ? key[b0 + lane] : 0xFFFFFFFFu;
@@ -488,7 +488,7 @@ __device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t
         tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
     }
     __syncwarp();
-    if (k <= kSortSmem && wsm) {
+    {
         int32_t np2 = 64;
         while (np2 < k) np2 <<= 1;
         for (int32_t i = lane; i < np2; i += 32)
@@ -512,17 +512,82 @@ __device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t
             d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = (uint32_t)(wsm[r] >> 32);
         }
         __syncwarp();
-        return;
     }
-    for (int32_t p = b0 + lane; p < b1; p += 32) {
-        const uint32_t kk = tkey[p];
-        int32_t rank = 0;
-        for (int32_t j = b0; j < b1; ++j) rank += (tkey[j] < kk) ? 1 : 0;
-        const int32_t q = b0 + rank;
-        d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
-        d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
+}
+
+constexpr int kSortBig = 16384;  // one block sorts up to this many entries in shared memory
+
+// Leaves whose entering region is longer than one warp's shared-memory sort: one block per
+// leaf, bitonic network on (key, slot) pairs in dynamic shared memory, gather through `tmp`.
+// Regions longer than kSortBig rank every key against all others with the whole block.
+template <typename R>
+__global__ void __launch_bounds__(512) k_sort_big(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+                                                  const int32_t *__restrict__ start,
+                                                  const int32_t *__restrict__ stay, SoA<R> d,
+                                                  uint32_t *__restrict__ key, SoA<R> tmp,
+                                                  uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
+                                                  const R *__restrict__ stay_lo, double *__restrict__ wsum) {
+    extern __shared__ unsigned long long bk[];
+    __shared__ R red_hi[16], red_lo[16];
+    const int32_t nbig = *count;
+    for (int32_t li = blockIdx.x; li < nbig; li += gridDim.x) {
+        const int32_t L = list[li];
+        const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
+        const int32_t k = b1 - b0;
+        for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+            tmp.u[p] = d.u[p]; tmp.v[p] = d.v[p]; tmp.vx[p] = d.vx[p]; tmp.vy[p] = d.vy[p];
+            tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
+        }
+        __syncthreads();
+        if (k <= kSortBig) {
+            int32_t np2 = 1;
+            while (np2 < k) np2 <<= 1;
+            for (int32_t i = threadIdx.x; i < np2; i += blockDim.x)
+                bk[i] = i < k ? (((unsigned long long)tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
+            __syncthreads();
+            for (int32_t kk = 2; kk <= np2; kk <<= 1) {
+                for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+                    for (int32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+                        const int32_t ij = i ^ j;
+                        if (ij > i) {
+                            const unsigned long long x = bk[i], y = bk[ij];
+                            if ((x > y) == ((i & kk) == 0)) { bk[i] = y; bk[ij] = x; }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int32_t r = threadIdx.x; r < k; r += blockDim.x) {
+                const int32_t p = b0 + (int32_t)(bk[r] & 0xFFFFFFFFull), q = b0 + r;
+                d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
+                d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = (uint32_t)(bk[r] >> 32);
+            }
+        } else {
+            for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+                const uint32_t kk = tkey[p];
+                int32_t rank = 0;
+                for (int32_t j = b0; j < b1; ++j) rank += (tkey[j] < kk) ? 1 : 0;
+                const int32_t q = b0 + rank;
+                d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
+                d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
+            }
+        }
+        __syncthreads();
+        if (wsum) {  // entering weights in list order: per-thread Kahan, warps combined in order
+            R sum = 0, c = 0;
+            for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) kahan_add(sum, c, d.w[p]);
+            R hi = sum, lo = -c;
+            warp_two_sum(hi, lo);
+            if ((threadIdx.x & 31) == 0) { red_hi[threadIdx.x >> 5] = hi; red_lo[threadIdx.x >> 5] = lo; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = (double)stay_hi[L] + (double)stay_lo[L];
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)red_hi[w] + (double)red_lo[w];
+                wsum[L] = t;
+            }
+            __syncthreads();
+        }
     }
-    __syncwarp();
 }
 
 // ------------------------------------------------------------------------------------
@@ -534,13 +599,18 @@ __global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32
                                                       const int32_t *__restrict__ stay, SoA<R> d,
                                                       uint32_t *__restrict__ key, SoA<R> tmp,
                                                       uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
-                                                      const R *__restrict__ stay_lo, double *__restrict__ wsum) {
+                                                      const R *__restrict__ stay_lo, double *__restrict__ wsum,
+                                                      int32_t *__restrict__ big_list, int32_t *__restrict__ big_count) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = warp; L < nleaf; L += nw) {
         const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
+        if (b1 - b0 > kSortSmem) {  // long region: k_sort_big sorts it and sums its weights
+            if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)L;
+            continue;
+        }
         sort_region(b0, b1, lane, d, key, tmp, tkey, sm_keys[threadIdx.x >> 5]);
         if (wsum) {
             // the leaf's weight for the next deposit: staying sum + entering particles in order
@@ -627,6 +697,21 @@ __global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, double 
             leaf[p] = (uint32_t)L;
         }
     }
+}
+
+// Order the entering regions of every leaf: long regions first (one block each), then the
+// warp-per-leaf pass (short regions, and the weight sums when wsum is given).
+template <typename R>
+void sort_lists(pic_ctx *ctx, int64_t nl, const int32_t *start, const int32_t *stay, SoA<R> d, uint32_t *key,
+                SoA<R> tmp, uint32_t *tkey, const R *shi, const R *slo, double *wsum, int32_t *list) {
+    // `list` holds nl + 1 ints: the long-region list and its counter at [nl]
+    GB_CUDA(cudaMemsetAsync(list + nl, 0, 4, ctx->stream));
+    k_sort_entering<R><<<warp_blocks(nl), kT, 0, ctx->stream>>>(nl, start, stay, d, key, tmp, tkey, shi, slo, wsum,
+                                                                list, list + nl);
+    const size_t smem = (size_t)kSortBig * sizeof(unsigned long long);
+    GB_CUDA(cudaFuncSetAttribute(k_sort_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sort_big<R><<<152, 512, smem, ctx->stream>>>(list, list + nl, start, stay, d, key, tmp, tkey, shi, slo, wsum);
+    count_launch(ctx, 2);
 }
 
 template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, int64_t step) {
@@ -747,10 +832,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         for (int s = 0; s < nsp; ++s) {
             Species &sp = in.sp[s];
             // entering region of leaf L: [start_new[L] + stay[L], start_new[L + 1])
-            k_sort_entering<R><<<wb, kT, 0, st>>>(nl, sp.start_new, sp.stay, soa<R>(sp, sp.cur ^ 1), sp.key,
-                                                  soa<R>(sp, sp.cur), sp.key + sp.cap, (const R *)sp.stay_hi,
-                                                  (const R *)sp.stay_lo, sp.wsum);
-            count_launch(ctx);
+            sort_lists<R>(ctx, nl, sp.start_new, sp.stay, soa<R>(sp, sp.cur ^ 1), sp.key, soa<R>(sp, sp.cur),
+                          sp.key + sp.cap, (const R *)sp.stay_hi, (const R *)sp.stay_lo, sp.wsum, sp.fill);
             std::swap(sp.start, sp.start_new);
             sp.cur ^= 1;
             sp.sums_valid = true;
@@ -860,14 +943,11 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
                                                               soa<float>(sp, 0), sp.key);
         count_launch(ctx);
         if (in.cfg.precision == PIC_FP64)
-            k_sort_entering<double><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, nullptr, soa<double>(sp, 0), sp.key,
-                                                                    soa<double>(sp, 1), sp.key + sp.cap, nullptr,
-                                                                    nullptr, nullptr);
+            sort_lists<double>(ctx, nl, sp.start, nullptr, soa<double>(sp, 0), sp.key, soa<double>(sp, 1),
+                               sp.key + sp.cap, nullptr, nullptr, nullptr, sp.fill);
         else
-            k_sort_entering<float><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, nullptr, soa<float>(sp, 0), sp.key,
-                                                                   soa<float>(sp, 1), sp.key + sp.cap, nullptr,
-                                                                   nullptr, nullptr);
-        count_launch(ctx);
+            sort_lists<float>(ctx, nl, sp.start, nullptr, soa<float>(sp, 0), sp.key, soa<float>(sp, 1),
+                              sp.key + sp.cap, nullptr, nullptr, nullptr, sp.fill);
     }
     unsigned long long nid = next_id;
     if (id) {
