@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "ccp-512x16-ppc100-fp32"
 METRIC = "particle-steps/s"
-WORKLOADS = ("ccp", "streamer")
+WORKLOADS = ("ccp", "streamer", "ensemble")
 
 
 def _dist():
@@ -56,7 +56,14 @@ def _workload(seed, name="ccp", n_particles=50_000_000):
 
 
 def _config_json(ws, name="ccp", extra=None):
-    if name == "streamer":
+    if name == "ensemble":
+        d = {"workload": "ccp-ensemble-256-fp32", "instances": 256,
+             "cells": "per instance 64-512 x 16 uniform leaves (multiples of 16 in x)",
+             "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
+             "batching": "all instances in one context; one launch solves every instance's Poisson",
+             "l2": "inputs larger than L2 (particle state >> 129 MB)", "parallelism": f"replicas x{ws}",
+             "poisson_rel_tol": 1e-8}
+    elif name == "streamer":
         d = {"workload": "streamer-amr-128x128-l4-fp32", "cells": "adaptive quadtree, 128x128 roots, up to 4 levels",
              "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
              "adapt": "pic_adapt (mesh + split/merge) every 10 steps inside the timed region",
@@ -126,6 +133,23 @@ class ClockSampler:
 ORACLE_STREAMER_PARTICLES = 200_000
 
 
+ORACLE_ENSEMBLE_INSTANCES = 2
+
+
+def _oracle_sims_ensemble(seed):
+    import oracle as O
+    from paper_1604_07713_gb300 import workloads as W
+    sims = []
+    for cfg, mesh, factory, _ in W.ensemble(256, seed=seed)[:ORACLE_ENSEMBLE_INSTANCES]:
+        M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, cfg["bc_x"], cfg["bc_y"])
+        sim = O.Sim(cfg, M)
+        parts = factory()
+        for s_ in sorted(parts):
+            sim.load(s_, **parts[s_])
+        sims.append(sim)
+    return sims
+
+
 def _oracle_sim(seed, name="ccp"):
     import oracle as O
     if name == "streamer":
@@ -169,6 +193,17 @@ def _sample_text(name, steps, t):
 
 
 def cpu_baseline(seed, steps=12, name="ccp"):
+    if name == "ensemble":
+        sims = _oracle_sims_ensemble(seed)
+        tot, t = 0, 0.0
+        for sim in sims:
+            sim.step(1)
+            r, tt = _oracle_rate(sim, max(1, steps // len(sims)))
+            tot += r * tt
+            t += tt
+        return {"value": tot / t, "unit": METRIC, "cores": 1, "kind": "oracle",
+                "sample": f"the first {len(sims)} of the 256 instances, {max(1, steps // len(sims))} steps each, "
+                          f"FP64 oracle, single thread, {t:.1f} s"}
     sim = _oracle_sim(seed, name)
     sim.step(1)  # warm-up (imports, first solve)
     rate, t = _oracle_rate(sim, steps, 10 if name == "streamer" else 0)
@@ -178,6 +213,16 @@ def cpu_baseline(seed, steps=12, name="ccp"):
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
+        return
+    if args.workload == "ensemble":
+        base = cpu_baseline(args.seed, steps=args.steps * ORACLE_ENSEMBLE_INSTANCES, name="ensemble")
+        rate = base["value"]
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": _config_json(1, "ensemble"), "cpu_baseline": base,
+                "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
         return
     sim = _oracle_sim(args.seed, args.workload)
     for _ in range(args.warmup):
@@ -235,18 +280,41 @@ def run_gpu(args):
     streamer = name == "streamer"
 
     stream = torch.cuda.Stream()
-    cfg, mesh, parts = _workload(args.seed + rank, name, args.particles)
-    ctx = G.Context(cfg, stream_handle=stream.cuda_stream)
-    ctx.set_mesh_dict(mesh)
-    for s in sorted(parts):
-        ctx.load(s, **parts[s])
+    ensemble = name == "ensemble"
+    if ensemble:
+        from paper_1604_07713_gb300 import workloads as W
+        members = W.ensemble(256, seed=args.seed + rank)
+        cfg = members[0][0]
+        ctx = G.Context([m[0] for m in members], stream_handle=stream.cuda_stream)
+        for i, (c_i, mesh_i, factory, _) in enumerate(members):
+            ctx.set_mesh_dict(mesh_i, inst=i)
+            parts_i = factory()
+            for s_ in sorted(parts_i):
+                ctx.load(s_, **parts_i[s_], inst=i)
+        n_inst = len(members)
+        mesh, parts = members[0][1], None
+    else:
+        cfg, mesh, parts = _workload(args.seed + rank, name, args.particles)
+        ctx = G.Context(cfg, stream_handle=stream.cuda_stream)
+        ctx.set_mesh_dict(mesh)
+        for s in sorted(parts):
+            ctx.load(s, **parts[s])
+        n_inst = 1
     if streamer:  # refine the uniform roots onto the particles, then manage them (setup, untimed)
         for _ in range(mesh["lmax"] + 1):
             ctx.compute_fields(allow_notconv=True)
             ctx.adapt(G.PIC_ADAPT_MESH)
         ctx.compute_fields(allow_notconv=True)
         ctx.adapt()
-    flush = None if streamer else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def counts_all():
+        tot = {"n_e": 0, "n_i": 0, "n_leaves": 0, "mg_cycles": 0}
+        for i in range(n_inst):
+            c = ctx.counts(i)
+            for k in tot:
+                tot[k] += c[k]
+        return tot
+    flush = None if (streamer or ensemble) else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     adapt_every = cfg.get("adapt_every", 0) if streamer else 0
 
     def one_step(k):
@@ -270,7 +338,7 @@ def run_gpu(args):
     particle_steps = 0
     leaf_steps = 0
     for k in range(args.steps):
-        c = ctx.counts()
+        c = counts_all()
         n = c["n_e"] + c["n_i"]
         with torch.cuda.stream(stream):
             if flush is not None:
@@ -300,7 +368,7 @@ def run_gpu(args):
     else:
         particle_steps_all = float(particle_steps)
     value = particle_steps_all / t_max
-    final = ctx.counts()
+    final = counts_all()
 
     # Roofline of the move pass (k_push in move mode, both species): algorithmic bytes = the
     # 28 B record (u, v, vx, vy, vz, w, id) read and written once per particle, plus per leaf
@@ -328,8 +396,32 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "phase_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]}}
 
+    if ensemble and args.sequential > 0:
+        # the same instances advanced one after another, each in its own context
+        t_seq, ps_seq = 0.0, 0
+        for c_i, mesh_i, factory, _ in members[:args.sequential]:
+            with G.Context(c_i, stream_handle=stream.cuda_stream) as one:
+                one.set_mesh_dict(mesh_i)
+                parts_i = factory()
+                for s_ in sorted(parts_i):
+                    one.load(s_, **parts_i[s_])
+                one.step(args.warmup)
+                c0 = one.counts()
+                torch.cuda.synchronize()
+                with torch.cuda.stream(stream):
+                    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                one.step(args.steps)
+                with torch.cuda.stream(stream):
+                    b.record(stream)
+                b.synchronize()
+                t_seq += a.elapsed_time(b) * 1e-3
+                ps_seq += (c0["n_e"] + c0["n_i"]) * args.steps
+        line["sequential_single_instance"] = {"value": ps_seq / t_seq, "unit": METRIC,
+                                              "instances": args.sequential,
+                                              "note": "the first instances of the ensemble, each alone, same steps"}
     # end to end through the C ABI with host buffers: load (H2D) + one step + read phi (D2H)
-    if not args.no_e2e:
+    if not args.no_e2e and not ensemble:
         host = {s: {k: np.ascontiguousarray(v) for k, v in parts[s].items()} for s in parts}
         h2d = sum(v.nbytes for s in host for v in host[s].values())
         e2e_steps = 3 if streamer else max(3, min(args.steps, 10))
@@ -366,6 +458,8 @@ def main():
     ap.add_argument("--seed", type=int, default=160407713)
     ap.add_argument("--workload", default="streamer", choices=WORKLOADS)
     ap.add_argument("--particles", type=int, default=50_000_000, help="streamer workload: total particles")
+    ap.add_argument("--sequential", type=int, default=0,
+                    help="ensemble workload: also time this many instances one after another")
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

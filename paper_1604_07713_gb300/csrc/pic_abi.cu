@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <exception>
 #include <new>
 
@@ -126,20 +127,34 @@ Instance &get_inst(pic_ctx *ctx, int32_t inst) {
     return ctx->inst[inst];
 }
 
-void fields_of(pic_ctx *ctx, Instance &in, int64_t step) {
-    double walls[4];
-    walls_at(in, step, walls);
+// Field half of a step for every instance: deposits, then one batched launch for all
+// instances whose meshes fit one block (one block each), other instances one by one.
+void fields_all(pic_ctx *ctx, int64_t step) {
+    std::vector<std::array<double, 4>> walls(ctx->inst.size());
+    for (size_t i = 0; i < ctx->inst.size(); ++i) walls_at(ctx->inst[i], step, walls[i].data());
     {
         Phase ph(ctx, PIC_PHASE_DEPOSIT);
-        deposit(ctx, in, walls);
+        for (size_t i = 0; i < ctx->inst.size(); ++i) deposit(ctx, ctx->inst[i], walls[i].data());
     }
     {
         Phase ph(ctx, PIC_PHASE_POISSON);
-        poisson_solve(ctx, in, walls);
+        std::vector<Instance *> small;
+        std::vector<const double *> sw;
+        for (size_t i = 0; i < ctx->inst.size(); ++i) {
+            Instance &in = ctx->inst[i];
+            if (in.small_item) {
+                small.push_back(&in);
+                sw.push_back(walls[i].data());
+            } else {
+                poisson_solve(ctx, in, walls[i].data());
+            }
+        }
+        if (small.size() == 1) poisson_solve(ctx, *small[0], sw[0]);
+        else poisson_solve_batch(ctx, small, sw);
     }
     {
         Phase ph(ctx, PIC_PHASE_NODE_E);
-        node_e(ctx, in, walls);
+        for (size_t i = 0; i < ctx->inst.size(); ++i) node_e(ctx, ctx->inst[i], walls[i].data());
     }
 }
 
@@ -222,6 +237,7 @@ pic_status pic_destroy(pic_ctx *ctx) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    ctx->batch_mem.release_all();
     delete ctx;
     return PIC_OK;
 }
@@ -280,9 +296,10 @@ pic_status pic_compute_fields(pic_ctx *ctx) {
             if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
             ensure_species(ctx, in);
             reset_solver_stats(ctx, in);
-            fields_of(ctx, in, ctx->step);
-            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
         }
+        fields_all(ctx, ctx->step);
+        for (Instance &in : ctx->inst)
+            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
         if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
         return st;
     });
@@ -299,11 +316,9 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
         }
         pic_status st = PIC_OK;
         for (int32_t k = 0; k < n_steps; ++k) {
-            for (Instance &in : ctx->inst) {
-                ensure_capacity(ctx, in);
-                fields_of(ctx, in, ctx->step);
-                particle_step(ctx, in, ctx->step);
-            }
+            for (Instance &in : ctx->inst) ensure_capacity(ctx, in);
+            fields_all(ctx, ctx->step);
+            for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
             ++ctx->step;
         }
         for (Instance &in : ctx->inst) {

@@ -111,6 +111,8 @@ struct Instance {
     double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
     bool mg_on_device = false;     // last solve ran its loop on the device (stats below)
     double *mg_stats = nullptr;    // device: [cycles, rel. residual, max rel. since reset]
+    void *small_item = nullptr;          // meshes that fit one block: the solve's work item
+    size_t small_smem = 0;               // and its dynamic shared memory
     cudaGraphExec_t mg_cycle = nullptr;  // multi-block meshes: one captured cycle (V-cycle,
     int64_t mg_cycle_nodes = 0;          // correction, residual, norm read-back) and its launches
     DeviceArena mesh_mem;        // freed on pic_set_mesh
@@ -136,6 +138,12 @@ struct pic_ctx {
     std::vector<cudaEvent_t> event_pool;
     std::vector<gbpic::Instance> inst;
     int precision = PIC_FP32;
+    // batched one-block Poisson solves (instances whose meshes fit one block)
+    int64_t mesh_epoch = 0, batch_epoch = -1;
+    int batch_n = 0;
+    void *batch_items = nullptr;
+    size_t batch_smem = 0;
+    gbpic::DeviceArena batch_mem;
 };
 
 namespace gbpic {
@@ -216,6 +224,8 @@ void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_de
 // pic_poisson.cu
 void poisson_setup(pic_ctx *ctx, Instance &in);
 void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]);
+void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list,
+                         const std::vector<const double *> &walls);
 // pic_particles.cu
 void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap);
 void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *x,

@@ -216,9 +216,13 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t n_old = a.start[a.nleaf];
+    // persistent warps: the next leaf's list offsets are fetched while this leaf runs
+    int32_t np0 = 0, np1 = 0;
+    if (warp < a.nleaf) { np0 = a.start[warp]; np1 = a.start[warp + 1]; }
     for (int64_t Lw = warp; Lw < a.nleaf; Lw += nw) {
         const int32_t L = (int32_t)Lw;
-        const int32_t p0 = a.start[L], p1 = a.start[L + 1];
+        const int32_t p0 = np0, p1 = np1;
+        if (Lw + nw < a.nleaf) { np0 = a.start[Lw + nw]; np1 = a.start[Lw + nw + 1]; }
         if (p0 == p1) {
             if (lane == 0) {
                 if (a.mode == 0) { a.stay[L] = 0; if (a.spawn) a.spawn[L] = 0; }
@@ -771,6 +775,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     const int nsp = in.cfg.n_species;
     const int64_t nl = in.nleaf;
     const unsigned wb = warp_blocks(nl);
+    // the push kernel runs persistent warps: 4 resident blocks per SM (64 registers)
+    const unsigned pb = std::min<unsigned>(wb, 152u * 4u);
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
@@ -787,7 +793,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                 a.spawn = e.spawn;
                 a.inc_ion = ion ? ion->inc : nullptr;
             }
-            k_push<R><<<wb, kT, 0, st>>>(a);
+            k_push<R><<<pb, kT, 0, st>>>(a);
             count_launch(ctx);
         }
     }
@@ -819,7 +825,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                     a.ion_fill = ion->fill;
                 }
             }
-            k_push<R><<<wb, kT, 0, st>>>(a);
+            k_push<R><<<pb, kT, 0, st>>>(a);
             count_launch(ctx);
         }
         if (ionize) {

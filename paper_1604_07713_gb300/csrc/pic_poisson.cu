@@ -575,15 +575,45 @@ __global__ void __launch_bounds__(1024, 1) k_tail_vcycle(SmallDesc D, const floa
 }
 
 // Whole solve for a mesh whose every level fits: FP64 residual and correction, FP32 V-cycles
-// in shared memory, convergence test on the device.  stats: [cycles, rel. residual, max rel.]
-__global__ void __launch_bounds__(1024, 1) k_small_solve(SmallDesc D, const double *__restrict__ diag64,
-                                                       const double *__restrict__ val64, double *__restrict__ phi,
-                                                       double *__restrict__ bvec, const uint8_t *__restrict__ lev,
-                                                       int lmax, int singular, double tol, int maxc,
-                                                       double *__restrict__ stats) {
+// in shared memory, convergence test on the device.  One block per item, so a batch of
+// instances solves in one launch.  stats: [cycles, rel. residual, max rel. since reset].
+struct SmallSolve {
+    SmallDesc D;
+    const double *diag64, *val64;
+    double *phi, *phi_prev, *bvec, *stats;
+    const uint8_t *lev;
+    int32_t *n_solves;  // device counter: the warm start extrapolates once two solves exist
+    int lmax, singular, maxc;
+    double tol;
+};
+
+__global__ void __launch_bounds__(1024, 1) k_small_solve(const SmallSolve *__restrict__ items) {
     extern __shared__ float sm[];
     __shared__ double red[33];
     __shared__ float redf[33];
+    __shared__ SmallDesc D;
+    const SmallSolve &it = items[blockIdx.x];
+    if (threadIdx.x == 0) D = it.D;
+    __syncthreads();
+    const double *__restrict__ diag64 = it.diag64;
+    const double *__restrict__ val64 = it.val64;
+    double *__restrict__ phi = it.phi;
+    double *__restrict__ bvec = it.bvec;
+    const uint8_t *__restrict__ lev = it.lev;
+    const int lmax = it.lmax, singular = it.singular, maxc = it.maxc;
+    const double tol = it.tol;
+    double *stats = it.stats;
+    {
+        const int ns = *it.n_solves;
+        if (ns >= 1)
+            for (int i = threadIdx.x; i < D.lv[0].n; i += blockDim.x) {
+                const double p = phi[i];
+                if (ns >= 2) phi[i] = 2.0 * p - it.phi_prev[i];
+                it.phi_prev[i] = p;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) *it.n_solves = ns + 1;
+    }
     const SmallLevel &L = D.lv[0];
     const int n = L.n;
     if (singular) {  // right-hand side compatibility: remove an area-proportional share
@@ -762,6 +792,52 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     // coarsest-level CG needs three extra vectors: give it its own buffers
     Level &c = in.lv.back();
     c.t = dalloc<float>(A, 3 * c.n + 16);
+    // meshes whose every level fits one block: the whole solve is one block's work item
+    in.small_item = nullptr;
+    if (small_from(in) == 0) {
+        SmallSolve it{};
+        it.D = small_desc(in, 0);
+        Level &L = in.lv[0];
+        it.diag64 = L.diag64; it.val64 = L.val64;
+        it.phi = in.phi; it.phi_prev = in.phi_prev; it.bvec = in.bvec; it.stats = in.mg_stats;
+        it.lev = L.lev; it.lmax = L.lmax;
+        it.singular = (in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC) ? 1 : 0;
+        it.maxc = std::max(1, in.cfg.mg_max_cycles);
+        it.tol = in.cfg.mg_rel_tol;
+        int32_t *ns = dalloc<int32_t>(A, 1);
+        GB_CUDA(cudaMemsetAsync(ns, 0, 4, ctx->stream));
+        it.n_solves = ns;
+        SmallSolve *d = (SmallSolve *)A.alloc(sizeof(SmallSolve));
+        GB_CUDA(cudaMemcpyAsync(d, &it, sizeof(SmallSolve), cudaMemcpyHostToDevice, ctx->stream));
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        in.small_item = d;
+        in.small_smem = (size_t)it.D.smem_floats * 4;
+    }
+    ++ctx->mesh_epoch;
+}
+
+// One launch for every instance whose mesh fits one block: block b solves instance b.
+void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list, const std::vector<const double *> &walls) {
+    if (list.empty()) return;
+    if (ctx->batch_epoch != ctx->mesh_epoch || ctx->batch_n != (int)list.size()) {
+        ctx->batch_mem.release_all();
+        ctx->batch_items = ctx->batch_mem.alloc(list.size() * sizeof(SmallSolve));
+        ctx->batch_smem = 0;
+        for (size_t k = 0; k < list.size(); ++k) {
+            GB_CUDA(cudaMemcpyAsync((SmallSolve *)ctx->batch_items + k, list[k]->small_item, sizeof(SmallSolve),
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+            ctx->batch_smem = std::max(ctx->batch_smem, list[k]->small_smem);
+        }
+        ctx->batch_epoch = ctx->mesh_epoch;
+        ctx->batch_n = (int)list.size();
+    }
+    for (size_t k = 0; k < list.size(); ++k) {
+        for (int w = 0; w < 4; ++w) list[k]->last_walls[w] = walls[k][w];
+        list[k]->mg_on_device = true;
+    }
+    k_small_solve<<<(unsigned)list.size(), 1024, ctx->batch_smem, ctx->stream>>>((const SmallSolve *)ctx->batch_items);
+    count_launch(ctx);
+    check_launch("poisson_solve_batch");
 }
 
 // Solve A phi = bvec to ||r|| <= mg_rel_tol ||b||, warm-started from the current phi.
@@ -771,21 +847,18 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     cudaStream_t s = ctx->stream;
     const int64_t n = L.n;
     const bool singular = in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC;
-    if (in.n_solves >= 1) {
-        k_extrapolate<<<blocks_for(n), kT, 0, s>>>(n, in.phi, in.phi_prev, in.n_solves >= 2 ? 1 : 0);
-        count_launch(ctx);
-    }
-    ++in.n_solves;
-    if (small_from(in) == 0) {
-        const SmallDesc D = small_desc(in, 0);
-        k_small_solve<<<1, 1024, (size_t)D.smem_floats * 4, s>>>(D, L.diag64, L.val64, in.phi, in.bvec, L.lev, L.lmax,
-                                                                 singular ? 1 : 0, in.cfg.mg_rel_tol,
-                                                                 std::max(1, in.cfg.mg_max_cycles), in.mg_stats);
+    if (in.small_item) {
+        k_small_solve<<<1, 1024, (size_t)in.small_smem, s>>>((const SmallSolve *)in.small_item);
         count_launch(ctx);
         check_launch("poisson_solve");
         in.mg_on_device = true;
         return;
     }
+    if (in.n_solves >= 1) {
+        k_extrapolate<<<blocks_for(n), kT, 0, s>>>(n, in.phi, in.phi_prev, in.n_solves >= 2 ? 1 : 0);
+        count_launch(ctx);
+    }
+    ++in.n_solves;
     in.mg_on_device = false;
     if (singular) {
         k_area_moments<<<kRedBlocks, kT, 0, s>>>(n, L.lev, L.lmax, in.bvec, in.red);

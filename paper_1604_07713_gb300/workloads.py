@@ -265,3 +265,29 @@ def streamer_snapshot(n_particles=50_000_000, nx0=128, lmax=4, seed=DEFAULT_SEED
                       phi_right=e0 * box, e_ref=e0, adapt_every=10, mg_rel_tol=1e-8)
     mesh = dict(nx0=nx0, ny0=nx0, h0=h0, lmax=lmax)
     return cfg, mesh, parts
+
+
+def ensemble(n_instances=256, seed=DEFAULT_SEED, precision=FP32, lx_per_cell=0.067 / 512):
+    """Batched capacitively coupled discharges of uneven size: per instance x-cells drawn
+    from {64, 80, ..., 512} (multiples of 16 so that the root grid coarsens), 16 y-cells,
+    20-200 macro-particles per cell and species, RF amplitude 100-400 V, gas density
+    log-uniform in 3e20-3e21 m^-3, otherwise the CCP physics; each instance has its own
+    seed and Philox instance word.  Returns a list of (cfg, mesh, parts_factory) where
+    parts_factory() draws that instance's particles (so the host holds one at a time)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_instances):
+        nx = int(rng.integers(4, 33)) * 16
+        ppc = int(rng.integers(20, 201))
+        volt = float(rng.uniform(100.0, 400.0))
+        ng = float(np.exp(rng.uniform(np.log(3e20), np.log(3e21))))
+        s_i = int(rng.integers(0, 2**31))
+        def factory(nx=nx, ppc=ppc, volt=volt, ng=ng, s_i=s_i):
+            return ccp(nx=nx, ny=16, ppc=ppc, lx=lx_per_cell * nx, seed=s_i, precision=precision,
+                       volt=volt, ng=ng)[2]
+        cfg, mesh, _ = ccp(nx=nx, ny=16, ppc=1, lx=lx_per_cell * nx, seed=s_i, precision=precision,
+                           volt=volt, ng=ng)
+        cfg["instance"] = i % 256
+        cfg["mg_rel_tol"] = 1e-8
+        out.append((cfg, mesh, factory, nx * 16 * ppc * 2))
+    return out
