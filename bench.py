@@ -46,11 +46,14 @@ def _dist():
     return ws, rank
 
 
-def _workload(seed, name="ccp", n_particles=50_000_000):
+PRECISION = {"fp32": 0, "fp64": 1}
+
+
+def _workload(seed, name="ccp", n_particles=50_000_000, precision="fp32"):
     from paper_1604_07713_gb300 import workloads as W
     if name == "streamer":
-        return W.streamer_snapshot(n_particles=n_particles, seed=seed, precision=W.FP32)
-    cfg, mesh, parts = W.ccp(seed=seed, precision=W.FP32)
+        return W.streamer_snapshot(n_particles=n_particles, seed=seed, precision=PRECISION[precision])
+    cfg, mesh, parts = W.ccp(seed=seed, precision=PRECISION[precision])
     cfg["mg_rel_tol"] = 1e-8
     return cfg, mesh, parts
 
@@ -294,7 +297,7 @@ def run_gpu(args):
         n_inst = len(members)
         mesh, parts = members[0][1], None
     else:
-        cfg, mesh, parts = _workload(args.seed + rank, name, args.particles)
+        cfg, mesh, parts = _workload(args.seed + rank, name, args.particles, args.precision)
         ctx = G.Context(cfg, stream_handle=stream.cuda_stream)
         ctx.set_mesh_dict(mesh)
         for s in sorted(parts):
@@ -373,25 +376,27 @@ def run_gpu(args):
     # Roofline of the move pass (k_push in move mode, both species): algorithmic bytes = the
     # 28 B record (u, v, vx, vy, vz, w, id) read and written once per particle, plus per leaf
     # the 8 corner field values and two list offsets (old, new) of each species.
-    rs = 4
+    rs = 8 if args.precision == "fp64" else 4
     move_ms, move_launches = phases["move"]
     move_s = move_ms * 1e-3
     alg_bytes = 2 * 7 * rs * particle_steps + leaf_steps * (8 * rs + 2 * 2 * 4)
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
-    tr = _traffic_record(name)
+    tr = _traffic_record(name) if args.precision == "fp32" else None
     tot_ms = sum(v[0] for v in phases.values())
-    roofline = {"bound": "hbm", "kernel": "k_push<float> move pass (both species)", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": f"k_push<{'double' if rs == 8 else 'float'}> move pass (both species)",
+                "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": tr["move_dram_bytes_per_step"] if tr else None,
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_step": alg_bytes / args.steps,
                 "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items() if v[1]}}
-    extra = {"particles_mean": int(particle_steps / args.steps),
+    extra = {"precision": f"{args.precision} particle state and push, fp64 Poisson residual",
+             "particles_mean": int(particle_steps / args.steps),
              "particles_end": int(final["n_e"] + final["n_i"]), "leaves_end": int(final["n_leaves"]),
              "poisson_cycles_last": int(final["mg_cycles"])}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32", "data": "synthetic",
             "config": _config_json(ws, name, extra), "roofline": roofline, "clocks": clocks,
             "gpu_launches": int(launches),
             "phase_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]}}
@@ -458,6 +463,8 @@ def main():
     ap.add_argument("--seed", type=int, default=160407713)
     ap.add_argument("--workload", default="streamer", choices=WORKLOADS)
     ap.add_argument("--particles", type=int, default=50_000_000, help="streamer workload: total particles")
+    ap.add_argument("--precision", default="fp32", choices=tuple(PRECISION),
+                    help="particle state and push arithmetic (ccp and streamer workloads)")
     ap.add_argument("--sequential", type=int, default=0,
                     help="ensemble workload: also time this many instances one after another")
     ap.add_argument("--cpu-steps", type=int, default=12)
