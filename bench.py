@@ -373,24 +373,29 @@ def run_gpu(args):
     value = particle_steps_all / t_max
     final = counts_all()
 
-    # Roofline of the move pass (k_push in move mode, both species): algorithmic bytes = the
-    # 28 B record (u, v, vx, vy, vz, w, id) read and written once per particle, plus per leaf
-    # the 8 corner field values and two list offsets (old, new) of each species.
+    # Roofline of the fused push (k_push, both species, lists updated in place): algorithmic
+    # bytes = the record (u, v, vx, vy, vz, w, id) read once and its five changed words
+    # (u, v, vx, vy, vz) written once per particle, plus per leaf and species the 8 corner
+    # field values, the list bounds (start, end) and the staying count and weight sum written.
+    # The extra words of records that change slot (w, id, order key) are not counted.
     rs = 8 if args.precision == "fp64" else 4
     move_ms, move_launches = phases["move"]
     move_s = move_ms * 1e-3
-    alg_bytes = 2 * 7 * rs * particle_steps + leaf_steps * (8 * rs + 2 * 2 * 4)
+    alg_bytes = 12 * rs * particle_steps + leaf_steps * 2 * (10 * rs + 12)
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
     tr = _traffic_record(name) if args.precision == "fp32" else None
     tot_ms = sum(v[0] for v in phases.values())
-    roofline = {"bound": "hbm", "kernel": f"k_push<{'double' if rs == 8 else 'float'}> move pass (both species)",
+    roofline = {"bound": "hbm", "kernel": f"k_push<{'double' if rs == 8 else 'float'}> in-place push (both species)",
                 "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": tr["move_dram_bytes_per_step"] if tr else None,
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_step": alg_bytes / args.steps,
                 "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items() if v[1]}}
+    list_stats = [G.pic_get_list_stats(ctx.ctx, 0, s_) for s_ in range(cfg["n_species"])]
     extra = {"precision": f"{args.precision} particle state and push, fp64 Poisson residual",
+             "list_relayouts_since_load": [r for r, _, _ in list_stats],
+             "list_tail_moves_since_load": [m for _, m, _ in list_stats],
              "particles_mean": int(particle_steps / args.steps),
              "particles_end": int(final["n_e"] + final["n_i"]), "leaves_end": int(final["n_leaves"]),
              "poisson_cycles_last": int(final["mg_cycles"])}

@@ -205,6 +205,18 @@ GBPIC_API pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches,
 /* Total kernel launches issued by the context since creation. */
 GBPIC_API pic_status pic_get_launch_count(const pic_ctx *ctx, int64_t *launches);
 
+/* Cell-list bookkeeping of one species (§3.1 list update; no counterpart in the paper's
+ * numbers).  Each leaf's list keeps free slots for particles that enter it during a step.
+ * A leaf that receives more entering particles than it has free slots moves to a fresh
+ * segment at the tail of the species' buffer (`tail_moves` counts these moves); when the
+ * tail is used up, every list of the species is laid out again with fresh free slots
+ * (`relayouts` counts the steps that needed it).  `overflowed` = entering records that
+ * found no free slot.  All three count since the species was last loaded.  Any pointer may
+ * be null.  Synchronizes the context's stream.  Errors: PIC_EINVAL (bad instance or
+ * species). */
+GBPIC_API pic_status pic_get_list_stats(pic_ctx *ctx, int32_t inst, int32_t species, int64_t *relayouts,
+                                        int64_t *tail_moves, int64_t *overflowed);
+
 /* |E| at the leaf centres of instance `inst`, exactly as pic_read_fields(PIC_FIELD_EMAG), for
  * callers that cannot allocate device memory: code that runs while another thread captures a
  * CUDA graph in global capture mode (where cudaMalloc is refused), callers whose device memory

@@ -30,7 +30,7 @@ PIC_N_PHASES = len(PHASES)
 EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_load_particles",
             "pic_step", "pic_compute_fields", "pic_adapt", "pic_read_fields", "pic_read_mesh",
             "pic_read_particles", "pic_get_counts", "pic_get_step", "pic_set_step",
-            "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_read_emag_noalloc",
+            "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_get_list_stats", "pic_read_emag_noalloc",
             "pic_last_error"]
 
 
@@ -109,6 +109,7 @@ def _declare(L):
         "pic_get_counts": [_p, _i32, _p, _p, _p, _p, _p], "pic_get_step": [_p, _p],
         "pic_set_step": [_p, _i64], "pic_set_timing": [_p, _i32],
         "pic_get_timing": [_p, _p, _p, _i32], "pic_get_launch_count": [_p, _p],
+        "pic_get_list_stats": [_p, _i32, _i32, _p, _p, _p],
         "pic_read_emag_noalloc": [_p, _i32, _p, _i64, _p],
     }
     for name, args in sig.items():
@@ -239,6 +240,13 @@ def pic_get_timing(ctx):
     ms = np.zeros(PIC_N_PHASES); ln = np.zeros(PIC_N_PHASES, np.int64)
     _call("pic_get_timing", ctx, _ptr(ms), _ptr(ln), PIC_N_PHASES)
     return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(PHASES)}
+
+
+def pic_get_list_stats(ctx, inst=0, species=0):
+    """(relayouts, tail_moves, overflowed records) of one species' cell lists since its load."""
+    r, m, o = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _call("pic_get_list_stats", ctx, inst, species, C.byref(r), C.byref(m), C.byref(o))
+    return r.value, m.value, o.value
 
 
 def pic_get_launch_count(ctx):

@@ -39,12 +39,74 @@ void check_launch(const char *what) {
     if (e != cudaSuccess) throw Failure(PIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+namespace {
+// Size classes 1/8 of a power of two apart, so a buffer that grows or shrinks by a few
+// percent between mesh rebuilds lands on a block it used before.
+size_t size_class(size_t b) {
+    b = std::max<size_t>(b, 256);
+    int e = 63 - __builtin_clzll((unsigned long long)b);
+    const size_t g = e >= 3 ? (size_t)1 << (e - 3) : 1;
+    return (b + g - 1) / g * g;
+}
+constexpr size_t kCacheMaxBlock = (size_t)512 << 20;  // larger blocks are freed, not cached
+constexpr size_t kCacheMaxIdle = (size_t)4 << 30;     // idle bytes kept at most
+
+void *raw_alloc(size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+}  // namespace
+
+void *BlockCache::get(size_t bytes) {
+    const size_t c = size_class(bytes);
+    auto it = idle.lower_bound(c);
+    if (it != idle.end() && it->first <= c + c / 4) {
+        void *p = it->second;
+        idle_bytes -= it->first;
+        idle.erase(it);
+        return p;
+    }
+    void *p = raw_alloc(c);
+    if (!p) {  // give the idle blocks back to the driver and try once more
+        trim();
+        p = raw_alloc(c);
+    }
+    if (!p) throw Failure(PIC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed");
+    cls[p] = c;
+    return p;
+}
+void BlockCache::put(void *p) {
+    auto it = cls.find(p);
+    if (it == cls.end()) return;
+    if (it->second > kCacheMaxBlock) {
+        cudaFree(p);
+        cls.erase(it);
+        return;
+    }
+    idle.emplace(it->second, p);
+    idle_bytes += it->second;
+    if (idle_bytes > kCacheMaxIdle) trim();
+}
+void BlockCache::trim() {
+    for (auto &e : idle) {
+        cudaFree(e.second);
+        cls.erase(e.second);
+    }
+    idle.clear();
+    idle_bytes = 0;
+}
+
 void *DeviceArena::alloc(size_t bytes) {
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Failure(PIC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed");
+    if (cache) {
+        p = cache->get(bytes);
+    } else {
+        p = raw_alloc(std::max<size_t>(bytes, 16));
+        if (!p) throw Failure(PIC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed");
     }
     blocks.push_back(p);
     return p;
@@ -52,12 +114,16 @@ void *DeviceArena::alloc(size_t bytes) {
 void DeviceArena::release(void *p) {
     auto it = std::find(blocks.begin(), blocks.end(), p);
     if (it != blocks.end()) {
-        cudaFree(p);
+        if (cache) cache->put(p);
+        else cudaFree(p);
         blocks.erase(it);
     }
 }
 void DeviceArena::release_all() {
-    for (void *p : blocks) cudaFree(p);
+    for (void *p : blocks) {
+        if (cache) cache->put(p);
+        else cudaFree(p);
+    }
     blocks.clear();
 }
 
@@ -199,9 +265,13 @@ pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out)
         ctx = new pic_ctx();
         GB_CUDA(cudaGetDevice(&ctx->device));
         ctx->inst.resize(n_instances);
+        ctx->batch_mem.cache = &ctx->cache;
         for (int i = 0; i < n_instances; ++i) {
             Instance &in = ctx->inst[i];
             in.cfg = cfg[i];
+            in.mesh_mem.cache = &ctx->cache;
+            in.part_mem[0].cache = &ctx->cache;
+            in.part_mem[1].cache = &ctx->cache;
             GB_CUDA(cudaMallocHost(&in.red_host, 64));
             GB_CUDA(cudaMallocHost(&in.cnt_host, 64));
             GB_CUDA(cudaMalloc(&in.d_next_id, 8));
@@ -238,6 +308,8 @@ pic_status pic_destroy(pic_ctx *ctx) {
         cudaEventDestroy(r.b);
     }
     ctx->batch_mem.release_all();
+    ctx->cache.trim();
+    for (auto &e : ctx->cache.cls) cudaFree(e.first);  // blocks an arena still held
     delete ctx;
     return PIC_OK;
 }
@@ -245,6 +317,8 @@ pic_status pic_destroy(pic_ctx *ctx) {
 pic_status pic_set_stream(pic_ctx *ctx, void *stream) {
     return guarded(ctx, [&]() -> pic_status {
         if (!ctx) fail(PIC_EINVAL, "null context");
+        // cached blocks may still be read by work queued on the old stream
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
         ctx->stream = (cudaStream_t)stream;
         return PIC_OK;
     });
@@ -322,13 +396,21 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
             ++ctx->step;
         }
         for (Instance &in : ctx->inst) {
-            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+            // exact record totals (the next steps' capacity bound) and the consistency flag
+            count_totals(ctx, in);
+            for (int s = 0; s < in.cfg.n_species; ++s)
+                GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].flags + 1, 4, cudaMemcpyDeviceToHost,
+                                        ctx->stream));
             GB_CUDA(cudaMemcpyAsync(in.cnt_host + 8, in.d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
-            GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (Instance &in : ctx->inst) {
+            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
             if (in.cnt_host[8] != 0) {
                 ctx->poisoned = true;
-                fail(PIC_ESTATE, "particle bookkeeping mismatch between count and move passes");
+                fail(PIC_ESTATE, "particle bookkeeping violated a slot bound (overflow store or re-layout)");
             }
+            for (int s = 0; s < in.cfg.n_species; ++s) in.sp[s].n = in.sp[s].n_upper = in.cnt_host[s];
         }
         if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
         return st;
@@ -388,10 +470,11 @@ pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *ou
                 std::fill(out, out + nl, 0.0);
                 break;
             }
-            std::vector<int32_t> st0(nl + 1);
-            GB_CUDA(cudaMemcpyAsync(st0.data(), in.sp[s].start, (nl + 1) * 4, cudaMemcpyDeviceToHost, st));
+            std::vector<int32_t> st0(nl), en0(nl);
+            GB_CUDA(cudaMemcpyAsync(st0.data(), in.sp[s].start, nl * 4, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaMemcpyAsync(en0.data(), in.sp[s].end, nl * 4, cudaMemcpyDeviceToHost, st));
             GB_CUDA(cudaStreamSynchronize(st));
-            for (int64_t l = 0; l < nl; ++l) out[l] = (double)(st0[l + 1] - st0[l]);
+            for (int64_t l = 0; l < nl; ++l) out[l] = (double)(en0[l] - st0[l]);
             break;
         }
         case PIC_FIELD_NODE_E:
@@ -406,7 +489,7 @@ pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *ou
             }
             break;
         case PIC_FIELD_EMAG: {
-            DeviceArena tmp;
+            DeviceArena tmp(&ctx->cache);
             double *d = dalloc<double>(tmp, nl);
             double walls[4];
             walls_at(in, ctx->step, walls);
@@ -447,12 +530,29 @@ pic_status pic_read_particles(pic_ctx *ctx, int32_t inst, int32_t species, doubl
         if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
         ensure_species(ctx, in);
         Species &sp = in.sp[species];
-        GB_CUDA(cudaMemcpyAsync(in.cnt_host, sp.start + in.nleaf, 4, cudaMemcpyDeviceToHost, ctx->stream));
-        GB_CUDA(cudaStreamSynchronize(ctx->stream));
-        sp.n = sp.n_upper = in.cnt_host[0];
+        refresh_counts(ctx, in);
         if (n_out) *n_out = sp.n;
         if (cap < sp.n) fail(PIC_EINVAL, "output capacity too small");
         particles_read(ctx, in, species, x, y, vx, vy, vz, w, id, leaf);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_get_list_stats(pic_ctx *ctx, int32_t inst, int32_t species, int64_t *relayouts,
+                              int64_t *tail_moves, int64_t *overflowed) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (species < 0 || species >= in.cfg.n_species) fail(PIC_EINVAL, "species out of range");
+        Species &sp = in.sp[species];
+        int32_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (sp.flags) {
+            GB_CUDA(cudaMemcpyAsync(in.cnt_host + 8, sp.flags, 8 * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GB_CUDA(cudaStreamSynchronize(ctx->stream));
+            for (int k = 0; k < 8; ++k) h[k] = in.cnt_host[8 + k];
+        }
+        if (relayouts) *relayouts = h[2];
+        if (tail_moves) *tail_moves = h[6];
+        if (overflowed) *overflowed = h[3];
         return PIC_OK;
     });
 }
@@ -462,17 +562,9 @@ pic_status pic_get_counts(pic_ctx *ctx, int32_t inst, int64_t *n_leaves, int64_t
     return guarded(ctx, [&]() -> pic_status {
         Instance &in = get_inst(ctx, inst);
         int64_t c[2] = {0, 0};
-        for (int s = 0; s < in.cfg.n_species; ++s) {
-            if (!in.sp[s].start) continue;
-            GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].start + in.nleaf, 4, cudaMemcpyDeviceToHost,
-                                    ctx->stream));
-        }
-        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        refresh_counts(ctx, in);
         for (int s = 0; s < in.cfg.n_species; ++s)
-            if (in.sp[s].start) {
-                c[s] = in.cnt_host[s];
-                in.sp[s].n = in.sp[s].n_upper = c[s];
-            }
+            if (in.sp[s].start) c[s] = in.sp[s].n;
         collect_solver_stats(ctx, in);
         if (n_leaves) *n_leaves = in.nleaf;
         if (n_e) *n_e = c[0];

@@ -31,14 +31,14 @@ struct AdaptArgs {
     int lmax;
     const uint8_t *lev;
     const uint32_t *root, *morton;
-    const int32_t *start_e;  // electron list offsets
+    const int32_t *start_e, *end_e;  // electron lists
     const double *emag;
     int32_t refine_count, coarsen_count;
     double refine_e, coarsen_e;
 };
 
 __device__ __forceinline__ bool wants_refine(const AdaptArgs &a, int64_t l) {
-    const int32_t c = a.start_e[l + 1] - a.start_e[l];
+    const int32_t c = a.end_e[l] - a.start_e[l];
     return a.lev[l] < a.lmax && (c > a.refine_count || a.emag[l] > a.refine_e);
 }
 
@@ -67,7 +67,7 @@ __global__ void k_adapt_flags(AdaptArgs a, int32_t *__restrict__ refine, int32_t
         int64_t tot = 0;
         for (int k = 0; k < 4; ++k) {
             ok = ok && !wants_refine(a, l + k) && a.emag[l + k] < a.coarsen_e;
-            tot += a.start_e[l + k + 1] - a.start_e[l + k];
+            tot += a.end_e[l + k] - a.start_e[l + k];
         }
         gactive[l] = (ok && tot <= a.coarsen_count) ? 1 : 0;
     }
@@ -164,38 +164,30 @@ __global__ void k_adapt_emit(int64_t n, const int32_t *__restrict__ refine, cons
     }
 }
 
-template <typename R> struct SoA {
-    R *u, *v, *vx, *vy, *vz, *w;
-    uint32_t *id;
-};
-template <typename R> SoA<R> soa(Species &sp, int buf) {
-    SoA<R> a;
-    a.u = (R *)sp.arr[buf][0]; a.v = (R *)sp.arr[buf][1]; a.vx = (R *)sp.arr[buf][2];
-    a.vy = (R *)sp.arr[buf][3]; a.vz = (R *)sp.arr[buf][4]; a.w = (R *)sp.arr[buf][5];
-    a.id = sp.id[buf];
-    return a;
-}
-
 // Particle counts of the new leaves (one warp per old leaf).
 template <typename R>
-__global__ void k_adapt_count(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ kind,
-                              const int32_t *__restrict__ group, const int32_t *__restrict__ new_of,
-                              SoA<R> d, int32_t *__restrict__ ncnt) {
+__global__ void k_adapt_count(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                              const int32_t *__restrict__ kind, const int32_t *__restrict__ group,
+                              const int32_t *__restrict__ new_of, SoA<R> d, int32_t *__restrict__ ncnt) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t l = warp; l < n; l += nw) {
         const int k = kind[l];
         if (k == 0) {
-            if (lane == 0) ncnt[new_of[l]] = start[l + 1] - start[l];
+            if (lane == 0) ncnt[new_of[l]] = end[l] - start[l];
         } else if (k == 2) {
-            if (lane == 0 && group[l] == (int32_t)l) ncnt[new_of[l]] = start[l + 4] - start[l];
+            if (lane == 0 && group[l] == (int32_t)l) {
+                int32_t c = 0;
+                for (int i = 0; i < 4; ++i) c += end[l + i] - start[l + i];
+                ncnt[new_of[l]] = c;
+            }
         } else {
             int32_t c4[4] = {0, 0, 0, 0};
-            for (int32_t p0 = start[l]; p0 < start[l + 1]; p0 += 32) {
+            for (int32_t p0 = start[l]; p0 < end[l]; p0 += 32) {
                 const int32_t p = p0 + lane;
                 int ch = -1;
-                if (p < start[l + 1]) ch = (d.u[p] >= (R)0.5 ? 1 : 0) + (d.v[p] >= (R)0.5 ? 2 : 0);
+                if (p < end[l]) ch = (d.u[p] >= (R)0.5 ? 1 : 0) + (d.v[p] >= (R)0.5 ? 2 : 0);
                 for (int c = 0; c < 4; ++c) c4[c] += __popc(__ballot_sync(0xFFFFFFFFu, ch == c));
             }
             if (lane == 0)
@@ -204,18 +196,27 @@ __global__ void k_adapt_count(int64_t n, const int32_t *__restrict__ start, cons
     }
 }
 
-// Move the records to the new lists; offsets re-expressed exactly in the new leaf.
+// Move the records to the new lists; offsets re-expressed exactly in the new leaf.  A
+// coarsened quartet's list is its children's lists one after another in Morton order.
 template <typename R>
-__global__ void k_adapt_move(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ kind,
-                             const int32_t *__restrict__ group, const int32_t *__restrict__ new_of,
-                             const uint32_t *__restrict__ morton, const int32_t *__restrict__ nstart, SoA<R> s,
-                             SoA<R> d) {
+__global__ void k_adapt_move(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                             const int32_t *__restrict__ kind, const int32_t *__restrict__ group,
+                             const int32_t *__restrict__ new_of, const uint32_t *__restrict__ morton,
+                             const int32_t *__restrict__ nstart, SoA<R> s, SoA<R> d) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t l = warp; l < n; l += nw) {
         const int k = kind[l];
-        const int32_t p0 = start[l], p1 = start[l + 1];
+        const int32_t p0 = start[l], p1 = end[l];
+        int32_t q0 = 0;  // first slot of this leaf's records in the new list
+        if (k == 0) {
+            q0 = nstart[new_of[l]];
+        } else if (k == 2) {
+            const int32_t g = group[l];
+            q0 = nstart[new_of[l]];
+            for (int32_t i = g; i < (int32_t)l; ++i) q0 += end[i] - start[i];
+        }
         int32_t run[4] = {0, 0, 0, 0};
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
@@ -228,11 +229,10 @@ __global__ void k_adapt_move(int64_t n, const int32_t *__restrict__ start, const
                 v = s.v[p];
             }
             if (k == 0) {
-                dst = nstart[new_of[l]] + (p - p0);
+                dst = q0 + (p - p0);
             } else if (k == 2) {
-                const int32_t g = group[l];
                 const R cx = (R)(morton[l] & 1u), cy = (R)((morton[l] >> 1) & 1u);
-                dst = nstart[new_of[l]] + (p - start[g]);
+                dst = q0 + (p - p0);
                 u = (cx + u) * (R)0.5;
                 v = (cy + v) * (R)0.5;
             } else {
@@ -262,7 +262,7 @@ __global__ void k_adapt_move(int64_t n, const int32_t *__restrict__ start, const
 // ------------------------------------------------------------------------------------
 struct SMArgs {
     int64_t n;
-    const int32_t *start;
+    const int32_t *start, *end;
     int32_t ppc_min, ppc_max, ppc_target;
 };
 
@@ -277,7 +277,7 @@ __global__ void k_sm_count(SMArgs a, int32_t *__restrict__ ncnt, int32_t *__rest
                            int32_t *__restrict__ merge_flag) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= a.n) return;
-    const int32_t c = a.start[l + 1] - a.start[l];
+    const int32_t c = a.end[l] - a.start[l];
     int32_t nc = c, ni = 0, mf = 0;
     if (c > 0 && c < a.ppc_min) {
         const int r = split_rounds(c, a.ppc_min);
@@ -300,7 +300,7 @@ __global__ void k_sm_write(SMArgs a, const int32_t *__restrict__ nstart, const i
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t l = warp; l < a.n; l += nw) {
-        const int32_t p0 = a.start[l], p1 = a.start[l + 1], c = p1 - p0;
+        const int32_t p0 = a.start[l], p1 = a.end[l], c = p1 - p0;
         if (c == 0 || c > a.ppc_max) continue;
         const int32_t q0 = nstart[l];
         if (c >= a.ppc_min) {
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(512) k_sm_merge(SMArgs a, const int32_t *__res
     __shared__ R red_lo[16], red_hi[16];
     for (int32_t mi = blockIdx.x; mi < nm; mi += gridDim.x) {
         const int32_t l = mlist[mi];
-        const int32_t p0 = a.start[l], c = a.start[l + 1] - p0;
+        const int32_t p0 = a.start[l], c = a.end[l] - p0;
         if (c > kMergeMax) {
             if (threadIdx.x == 0) atomicExch(err, 1);
             continue;
@@ -461,27 +461,14 @@ int32_t read_i32(pic_ctx *ctx, const int32_t *d) {
 }
 
 // Re-allocate one species' per-leaf arrays for a new leaf count; the records stay.
-void species_relist(pic_ctx *ctx, Instance &in, int s, int64_t nl, const int32_t *new_start) {
+void species_relist(pic_ctx *ctx, Instance &in, int s, int64_t nl, const int32_t *new_start,
+                    const int32_t *new_end) {
     Species &sp = in.sp[s];
-    DeviceArena &A = in.part_mem[s];
-    void *olds[10] = {sp.start, sp.start_new, sp.stay, sp.inc, sp.fill, sp.spawn, sp.spawn_base,
-                      sp.stay_hi, sp.stay_lo, sp.wsum};
-    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
-    sp.start = dalloc<int32_t>(A, nl + 1);
-    sp.start_new = dalloc<int32_t>(A, nl + 1);
-    sp.stay = dalloc<int32_t>(A, nl + 1);
-    sp.inc = dalloc<int32_t>(A, nl + 1);
-    sp.fill = dalloc<int32_t>(A, nl + 1);
-    sp.spawn = dalloc<int32_t>(A, nl + 1);
-    sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
-    sp.stay_hi = A.alloc((nl + 1) * rs + 64);
-    sp.stay_lo = A.alloc((nl + 1) * rs + 64);
-    sp.wsum = dalloc<double>(A, nl + 1);
-    sp.sums_valid = false;
-    GB_CUDA(cudaMemsetAsync(sp.spawn_base, 0, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4, ctx->stream));
+    species_leaf_arrays(ctx, in, s, nl);
     GB_CUDA(cudaMemcpyAsync(sp.start, new_start, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.end, new_end, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    lists_installed(ctx, sp, nl);
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
-    for (void *p : olds) A.release(p);
 }
 
 template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n_old, int64_t n_new,
@@ -490,19 +477,21 @@ template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n
     cudaStream_t st = ctx->stream;
     for (int s = 0; s < in.cfg.n_species; ++s) {
         Species &sp = in.sp[s];
+        // the new lists take at most slots_for(records, new leaves) slots
+        ensure_slots(ctx, in, s, slots_for(sp.n_upper, n_new));
         int32_t *ncnt = dalloc<int32_t>(T, n_new + 1);
-        int32_t *nstart = dalloc<int32_t>(T, n_new + 1);
+        int32_t *nstart = dalloc<int32_t>(T, n_new + 1), *nend = dalloc<int32_t>(T, n_new + 1);
         int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(n_new));
         GB_CUDA(cudaMemsetAsync(ncnt, 0, (n_new + 1) * 4, st));
-        k_adapt_count<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, kind, group, new_of, soa<R>(sp, sp.cur),
-                                                           ncnt);
+        k_adapt_count<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, kind, group, new_of,
+                                                           soa<R>(sp, sp.cur), ncnt);
         count_launch(ctx);
-        exclusive_scan_i32(ctx, ncnt, nstart, n_new, scr);
-        k_adapt_move<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, kind, group, new_of, morton_old, nstart,
-                                                          soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
+        lists_from_counts(ctx, sp, n_new, ncnt, nstart, nend, scr);
+        k_adapt_move<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, kind, group, new_of, morton_old,
+                                                          nstart, soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
         count_launch(ctx);
         check_launch("adapt_particles");
-        species_relist(ctx, in, s, n_new, nstart);
+        species_relist(ctx, in, s, n_new, nstart, nend);
         sp.cur ^= 1;
     }
 }
@@ -510,7 +499,7 @@ template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n
 template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
     cudaStream_t st = ctx->stream;
     const int64_t nl = in.nleaf;
-    DeviceArena T;
+    DeviceArena T(&ctx->cache);
     unsigned long long next_id = 0;
     GB_CUDA(cudaMemcpyAsync(&next_id, in.d_next_id, 8, cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
@@ -518,15 +507,18 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
     GB_CUDA(cudaMemsetAsync(err, 0, 4, st));
     for (int s = 0; s < in.cfg.n_species; ++s) {
         Species &sp = in.sp[s];
-        SMArgs a{nl, sp.start, in.cfg.ppc_min, in.cfg.ppc_max, in.cfg.ppc_target};
         int32_t *ncnt = dalloc<int32_t>(T, nl + 1), *nids = dalloc<int32_t>(T, nl + 1);
         int32_t *mflag = dalloc<int32_t>(T, nl + 1);
-        int32_t *nstart = dalloc<int32_t>(T, nl + 1), *idb = dalloc<int32_t>(T, nl + 1);
+        int32_t *nstart = dalloc<int32_t>(T, nl + 1), *nend = dalloc<int32_t>(T, nl + 1);
+        int32_t *idb = dalloc<int32_t>(T, nl + 1);
         int32_t *mpos = dalloc<int32_t>(T, nl + 1), *mlist = dalloc<int32_t>(T, nl + 1);
         int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(nl));
-        k_sm_count<<<blocks_for(nl), kT, 0, st>>>(a, ncnt, nids, mflag);
-        count_launch(ctx);
-        exclusive_scan_i32(ctx, ncnt, nstart, nl, scr);
+        {
+            SMArgs a{nl, sp.start, sp.end, in.cfg.ppc_min, in.cfg.ppc_max, in.cfg.ppc_target};
+            k_sm_count<<<blocks_for(nl), kT, 0, st>>>(a, ncnt, nids, mflag);
+            count_launch(ctx);
+        }
+        lists_from_counts(ctx, sp, nl, ncnt, nstart, nend, scr);
         exclusive_scan_i32(ctx, nids, idb, nl, scr);
         exclusive_scan_i32(ctx, mflag, mpos, nl, scr);
         int32_t tot[3];
@@ -534,7 +526,10 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
         GB_CUDA(cudaMemcpyAsync(&tot[1], idb + nl, 4, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaMemcpyAsync(&tot[2], mpos + nl, 4, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaStreamSynchronize(st));
-        if (tot[0] > sp.cap) fail(PIC_ECAPACITY, "split would exceed the particle capacity");
+        if (in.cfg.particle_capacity > 0 && sp.n_upper + tot[1] > in.cfg.particle_capacity)
+            fail(PIC_ECAPACITY, "split would exceed the particle capacity");
+        ensure_slots(ctx, in, s, tot[0]);  // may move the lists to larger buffers
+        SMArgs a{nl, sp.start, sp.end, in.cfg.ppc_min, in.cfg.ppc_max, in.cfg.ppc_target};
         k_compact_flags<<<blocks_for(nl), kT, 0, st>>>(nl, mflag, mpos, mlist);
         k_sm_write<R><<<warp_blocks(nl), kT, 0, st>>>(a, nstart, idb, next_id, soa<R>(sp, sp.cur),
                                                       soa<R>(sp, sp.cur ^ 1));
@@ -550,14 +545,16 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
         if (read_i32(ctx, err)) fail(PIC_EINVAL, "a leaf holds more particles than one merge block sorts (12288)");
         next_id += (unsigned long long)tot[1];
         GB_CUDA(cudaMemcpyAsync(sp.start, nstart, (nl + 1) * 4, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(sp.end, nend, (nl + 1) * 4, cudaMemcpyDeviceToDevice, st));
+        lists_installed(ctx, sp, nl);
         sp.cur ^= 1;
-        sp.n = sp.n_upper = tot[0];
         sp.sums_valid = false;
     }
     GB_CUDA(cudaMemcpyAsync(in.d_next_id, &next_id, 8, cudaMemcpyHostToDevice, st));
     GB_CUDA(cudaStreamSynchronize(st));
     in.next_id = (int64_t)next_id;
     T.release_all();
+    refresh_counts(ctx, in);
 }
 
 }  // namespace
@@ -565,13 +562,13 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
 void adapt_mesh(pic_ctx *ctx, Instance &in) {
     cudaStream_t st = ctx->stream;
     const int64_t n = in.nleaf;
-    DeviceArena T;
+    DeviceArena T(&ctx->cache);
     Level &g = in.lv[0];
     // |E| at leaf centres from the last solve
     double *emag = dalloc<double>(T, n);
     cell_emag(ctx, in, in.last_walls, emag);
     int32_t *refine = dalloc<int32_t>(T, n), *group = dalloc<int32_t>(T, n), *gactive = dalloc<int32_t>(T, n);
-    AdaptArgs a{n, in.lmax, g.lev, in.root, in.morton, in.sp[0].start, emag, in.cfg.refine_count,
+    AdaptArgs a{n, in.lmax, g.lev, in.root, in.morton, in.sp[0].start, in.sp[0].end, emag, in.cfg.refine_count,
                 in.cfg.coarsen_count, in.cfg.refine_field * in.cfg.e_ref, in.cfg.coarsen_field * in.cfg.e_ref};
     k_adapt_flags<<<blocks_for(n), kT, 0, st>>>(a, refine, group, gactive);
     count_launch(ctx);
@@ -608,7 +605,7 @@ void adapt_mesh(pic_ctx *ctx, Instance &in) {
         adapt_particles<float>(ctx, in, n, n_new, kind, group, new_of, morton_old, T);
     // rebuild the mesh structures from the new leaf description
     DeviceArena old_mesh = std::move(in.mesh_mem);
-    in.mesh_mem = DeviceArena();
+    in.mesh_mem = DeviceArena(&ctx->cache);
     DeviceArena &M = in.mesh_mem;
     uint32_t *r2 = dalloc<uint32_t>(M, n_new), *m2 = dalloc<uint32_t>(M, n_new);
     uint8_t *l2 = dalloc<uint8_t>(M, n_new);

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <map>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/gbpic.h"
@@ -29,10 +31,26 @@ constexpr int kMaxLevel = 8;      // deepest supported refinement level
 constexpr int kWarp = 32;
 
 // ------------------------------------------------------------------------------------
-// Device memory helpers (plain cudaMalloc; the context frees everything it owns)
+// Device memory.  A context keeps the blocks it releases in a size-class cache and hands
+// them out again, so a mesh rebuild (adaptation) or a temporary buffer costs no
+// cudaMalloc / cudaFree (cudaFree also synchronizes the device).  Every user of a cache
+// enqueues its work on the context's one stream, so a block released while kernels that
+// read it are still queued is only rewritten by work queued after them.
 // ------------------------------------------------------------------------------------
+struct BlockCache {
+    std::multimap<size_t, void *> idle;      // size class -> cached block
+    std::unordered_map<void *, size_t> cls;  // every block from this cache -> its size class
+    size_t idle_bytes = 0;
+    void *get(size_t bytes);
+    void put(void *p);
+    void trim();  // cudaFree every cached block
+};
+
 struct DeviceArena {
+    BlockCache *cache = nullptr;  // null: plain cudaMalloc / cudaFree
     std::vector<void *> blocks;
+    DeviceArena() = default;
+    explicit DeviceArena(BlockCache *c) : cache(c) {}
     void *alloc(size_t bytes);
     void release(void *p);
     void release_all();
@@ -64,25 +82,73 @@ struct Level {
     int64_t lat_n() const { return ((int64_t)nx0 << lmax) * ((int64_t)ny0 << lmax); }
 };
 
-// One species: double-buffered SoA record (offsets u, v in [0,1) of the leaf, velocity,
-// weight: precision R; id: u32) and the cell-list offsets.
+// Cell lists with free slots.  Leaf L of a species owns the slot segment
+// [start[L], lim[L]) of the species' buffers; its records are [start[L], end[L]) in list
+// order and the free slots [end[L], lim[L]) take the particles that enter L during a step,
+// so the push updates the lists in place.  A leaf that receives more particles than it has
+// free slots moves to a fresh segment at the tail of the buffer (past every segment); only
+// when the tail is used up are all lists of the species laid out again.  Every list builder
+// (load, adaptation, split/merge, re-layout) gives a leaf with c records list_slack(c) free
+// slots, segments in leaf order.
+__host__ __device__ inline int32_t list_slack(int32_t c) { return 16 + (c >> 2); }
+// Slots that lists of n records over nl leaves need, free slots included.
+inline int64_t slots_for(int64_t n, int64_t nl) { return n + n / 4 + 16 * nl + 64; }
+
+// One species: SoA records (offsets u, v in [0,1) of the leaf, velocity, weight:
+// precision R; id: u32) in three buffers of `cap` slots: the lists (arr[cur]), a scratch
+// buffer (arr[cur ^ 1]: sorts, re-layout) and the overflow store (records whose leaf had
+// no free slot left, with their destination).
 struct Species {
-    int64_t cap = 0;      // elements per array
+    int64_t cap = 0;      // slots per buffer
     int64_t n = 0;        // exact count known to the host
     int64_t n_upper = 0;  // upper bound on the count while steps are in flight
     int cur = 0;
     void *arr[2][6] = {};      // u, v, vx, vy, vz, w
     uint32_t *id[2] = {};
-    uint32_t *key = nullptr;   // sort keys of entering particles (cap)
-    int32_t *start = nullptr;  // [nleaf + 1] current list offsets
+    uint32_t *key = nullptr;   // [2 cap] sort key of entering records (lists | scratch)
+    uint32_t *aux = nullptr;   // [2 cap] spawned records: the parent's leaf
+    int32_t *start = nullptr;  // [nleaf + 1] first slot of each leaf's segment
+    int32_t *end = nullptr;    // [nleaf + 1] end of each leaf's records
+    int32_t *lim = nullptr;    // [nleaf + 1] end of each leaf's segment
+    int32_t *rank0 = nullptr;  // [nleaf + 1] records before leaf L in list order; [nleaf] = total
     int32_t *start_new = nullptr;
-    int32_t *stay = nullptr, *inc = nullptr, *fill = nullptr;  // [nleaf]
+    int32_t *stay = nullptr, *inc = nullptr, *fill = nullptr;  // [nleaf + 1]
+    int32_t *big = nullptr;    // [nleaf + 1] long entering regions, their count at [nleaf]
+    int32_t *moved = nullptr;  // [nleaf + 1] leaves that ran out of free slots, count at [nleaf]
     int32_t *spawn = nullptr, *spawn_base = nullptr;           // [nleaf], [nleaf + 1]
+    // overflow store
+    void *ovf[6] = {};
+    uint32_t *ovf_id = nullptr, *ovf_key = nullptr, *ovf_aux = nullptr;
+    int32_t *ovf_dest = nullptr, *ovf_slot = nullptr;
+    // device words: [0] records in the overflow store, [1] record total, [2] re-layouts,
+    // [3] records that went through the store, [4] first unused slot of the buffer (tail),
+    // [5] tail used up this step (re-layout), [6] leaves moved to the tail (statistics),
+    // [7] the re-layout drops the inflow room to fit the buffer
+    int32_t *flags = nullptr;
     // per-leaf weight sums left by the last cell-list update for the next deposit
     void *stay_hi = nullptr, *stay_lo = nullptr;               // R [nleaf]
     double *wsum = nullptr;                                     // [nleaf]
     bool sums_valid = false;
 };
+
+template <typename R> struct SoA {
+    R *u, *v, *vx, *vy, *vz, *w;
+    uint32_t *id;
+};
+template <typename R> inline SoA<R> soa(Species &sp, int buf) {
+    SoA<R> a;
+    a.u = (R *)sp.arr[buf][0]; a.v = (R *)sp.arr[buf][1]; a.vx = (R *)sp.arr[buf][2];
+    a.vy = (R *)sp.arr[buf][3]; a.vz = (R *)sp.arr[buf][4]; a.w = (R *)sp.arr[buf][5];
+    a.id = sp.id[buf];
+    return a;
+}
+template <typename R> inline SoA<R> soa_ovf(Species &sp) {
+    SoA<R> a;
+    a.u = (R *)sp.ovf[0]; a.v = (R *)sp.ovf[1]; a.vx = (R *)sp.ovf[2];
+    a.vy = (R *)sp.ovf[3]; a.vz = (R *)sp.ovf[4]; a.w = (R *)sp.ovf[5];
+    a.id = sp.ovf_id;
+    return a;
+}
 
 struct Instance {
     pic_config cfg{};
@@ -144,6 +210,7 @@ struct pic_ctx {
     void *batch_items = nullptr;
     size_t batch_smem = 0;
     gbpic::DeviceArena batch_mem;
+    gbpic::BlockCache cache;  // device blocks released by this context, for reuse
 };
 
 namespace gbpic {
@@ -227,7 +294,6 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]);
 void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list,
                          const std::vector<const double *> &walls);
 // pic_particles.cu
-void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap);
 void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *x,
                     const double *y, const double *vx, const double *vy, const double *vz,
                     const double *w, const uint64_t *id);
@@ -236,7 +302,18 @@ void particle_step(pic_ctx *ctx, Instance &in, int64_t step);
 void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, double *vx,
                     double *vy, double *vz, double *w, uint64_t *id, uint32_t *leaf);
 void ensure_capacity(pic_ctx *ctx, Instance &in);
+void ensure_slots(pic_ctx *ctx, Instance &in, int s, int64_t slots);
+void refresh_counts(pic_ctx *ctx, Instance &in);  // sp.n := exact record totals (syncs)
 void walls_at(const Instance &in, int64_t step, double walls[4]);
+// pic_lists.cu
+void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap);
+void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl);
+void lists_from_counts(pic_ctx *ctx, Species &sp, int64_t nl, const int32_t *cnt, int32_t *start,
+                       int32_t *end, int32_t *scratch);
+void lists_installed(pic_ctx *ctx, Species &sp, int64_t nl);  // lim, tail after start / end are set
+void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl);       // rank0 from start / end
+void count_totals(pic_ctx *ctx, Instance &in);  // flags[1] of every species, device side
+void place_overflow(pic_ctx *ctx, Instance &in, int s);  // tail moves, else re-layout
 // pic_adapt.cu
 void adapt_mesh(pic_ctx *ctx, Instance &in);
 void split_merge(pic_ctx *ctx, Instance &in);
@@ -247,7 +324,7 @@ pic_status guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg);
 
 // scan helpers (pic_particles.cu): exclusive scan of n int32 into out[0..n] (out[n] = total)
 void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
-                        int32_t *scratch);
+                        int32_t *scratch, const int32_t *gate = nullptr);
 int64_t scan_scratch_elems(int64_t n);
 
 }  // namespace gbpic

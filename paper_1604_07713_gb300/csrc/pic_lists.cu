@@ -1,0 +1,376 @@
+// Cell lists with free slots (§3.1: each leaf keeps the list of its particles; a particle
+// that crosses a face leaves its list and joins the neighbour's).
+//
+// Leaf L of a species owns the slot segment [start[L], lim[L]) of the species' buffers.
+// Its records are [start[L], end[L]) in list order; the free slots [end[L], lim[L]) receive
+// the particles that enter L during a step, so one push pass updates every list in place.
+// Entering records that find no free slot left go to the overflow store, and their leaf
+// moves to a fresh segment at the tail of the buffer (past every segment in use) with room
+// for them.  Only when the tail is used up are all lists of the species laid out again, in
+// leaf order with fresh free slots.  Both repairs run as kernels queued every step that do
+// nothing unless the device saw an overflow; the order of records inside a list never
+// depends on where its segment lies (order keys are list ranks, not slot numbers).
+//
+// This file holds the allocation of a species' buffers, the construction of segments from
+// per-leaf counts, list ranks and record totals, and the two repairs.
+#include <algorithm>
+#include <cstring>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+namespace {
+constexpr int kT = 256;
+inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+inline unsigned warp_blocks(int64_t nw) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((nw + kT / 32 - 1) / (kT / 32), 1 << 20));
+}
+
+// seg[L] = c + list_slack(c) with c = a[L] (+ b[L]); with `room` (a re-layout: b = this
+// step's entering records) the leaf also keeps room for one more step of that inflow.
+__global__ void k_seg_sizes(int64_t nl, const int32_t *__restrict__ a, const int32_t *__restrict__ b, int room,
+                            int32_t *__restrict__ seg, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nl) return;
+    const int32_t c = a[L] + (b ? b[L] : 0);
+    seg[L] = c + list_slack(c) + (room ? b[L] : 0);
+}
+
+// A re-layout whose inflow room does not fit the buffer lays out without it (flags[7]).
+__global__ void k_relayout_fit(const int32_t *__restrict__ start_new, int64_t nl, int64_t cap,
+                               int32_t *__restrict__ flags) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) flags[7] = (flags[5] && (int64_t)start_new[nl] > cap) ? 1 : 0;
+}
+
+// end[L] = start[L] + c[L]
+__global__ void k_set_end(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ cnt,
+                          int32_t *__restrict__ end) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < nl) end[L] = start[L] + cnt[L];
+}
+
+// Segments in leaf order: lim[L] = start[L + 1]; the tail starts at start[nl].
+__global__ void k_lists_installed(int64_t nl, const int32_t *__restrict__ start, int32_t *__restrict__ lim,
+                                  int32_t *__restrict__ flags) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < nl) lim[L] = start[L + 1];
+    if (L == 0) {
+        flags[4] = start[nl];
+        flags[5] = 0;
+    }
+}
+
+__global__ void k_list_counts(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                              int32_t *__restrict__ cnt) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < nl) cnt[L] = end[L] - start[L];
+}
+
+// total[0] += sum over leaves of end - start
+__global__ void k_count_total(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                              int32_t *__restrict__ total) {
+    __shared__ int32_t part[kT / 32];
+    int32_t s = 0;
+    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < nl; L += (int64_t)gridDim.x * blockDim.x)
+        s += end[L] - start[L];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(total, t);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void copy_record(SoA<R> t, int64_t q, SoA<R> d, int64_t p) {
+    t.u[q] = d.u[p]; t.v[q] = d.v[p]; t.vx[q] = d.vx[p]; t.vy[q] = d.vy[p]; t.vz[q] = d.vz[p];
+    t.w[q] = d.w[p]; t.id[q] = d.id[p];
+}
+
+// Repair 1 (one warp per leaf that ran out of free slots): a segment at the tail with room
+// for its staying and entering records and free slots, the staying records and the entering
+// records already in free slots copied there.  A leaf that does not fit any more marks the
+// tail as used up (flags[5]) and keeps its segment; the re-layout then takes over.
+template <typename R>
+__global__ void k_move_to_tail(const int32_t *__restrict__ moved, int64_t nl, int64_t cap,
+                               int32_t *__restrict__ start, int32_t *__restrict__ end, int32_t *__restrict__ lim,
+                               const int32_t *__restrict__ stay, const int32_t *__restrict__ fill, SoA<R> d,
+                               uint32_t *__restrict__ key, uint32_t *__restrict__ aux, int32_t *__restrict__ flags) {
+    if (flags[0] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nm = moved[nl];
+    for (int64_t i = warp; i < nm; i += nw) {
+        const int32_t L = moved[i];
+        const int32_t ns = stay[L], f = fill[L], c = ns + f;
+        const int32_t need = c + list_slack(c) + f;
+        int32_t base = 0;
+        if (lane == 0) base = atomicAdd(flags + 4, need);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if ((int64_t)base + need > cap) {
+            if (lane == 0) flags[5] = 1;
+            continue;
+        }
+        const int32_t s0 = start[L], e0 = end[L], room = lim[L] - e0;
+        for (int32_t j = lane; j < ns; j += 32) copy_record(d, base + j, d, s0 + j);
+        for (int32_t j = lane; j < room; j += 32) {
+            copy_record(d, base + ns + j, d, e0 + j);
+            key[base + ns + j] = key[e0 + j];
+            aux[base + ns + j] = aux[e0 + j];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            start[L] = base;
+            end[L] = base + ns;
+            lim[L] = base + need;
+        }
+    }
+}
+
+// Repair 2: the overflow store's records join their moved leaf at their slot.
+template <typename R>
+__global__ void k_place_ovf(const int32_t *__restrict__ end, int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
+                            const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
+                            const int32_t *__restrict__ oslot, SoA<R> d, uint32_t *__restrict__ key,
+                            uint32_t *__restrict__ aux, const int32_t *__restrict__ moved, int64_t nl,
+                            int32_t *__restrict__ flags) {
+    const int32_t n = flags[0] < cap ? flags[0] : (int32_t)cap;  // beyond cap: err is set already
+    if (n == 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // statistics
+        flags[3] += n;
+        flags[6] += moved[nl];
+    }
+    if (flags[5]) return;  // the re-layout places them
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = end[odest[i]] + oslot[i];
+        copy_record(d, q, o, i);
+        key[q] = okey[i];
+        aux[q] = oaux[i];
+    }
+}
+
+// Re-layout, step 1 (one warp per leaf): the staying records and the entering records that
+// found a free slot go to the scratch buffer at the new segment starts; staying records
+// first, entering records at their slot after them.
+template <typename R>
+__global__ void k_relayout_move(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                                const int32_t *__restrict__ lim, const int32_t *__restrict__ stay,
+                                const int32_t *__restrict__ fill, const int32_t *__restrict__ start_new, int64_t cap,
+                                SoA<R> d, const uint32_t *__restrict__ key, const uint32_t *__restrict__ aux,
+                                SoA<R> t, uint32_t *__restrict__ tkey, uint32_t *__restrict__ taux,
+                                const int32_t *__restrict__ flags, int32_t *__restrict__ err) {
+    if (flags[5] == 0) return;
+    if ((int64_t)start_new[nl] > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(err, 1);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t L = warp; L < nl; L += nw) {
+        const int32_t s0 = start[L], q0 = start_new[L], ns = stay[L];
+        for (int32_t j = lane; j < ns; j += 32) copy_record(t, q0 + j, d, s0 + j);
+        const int32_t e0 = end[L], room = lim[L] - e0;
+        const int32_t k = fill[L] < room ? fill[L] : room;
+        for (int32_t j = lane; j < k; j += 32) {
+            const int32_t p = e0 + j, q = q0 + ns + j;
+            copy_record(t, q, d, p);
+            tkey[q] = key[p]; taux[q] = aux[p];
+        }
+    }
+}
+
+// Re-layout, step 2: the records of the overflow store join them at their slot.
+template <typename R>
+__global__ void k_relayout_ovf(const int32_t *__restrict__ stay, const int32_t *__restrict__ start_new, int64_t nl,
+                               int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
+                               const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
+                               const int32_t *__restrict__ oslot, SoA<R> t, uint32_t *__restrict__ tkey,
+                               uint32_t *__restrict__ taux, const int32_t *__restrict__ flags) {
+    if (flags[5] == 0) return;
+    const int32_t n = flags[0] < cap ? flags[0] : (int32_t)cap;
+    if ((int64_t)start_new[nl] > cap) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t L = odest[i];
+        const int32_t q = start_new[L] + stay[L] + oslot[i];
+        copy_record(t, q, o, i);
+        tkey[q] = okey[i]; taux[q] = oaux[i];
+    }
+}
+
+// Re-layout, step 3: the scratch buffer back into the lists, the new segments, and end[L] at
+// the first entering record (where the entering sort expects it).
+template <typename R>
+__global__ void k_relayout_back(int64_t nl, const int32_t *__restrict__ start_new, const int32_t *__restrict__ stay,
+                                int64_t cap, SoA<R> t, const uint32_t *__restrict__ tkey,
+                                const uint32_t *__restrict__ taux, SoA<R> d, uint32_t *__restrict__ key,
+                                uint32_t *__restrict__ aux, int32_t *__restrict__ start, int32_t *__restrict__ end,
+                                int32_t *__restrict__ lim, int32_t *__restrict__ flags) {
+    if (flags[5] == 0) return;
+    const int64_t span = start_new[nl];
+    if (span > cap) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < span; i += stride) {
+        copy_record(d, i, t, i);
+        key[i] = tkey[i]; aux[i] = taux[i];
+    }
+    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L <= nl; L += stride) {
+        start[L] = start_new[L];
+        if (L < nl) {
+            end[L] = start_new[L] + stay[L];
+            lim[L] = start_new[L + 1];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[2] += 1;  // statistics
+        flags[4] = (int32_t)span;
+    }
+}
+
+template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
+    Species &sp = in.sp[s];
+    cudaStream_t st = ctx->stream;
+    const int64_t nl = in.nleaf;
+    const SoA<R> d = soa<R>(sp, sp.cur), t = soa<R>(sp, sp.cur ^ 1);
+    const SoA<R> o = soa_ovf<R>(sp);
+    // leaves out of free slots move to the tail
+    k_move_to_tail<R><<<152 * 4, kT, 0, st>>>(sp.moved, nl, sp.cap, sp.start, sp.end, sp.lim, sp.stay, sp.fill, d,
+                                              sp.key, sp.aux, sp.flags);
+    k_place_ovf<R><<<152 * 2, kT, 0, st>>>(sp.end, sp.cap, o, sp.ovf_key, sp.ovf_aux, sp.ovf_dest, sp.ovf_slot, d,
+                                           sp.key, sp.aux, sp.moved, nl, sp.flags);
+    // tail used up: every list again, in leaf order (gated on flags[5])
+    int32_t *scr = sp.spawn_base + nl + 1 + scan_scratch_elems(nl);
+    k_seg_sizes<<<blocks_for(nl), kT, 0, st>>>(nl, sp.stay, sp.fill, 1, sp.inc, sp.flags + 5);
+    exclusive_scan_i32(ctx, sp.inc, sp.start_new, nl, scr, sp.flags + 5);
+    k_relayout_fit<<<1, 32, 0, st>>>(sp.start_new, nl, sp.cap, sp.flags);
+    k_seg_sizes<<<blocks_for(nl), kT, 0, st>>>(nl, sp.stay, sp.fill, 0, sp.inc, sp.flags + 7);
+    exclusive_scan_i32(ctx, sp.inc, sp.start_new, nl, scr, sp.flags + 7);
+    uint32_t *tkey = sp.key + sp.cap, *taux = sp.aux + sp.cap;
+    k_relayout_move<R><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, sp.end, sp.lim, sp.stay, sp.fill, sp.start_new,
+                                                       sp.cap, d, sp.key, sp.aux, t, tkey, taux, sp.flags, in.d_err);
+    k_relayout_ovf<R><<<152 * 4, kT, 0, st>>>(sp.stay, sp.start_new, nl, sp.cap, o, sp.ovf_key, sp.ovf_aux,
+                                              sp.ovf_dest, sp.ovf_slot, t, tkey, taux, sp.flags);
+    k_relayout_back<R><<<152 * 8, kT, 0, st>>>(nl, sp.start_new, sp.stay, sp.cap, t, tkey, taux, d, sp.key, sp.aux,
+                                               sp.start, sp.end, sp.lim, sp.flags);
+    count_launch(ctx, 8);
+    check_launch("place_overflow");
+}
+}  // namespace
+
+// Per-leaf arrays of one species for nl leaves (segments empty).
+void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
+    Species &sp = in.sp[s];
+    DeviceArena &A = in.part_mem[s];
+    void *olds[] = {sp.start, sp.end, sp.lim, sp.rank0, sp.start_new, sp.stay, sp.inc, sp.fill, sp.big,
+                    sp.moved, sp.spawn, sp.spawn_base, sp.stay_hi, sp.stay_lo, sp.wsum};
+    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
+    sp.start = dalloc<int32_t>(A, nl + 1);
+    sp.end = dalloc<int32_t>(A, nl + 1);
+    sp.lim = dalloc<int32_t>(A, nl + 1);
+    sp.rank0 = dalloc<int32_t>(A, nl + 1);
+    sp.start_new = dalloc<int32_t>(A, nl + 1);
+    sp.stay = dalloc<int32_t>(A, nl + 1);
+    sp.inc = dalloc<int32_t>(A, nl + 1);
+    sp.fill = dalloc<int32_t>(A, nl + 1);
+    sp.big = dalloc<int32_t>(A, nl + 1);
+    sp.moved = dalloc<int32_t>(A, nl + 1);
+    sp.spawn = dalloc<int32_t>(A, nl + 1);
+    // spawn_base [nl + 1] | scan scratch | scan scratch
+    sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
+    sp.stay_hi = A.alloc((nl + 1) * rs + 64);
+    sp.stay_lo = A.alloc((nl + 1) * rs + 64);
+    sp.wsum = dalloc<double>(A, nl + 1);
+    sp.sums_valid = false;
+    cudaStream_t st = ctx->stream;
+    GB_CUDA(cudaMemsetAsync(sp.start, 0, (nl + 1) * 4, st));
+    GB_CUDA(cudaMemsetAsync(sp.end, 0, (nl + 1) * 4, st));
+    GB_CUDA(cudaMemsetAsync(sp.lim, 0, (nl + 1) * 4, st));
+    GB_CUDA(cudaMemsetAsync(sp.spawn_base, 0, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4, st));
+    for (void *p : olds)
+        if (p) A.release(p);
+}
+
+// Buffers of one species with `cap` slots each, and its per-leaf arrays (no records).
+void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
+    Species &sp = in.sp[s];
+    DeviceArena &A = in.part_mem[s];
+    A.release_all();
+    sp.start = sp.end = sp.lim = sp.rank0 = sp.start_new = sp.stay = sp.inc = sp.fill = sp.big = sp.moved = nullptr;
+    sp.spawn = sp.spawn_base = nullptr;
+    sp.stay_hi = sp.stay_lo = nullptr;
+    sp.wsum = nullptr;
+    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
+    sp.cap = cap;
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 6; ++k) sp.arr[b][k] = A.alloc(cap * rs + 64);
+        sp.id[b] = dalloc<uint32_t>(A, cap);
+    }
+    for (int k = 0; k < 6; ++k) sp.ovf[k] = A.alloc(cap * rs + 64);
+    sp.ovf_id = dalloc<uint32_t>(A, cap);
+    sp.ovf_key = dalloc<uint32_t>(A, cap);
+    sp.ovf_aux = dalloc<uint32_t>(A, cap);
+    sp.ovf_dest = dalloc<int32_t>(A, cap);
+    sp.ovf_slot = dalloc<int32_t>(A, cap);
+    sp.key = dalloc<uint32_t>(A, 2 * cap);
+    sp.aux = dalloc<uint32_t>(A, 2 * cap);
+    sp.flags = dalloc<int32_t>(A, 8);
+    GB_CUDA(cudaMemsetAsync(sp.flags, 0, 8 * 4, ctx->stream));
+    species_leaf_arrays(ctx, in, s, in.nleaf);
+    sp.cur = 0;
+    sp.n = 0;
+    sp.n_upper = 0;
+}
+
+// start = exclusive scan of (cnt + free slots), end = start + cnt.  `start` has nl + 1
+// entries (start[nl] = slot span); scratch: scan_scratch_elems(nl).  `start` must not
+// alias cnt.  Installing them as a species' lists takes lists_installed() afterwards.
+void lists_from_counts(pic_ctx *ctx, Species &sp, int64_t nl, const int32_t *cnt, int32_t *start, int32_t *end,
+                       int32_t *scratch) {
+    cudaStream_t st = ctx->stream;
+    k_seg_sizes<<<blocks_for(nl), kT, 0, st>>>(nl, cnt, nullptr, 0, start, nullptr);
+    count_launch(ctx);
+    exclusive_scan_i32(ctx, start, start, nl, scratch);
+    k_set_end<<<blocks_for(nl), kT, 0, st>>>(nl, start, cnt, end);
+    count_launch(ctx);
+    (void)sp;
+}
+
+// After a builder wrote sp.start (leaf order, nl + 1 entries) and sp.end: segment limits and
+// the tail.
+void lists_installed(pic_ctx *ctx, Species &sp, int64_t nl) {
+    k_lists_installed<<<blocks_for(nl), kT, 0, ctx->stream>>>(nl, sp.start, sp.lim, sp.flags);
+    count_launch(ctx);
+    check_launch("lists_installed");
+}
+
+// rank0[L] = records of the leaves before L (list order), rank0[nl] = total.
+void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl) {
+    k_list_counts<<<blocks_for(nl), kT, 0, ctx->stream>>>(nl, sp.start, sp.end, sp.inc);
+    count_launch(ctx);
+    exclusive_scan_i32(ctx, sp.inc, sp.rank0, nl, sp.spawn_base + nl + 1);
+}
+
+// flags[1] of every species := its record total (device side; read after a sync).
+void count_totals(pic_ctx *ctx, Instance &in) {
+    for (int s = 0; s < in.cfg.n_species; ++s) {
+        Species &sp = in.sp[s];
+        if (!sp.start) continue;
+        GB_CUDA(cudaMemsetAsync(sp.flags + 1, 0, 4, ctx->stream));
+        const unsigned nb = std::min<unsigned>(blocks_for(in.nleaf), 152u * 2u);
+        k_count_total<<<nb, kT, 0, ctx->stream>>>(in.nleaf, sp.start, sp.end, sp.flags + 1);
+        count_launch(ctx);
+    }
+    check_launch("count_totals");
+}
+
+void place_overflow(pic_ctx *ctx, Instance &in, int s) {
+    if (in.cfg.precision == PIC_FP64) place_impl<double>(ctx, in, s);
+    else place_impl<float>(ctx, in, s);
+}
+
+}  // namespace gbpic

@@ -2,20 +2,22 @@
 // wall handling / leaf location / Monte Carlo collisions with electron-ion pair spawning,
 // and the cell-list update.
 //
-// Storage: per species a structure of arrays in cell-list order (leaf by leaf, the order of
-// the leaf's list inside): offsets (u, v) in [0, 1) of the leaf, velocity (vx, vy, vz),
-// weight w in precision R, id as u32.  The leaf of a particle is implicit in the list offsets
-// start[leaf] .. start[leaf + 1].  One warp walks one leaf, so the leaf's corner field and
-// geometry are loaded once and broadcast.
+// Storage: per species a structure of arrays in cell-list order: offsets (u, v) in [0, 1) of
+// the leaf, velocity (vx, vy, vz), weight w in precision R, id as u32.  Leaf L's records are
+// the slots [start[L], end[L]) of its segment [start[L], lim[L]); the leaf of a particle is
+// implicit.  One warp walks one leaf, so the leaf's corner field and geometry are loaded
+// once and broadcast.
 //
 // Cell-list update (§3.1: a particle that crosses a face leaves its cell's list and is added
 // to the neighbour's list): the new list of a leaf is its staying particles in their old
 // order, then the entering particles in the order of their old list position, then the
-// electron-ion pairs spawned this step in the order of their parents.  It is built in two
-// passes over the particles with identical arithmetic: a count pass (per-leaf staying and
-// entering counts, spawn counts), prefix sums, a move pass that writes every record to its
-// new list (staying: exact rank; entering: an atomic slot plus its order key), and a per-leaf
-// sort of the entering slots by key, which makes the result deterministic.
+// electron-ion pairs spawned this step in the order of their parents.  One push pass per
+// species does it in place: staying records are compacted to the front of their segment at
+// their exact rank, entering and spawned records take an atomic free slot of their new
+// leaf together with an order key (or the overflow store when the leaf has no free slot
+// left, after which the leaf moves to a fresh segment).  A per-leaf sort of the entering
+// slots by key then moves them behind the staying records, which makes the result
+// deterministic.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,18 +32,6 @@ constexpr int kWarpsPerBlock = kT / 32;
 inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 inline unsigned warp_blocks(int64_t nwarps) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock, 1 << 20));
-}
-
-template <typename R> struct SoA {
-    R *u, *v, *vx, *vy, *vz, *w;
-    uint32_t *id;
-};
-template <typename R> SoA<R> soa(Species &sp, int buf) {
-    SoA<R> a;
-    a.u = (R *)sp.arr[buf][0]; a.v = (R *)sp.arr[buf][1]; a.vx = (R *)sp.arr[buf][2];
-    a.vy = (R *)sp.arr[buf][3]; a.vz = (R *)sp.arr[buf][4]; a.w = (R *)sp.arr[buf][5];
-    a.id = sp.id[buf];
-    return a;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -95,7 +85,7 @@ template <typename R> __device__ __forceinline__ void warp_two_sum(R &hi, R &lo)
 struct DepositArgs {
     int64_t nleaf;
     int nsp;
-    const int32_t *start[2];
+    const int32_t *start[2], *end[2];
     const void *w[2];
     double q[2];
     const uint8_t *lev;
@@ -114,7 +104,7 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
     for (int64_t L = warp; L < a.nleaf; L += nw) {
         double total = 0.0;
         for (int s = 0; s < a.nsp; ++s) {
-            const int32_t p0 = a.start[s][L], p1 = a.start[s][L + 1];
+            const int32_t p0 = a.start[s][L], p1 = a.end[s][L];
             const R *w = (const R *)a.w[s];
             R sum = 0, c = 0;
             for (int32_t p = p0 + lane; p < p1; p += 128) {
@@ -153,42 +143,75 @@ __global__ void k_deposit_sums(DepositArgs a, const double *__restrict__ ws0, co
 }
 
 // ------------------------------------------------------------------------------------
-// Fused gather - push - walls - locate - MCC, in count or move mode.
+// Fused gather - push - walls - locate - MCC, updating the cell lists in place.
 // ------------------------------------------------------------------------------------
+// Where the entering and spawned records of one species go: a free slot of the new leaf,
+// else the overflow store (destination leaf and slot kept for the re-layout).
+template <typename R> struct ListPut {
+    SoA<R> d;
+    uint32_t *key, *aux;
+    const int32_t *end, *lim;
+    int32_t *fill;
+    int32_t *moved;  // leaves that ran out of free slots; their count at moved[nleaf]
+    int64_t nleaf;
+    SoA<R> ovf;
+    uint32_t *ovf_key, *ovf_aux;
+    int32_t *ovf_dest, *ovf_slot, *ovf_n;
+    int32_t ovf_cap;
+};
+
+template <typename R>
+__device__ __forceinline__ void list_put(const ListPut<R> &o, int32_t L, R u, R v, R vx, R vy, R vz, R w,
+                                         uint32_t id, uint32_t key, uint32_t aux, int32_t *err) {
+    const int32_t slot = atomicAdd(o.fill + L, 1);
+    const int32_t q = o.end[L] + slot;
+    const int32_t lim = o.lim[L];
+    if (q < lim) {
+        o.d.u[q] = u; o.d.v[q] = v; o.d.vx[q] = vx; o.d.vy[q] = vy; o.d.vz[q] = vz; o.d.w[q] = w;
+        o.d.id[q] = id;
+        o.key[q] = key;
+        o.aux[q] = aux;
+    } else {
+        if (q == lim) o.moved[atomicAdd(o.moved + o.nleaf, 1)] = L;  // first record without a slot
+        const int32_t i = atomicAdd(o.ovf_n, 1);
+        if (i < o.ovf_cap) {
+            o.ovf.u[i] = u; o.ovf.v[i] = v; o.ovf.vx[i] = vx; o.ovf.vy[i] = vy; o.ovf.vz[i] = vz; o.ovf.w[i] = w;
+            o.ovf.id[i] = id;
+            o.ovf_key[i] = key;
+            o.ovf_aux[i] = aux;
+            o.ovf_dest[i] = L;
+            o.ovf_slot[i] = slot;
+        } else {
+            atomicExch(err, 1);
+        }
+    }
+}
+
 template <typename R> struct PushArgs {
     int64_t nleaf;
     int lmax, NX, NY;
     int px, py;
     R dth[kMaxLevel + 1];  // dt / h per level
     R qm_dt;               // (q/m) dt
-    const int32_t *start, *map, *ix, *iy;
+    const int32_t *start, *end, *map, *ix, *iy;
+    const int32_t *rank0;      // list rank of each leaf's first record; [nleaf] = species total
+    const int32_t *ion_total;  // electrons with ionization: the ion total (spawned ions' keys)
     const uint8_t *lev;
     const R *stencil;
-    SoA<R> in;
-    int mode;  // 0 = count, 1 = move
-    // counts (this species)
-    int32_t *stay, *inc, *spawn;
-    int32_t *inc_ion;  // electrons: entering counts of the ion lists (spawned ions)
-    // move
-    SoA<R> out;
-    uint32_t *key_out;
-    const int32_t *start_new, *stay_new;
-    int32_t *fill;
-    const int32_t *spawn_base;
-    const unsigned long long *next_id;
-    SoA<R> ion_out;
-    uint32_t *ion_key;
-    const int32_t *ion_start_new, *ion_stay, *ion_start_old;
-    int32_t *ion_fill;
-    R *stay_hi, *stay_lo;  // move pass: compensated weight sum of each leaf's staying particles
-    int32_t cap, ion_cap;  // record capacity of the output buffers
-    int32_t *err;          // set when a write would fall outside them (count/move mismatch)
+    SoA<R> d;             // this species' lists, updated in place
+    ListPut<R> self;      // entering records and spawned electrons of this species
+    ListPut<R> ion;       // electrons with ionization: the spawned ions (ion.fill null otherwise)
+    int32_t *stay;        // per leaf: staying records
+    int32_t *spawn;       // electrons with ionization: per leaf, spawning electrons
+    R *stay_hi, *stay_lo; // compensated weight sum of each leaf's staying particles
+    int32_t *err;
     // collisions
     int mcc, species;
     R ng_dt, sig_el, sig_iz0, eps_th, half_m_over_qe, two_qe_over_m, two_m_over_mn;
     R vt_gas;       // neutral thermal speed sqrt(T qe / M)
     R red_a, red_m, red_mn;  // ions: M / (m + M), m / (m + M), M / (m + M)
     R g_partner_max, g_pad;  // ions: bound on the partner speed (8.2 v_t), rounding margin
+    R p_pad;                 // rounding margin of the linear bound on the collision probability
     uint32_t k0, k1, inst_word, step;
 };
 
@@ -210,27 +233,37 @@ template <typename R> __device__ __forceinline__ void normals3(const U4 &r, R n[
     n[0] = r1 * c1; n[1] = r1 * s1; n[2] = r2 * c3;
 }
 
+// One warp per leaf (persistent warps).  A staying particle's record goes to slot
+// start[L] + its rank among the leaf's staying particles, which is never past its own slot,
+// so the leaf's own records are compacted in place; everything the warp reads of the next
+// chunk lies beyond every slot it writes in this one.  Entering and spawned records only go
+// to free slots past end[], which no warp reads during the pass.
 template <typename R>
 __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t n_old = a.start[a.nleaf];
-    // persistent warps: the next leaf's list offsets are fetched while this leaf runs
+    // persistent warps: the next leaf's list bounds are fetched while this leaf runs
     int32_t np0 = 0, np1 = 0;
-    if (warp < a.nleaf) { np0 = a.start[warp]; np1 = a.start[warp + 1]; }
+    if (warp < a.nleaf) { np0 = a.start[warp]; np1 = a.end[warp]; }
     for (int64_t Lw = warp; Lw < a.nleaf; Lw += nw) {
         const int32_t L = (int32_t)Lw;
         const int32_t p0 = np0, p1 = np1;
-        if (Lw + nw < a.nleaf) { np0 = a.start[Lw + nw]; np1 = a.start[Lw + nw + 1]; }
+        if (Lw + nw < a.nleaf) { np0 = a.start[Lw + nw]; np1 = a.end[Lw + nw]; }
         if (p0 == p1) {
             if (lane == 0) {
-                if (a.mode == 0) { a.stay[L] = 0; if (a.spawn) a.spawn[L] = 0; }
-                else { a.stay_hi[L] = (R)0; a.stay_lo[L] = (R)0; }
+                a.stay[L] = 0;
+                if (a.spawn) a.spawn[L] = 0;
+                a.stay_hi[L] = (R)0; a.stay_lo[L] = (R)0;
             }
             continue;
         }
         R ws_sum = 0, ws_c = 0;  // staying particles' weights, in list order per lane
+        // order keys: an entering record's list rank before the step; a spawned record's is
+        // the species total plus its parent's rank, so it sorts after every entering record
+        const uint32_t key0 = (uint32_t)(a.rank0[L] - p0);
+        const uint32_t span = (uint32_t)a.rank0[a.nleaf];
+        const uint32_t ion_span = a.ion_total ? (uint32_t)*a.ion_total : 0u;
         const int lv = a.lev[L];
         const int32_t s = 1 << (a.lmax - lv);
         const int32_t lx = a.ix[L], ly = a.iy[L];
@@ -239,29 +272,25 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) E[k] = a.stencil[8 * (int64_t)L + k];
         int32_t stay_run = 0, spawn_run = 0;
-        const int32_t sbase = (a.mode == 1 && a.spawn_base) ? a.spawn_base[L] : 0;
-        const int32_t dst0 = a.mode == 1 ? a.start_new[L] : 0;
         // software pipeline: the next chunk's record is loaded while this chunk computes
-        R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nw = 0;
+        R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nwt = 0;
         uint32_t nid = 0;
         if (p0 + lane < p1) {
             const int32_t q = p0 + lane;
-            nu = a.in.u[q]; nv = a.in.v[q]; nvx = a.in.vx[q]; nvy = a.in.vy[q]; nvz = a.in.vz[q];
-            nid = a.in.id[q];
-            if (a.mode == 1) nw = a.in.w[q];
+            nu = a.d.u[q]; nv = a.d.v[q]; nvx = a.d.vx[q]; nvy = a.d.vy[q]; nvz = a.d.vz[q];
+            nid = a.d.id[q]; nwt = a.d.w[q];
         }
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
             const bool live = p < p1;
             bool alive = false, stays = false, spawns = false;
             int32_t nl = -1;
-            R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nw;
+            R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nwt;
             uint32_t id = nid;
             if (p + 32 < p1) {
                 const int32_t q = p + 32;
-                nu = a.in.u[q]; nv = a.in.v[q]; nvx = a.in.vx[q]; nvy = a.in.vy[q]; nvz = a.in.vz[q];
-                nid = a.in.id[q];
-                if (a.mode == 1) nw = a.in.w[q];
+                nu = a.d.u[q]; nv = a.d.v[q]; nvx = a.d.vx[q]; nvy = a.d.vy[q]; nvz = a.d.vz[q];
+                nid = a.d.id[q]; nwt = a.d.w[q];
             }
             R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
             if (live) {
@@ -304,21 +333,19 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
                         stays = nl == L;
                     }
                 }
-                // The count pass only needs the spawn decisions, which only electrons above the
-                // ionization threshold can make; the move pass runs every collision.  v2 and eps
-                // are computed once so both passes take the identical decision.
                 const R v2 = vx * vx + vy * vy + vz * vz;
-                const R eps = a.half_m_over_qe * v2;
-                const bool collide_here = a.mode == 1 || (a.species == 0 && a.sig_iz0 > (R)0 && eps > a.eps_th);
-                if (alive && a.mcc && collide_here) {
+                if (alive && a.mcc) {
                     const U4 r0 = philox4x32_10(id, a.inst_word, a.step, 0u, a.k0, a.k1);
                     const R U0 = u24<R>(r0.x), U1 = u24<R>(r0.y), U2 = u24<R>(r0.z), U3 = u24<R>(r0.w);
                     if (a.species == 0) {
+                        const R eps = a.half_m_over_qe * v2;
                         const R speed = m_sqrt(v2);
                         const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - a.eps_th / eps) : (R)0;
                         const R st = a.sig_el + siz;
-                        const R P = -m_expm1(-a.ng_dt * st * speed);
-                        if (U0 < P) {
+                        const R xc = a.ng_dt * st * speed;
+                        // 1 - exp(-x) <= x: a uniform at or above x (with a rounding margin)
+                        // already means no collision, without evaluating the exponential
+                        if (U0 < xc * a.p_pad && U0 < -m_expm1(-xc)) {
                             if (U1 * st < siz) {
                                 const R rest = eps - a.eps_th;
                                 const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
@@ -342,11 +369,10 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
                                 vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
                             }
                         }
-                    } else if (U0 < -m_expm1(-a.ng_dt * a.sig_el * a.g_pad *
-                                             (m_sqrt(vx * vx + vy * vy + vz * vz) + a.g_partner_max))) {
-                        // The Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms), so
-                        // U0 above the probability at |v| + that bound already means no collision;
-                        // below it, the partner is drawn and the exact test decides.
+                    } else if (U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad) {
+                        // The Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms) and
+                        // 1 - exp(-x) <= x, so U0 above x at |v| + that bound already means no
+                        // collision; below it, the partner is drawn and the exact test decides.
                         const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
                         R nn[3];
                         normals3<R>(r2, nn);
@@ -368,104 +394,94 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
             }
             const uint32_t stay_mask = __ballot_sync(0xFFFFFFFFu, live && alive && stays);
             const uint32_t spawn_mask = __ballot_sync(0xFFFFFFFFu, live && spawns);
-            const bool enters = live && alive && !stays;
-            if (a.mode == 0) {
-                // entering particles and spawned pairs: per-destination counts
-                if (enters || spawns) {
-                    const uint32_t grp = __match_any_sync(__activemask(), nl);
-                    const int nent = __popc(__ballot_sync(grp, enters));
-                    const int nsp = __popc(__ballot_sync(grp, spawns));
-                    if ((__ffs(grp) - 1) == lane) {
-                        if (nent + nsp) atomicAdd(a.inc + nl, nent + nsp);
-                        if (nsp && a.inc_ion) atomicAdd(a.inc_ion + nl, nsp);
-                    }
+            if (live && alive) {
+                if (stays) {
+                    const int32_t dst = p0 + stay_run + __popc(stay_mask & lanemask_lt());
+                    kahan_add(ws_sum, ws_c, w);
+                    a.d.u[dst] = u; a.d.v[dst] = v;
+                    a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz;
+                    if (dst != p) { a.d.w[dst] = w; a.d.id[dst] = id; }
+                } else {
+                    list_put(a.self, nl, u, v, vx, vy, vz, w, id, key0 + (uint32_t)p, 0u, a.err);
                 }
-                stay_run += __popc(stay_mask);
-                spawn_run += __popc(spawn_mask);
-            } else {
-                if (live && alive) {
-                    int32_t dst;
-                    if (stays) {
-                        dst = dst0 + stay_run + __popc(stay_mask & lanemask_lt());
-                    } else {
-                        const int32_t slot = atomicAdd(a.fill + nl, 1);
-                        dst = a.start_new[nl] + a.stay_new[nl] + slot;
-                        if (dst >= 0 && dst < a.cap) a.key_out[dst] = (uint32_t)p;
-                    }
-                    if (dst < 0 || dst >= a.cap) { atomicExch(a.err, 1); dst = -1; }
-                    if (stays) kahan_add(ws_sum, ws_c, w);
-                    if (dst >= 0) {
-                    a.out.u[dst] = u; a.out.v[dst] = v;
-                    a.out.vx[dst] = vx; a.out.vy[dst] = vy; a.out.vz[dst] = vz;
-                    a.out.w[dst] = w; a.out.id[dst] = id;
-                    }
-                }
-                if (spawns) {
-                    const int32_t rank = sbase + spawn_run + __popc(spawn_mask & lanemask_lt());
-                    const unsigned long long base = *a.next_id + 2ull * (unsigned long long)rank;
-                    const int32_t slot = atomicAdd(a.fill + nl, 1);
-                    const int32_t dst = a.start_new[nl] + a.stay_new[nl] + slot;
-                    if (dst < 0 || dst >= a.cap) {
-                        atomicExch(a.err, 1);
-                    } else {
-                        a.key_out[dst] = (uint32_t)(n_old + p);
-                        a.out.u[dst] = u; a.out.v[dst] = v;
-                        a.out.vx[dst] = sv[0]; a.out.vy[dst] = sv[1]; a.out.vz[dst] = sv[2];
-                        a.out.w[dst] = w; a.out.id[dst] = (uint32_t)base;
-                    }
-                    if (a.ion_fill) {
-                        const int32_t islot = atomicAdd(a.ion_fill + nl, 1);
-                        const int32_t idst = a.ion_start_new[nl] + a.ion_stay[nl] + islot;
-                        if (idst < 0 || idst >= a.ion_cap) {
-                            atomicExch(a.err, 1);
-                        } else {
-                        a.ion_key[idst] = (uint32_t)(a.ion_start_old[a.nleaf] + p);
-                        a.ion_out.u[idst] = u; a.ion_out.v[idst] = v;
-                        a.ion_out.vx[idst] = si[0]; a.ion_out.vy[idst] = si[1]; a.ion_out.vz[idst] = si[2];
-                        a.ion_out.w[idst] = w; a.ion_out.id[idst] = (uint32_t)(base + 1);
-                        }
-                    }
-                }
-                stay_run += __popc(stay_mask);
-                spawn_run += __popc(spawn_mask);
             }
+            if (spawns) {
+                // the pair's ids follow from the parent's spawn rank once all leaves are counted:
+                // the rank within this leaf travels in the id word, the leaf in the aux word
+                const uint32_t rank = (uint32_t)(spawn_run + __popc(spawn_mask & lanemask_lt()));
+                list_put(a.self, nl, u, v, sv[0], sv[1], sv[2], w, rank, span + key0 + (uint32_t)p, (uint32_t)L,
+                         a.err);
+                if (a.ion.fill)
+                    list_put(a.ion, nl, u, v, si[0], si[1], si[2], w, rank, ion_span + key0 + (uint32_t)p,
+                             (uint32_t)L, a.err);
+            }
+            stay_run += __popc(stay_mask);
+            spawn_run += __popc(spawn_mask);
         }
-        if (a.mode == 0 && lane == 0) {
+        R hi = ws_sum, lo = -ws_c;
+        warp_two_sum(hi, lo);
+        if (lane == 0) {
             a.stay[L] = stay_run;
             if (a.spawn) a.spawn[L] = spawn_run;
-        }
-        if (a.mode == 1) {
-            R hi = ws_sum, lo = -ws_c;
-            warp_two_sum(hi, lo);
-            if (lane == 0) { a.stay_hi[L] = hi; a.stay_lo[L] = lo; }
+            a.stay_hi[L] = hi; a.stay_lo[L] = lo;
         }
     }
-}
-
-__global__ void k_add_counts(int64_t n, const int32_t *__restrict__ a, int32_t *__restrict__ b) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = a[i] + b[i];
 }
 
 __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__restrict__ spawn_total) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *next_id += 2ull * (unsigned long long)(*spawn_total);
 }
 
-// Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
-// longer runs go through the idle buffer `tmp`.
+// ------------------------------------------------------------------------------------
+// Per-leaf sort of the entering records [end[L], end[L] + n) by order key into their final
+// slots [start[L] + stay[L], ...).  A spawned record (key >= span) gets its id here:
+// next_id + 2 (spawn rank of its parent) (+ 1 for the ion), the rank being the parent
+// leaf's spawn offset (aux word) plus the rank within that leaf (id word).
+// ------------------------------------------------------------------------------------
+struct SortArgs {
+    int64_t nleaf;
+    const int32_t *start, *stay, *fill, *lim;
+    int32_t *end;
+    uint32_t *key, *aux, *tkey, *taux;  // lists' and scratch buffer's key / aux words
+    const int32_t *span;                // keys from *span on are spawned records (null: none)
+    const int32_t *spawn_base;          // electrons' spawn offsets per parent leaf
+    const unsigned long long *next_id;
+    uint32_t ion_bit;                   // 1 for the ion list
+    double *wsum;                       // with stay sums: the leaf's weight for the next deposit
+    const void *stay_hi, *stay_lo;
+    int32_t *big;                       // long regions for k_sort_big, count at big[nleaf]
+    int32_t *err;
+};
+
+__device__ __forceinline__ uint32_t spawn_id(const SortArgs &a, uint32_t span, uint32_t key, uint32_t aux,
+                                             uint32_t id) {
+    if (key < span) return id;
+    return (uint32_t)(*a.next_id + 2ull * ((unsigned long long)a.spawn_base[aux] + id) + a.ion_bit);
+}
+
+// Entering region of leaf L, or k < 0 when it cannot be (an aborted re-layout).
+__device__ __forceinline__ void entering_region(const SortArgs &a, int64_t L, int32_t &b0, int32_t &k,
+                                                int32_t &q0) {
+    b0 = a.end[L];
+    k = a.fill[L];
+    q0 = a.start[L] + a.stay[L];
+    if (b0 + k > a.lim[L] || q0 > b0) {
+        k = -1;
+        atomicExch(a.err, 1);
+    }
+}
+
 constexpr int kSortSmem = 512;  // per-warp shared-memory sort capacity (keys + slots)
 
-// Sort the slots [b0, b1) of one leaf by key (one warp).  Up to 32 entries sort in registers;
-// up to 512 by a bitonic network on (key, slot) pairs in the warp's shared memory followed by
-// a gather through the idle buffer `tmp`; longer runs were sorted by k_sort_big already.
+// Sort the k entries at [b0, b0 + k) into [q0, q0 + k) (one warp).  Up to 32 entries sort
+// in registers; up to 512 by a bitonic network on (key, slot) pairs in the warp's shared
+// memory followed by a gather through the scratch buffer `t`.
 template <typename R>
-__device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t *__restrict__ key, SoA<R> tmp,
-                            uint32_t *__restrict__ tkey, unsigned long long *wsm) {
-    const int32_t k = b1 - b0;
-    if (k <= 1 || k > kSortSmem) return;  // longer regions: k_sort_big
+__device__ void sort_region(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0, int lane, SoA<R> d,
+                            SoA<R> t, unsigned long long *wsm) {
     if (k <= 32) {
         const bool act = lane < k;
-        const uint32_t kk = act ? key[b0 + lane] : 0xFFFFFFFFu;
+        const uint32_t kk = act ? a.key[b0 + lane] : 0xFFFFFFFFu;
         int rank = 0;
         for (int j = 0; j < k; ++j) {
             const uint32_t o = __shfl_sync(0xFFFFFFFFu, kk, j);
@@ -475,79 +491,76 @@ __device__ void sort_region(int32_t b0, int32_t b1, int lane, SoA<R> d, uint32_t
         uint32_t id = 0;
         if (act) {
             const int32_t p = b0 + lane;
-            u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p]; id = d.id[p];
+            u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p];
+            id = spawn_id(a, span, kk, kk >= span ? a.aux[p] : 0u, d.id[p]);
         }
         __syncwarp();
         if (act) {
-            const int32_t q = b0 + rank;
+            const int32_t q = q0 + rank;
             d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
-            key[q] = kk;
         }
         __syncwarp();
         return;
     }
-    // copy the region to the idle buffer
-    for (int32_t p = b0 + lane; p < b1; p += 32) {
-        tmp.u[p] = d.u[p]; tmp.v[p] = d.v[p]; tmp.vx[p] = d.vx[p]; tmp.vy[p] = d.vy[p];
-        tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
+    // copy the region to the scratch buffer
+    for (int32_t p = b0 + lane; p < b0 + k; p += 32) {
+        t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p];
+        t.vz[p] = d.vz[p]; t.w[p] = d.w[p]; t.id[p] = d.id[p]; a.tkey[p] = a.key[p]; a.taux[p] = a.aux[p];
     }
     __syncwarp();
-    {
-        int32_t np2 = 64;
-        while (np2 < k) np2 <<= 1;
-        for (int32_t i = lane; i < np2; i += 32)
-            wsm[i] = i < k ? (((unsigned long long)tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
-        __syncwarp();
-        for (int32_t kk = 2; kk <= np2; kk <<= 1) {
-            for (int32_t j = kk >> 1; j > 0; j >>= 1) {
-                for (int32_t i = lane; i < np2; i += 32) {
-                    const int32_t ij = i ^ j;
-                    if (ij > i) {
-                        const unsigned long long x = wsm[i], y = wsm[ij];
-                        if ((x > y) == ((i & kk) == 0)) { wsm[i] = y; wsm[ij] = x; }
-                    }
+    int32_t np2 = 64;
+    while (np2 < k) np2 <<= 1;
+    for (int32_t i = lane; i < np2; i += 32)
+        wsm[i] = i < k ? (((unsigned long long)a.tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
+    __syncwarp();
+    for (int32_t kk = 2; kk <= np2; kk <<= 1) {
+        for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+            for (int32_t i = lane; i < np2; i += 32) {
+                const int32_t ij = i ^ j;
+                if (ij > i) {
+                    const unsigned long long x = wsm[i], y = wsm[ij];
+                    if ((x > y) == ((i & kk) == 0)) { wsm[i] = y; wsm[ij] = x; }
                 }
-                __syncwarp();
             }
+            __syncwarp();
         }
-        for (int32_t r = lane; r < k; r += 32) {
-            const int32_t p = b0 + (int32_t)(wsm[r] & 0xFFFFFFFFull), q = b0 + r;
-            d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
-            d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = (uint32_t)(wsm[r] >> 32);
-        }
-        __syncwarp();
     }
+    for (int32_t r = lane; r < k; r += 32) {
+        const int32_t p = b0 + (int32_t)(wsm[r] & 0xFFFFFFFFull), q = q0 + r;
+        const uint32_t kk = (uint32_t)(wsm[r] >> 32);
+        d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
+        d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
+        d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
+    }
+    __syncwarp();
 }
 
 constexpr int kSortBig = 16384;  // one block sorts up to this many entries in shared memory
 
 // Leaves whose entering region is longer than one warp's shared-memory sort: one block per
-// leaf, bitonic network on (key, slot) pairs in dynamic shared memory, gather through `tmp`.
-// Regions longer than kSortBig rank every key against all others with the whole block.
+// leaf, bitonic network on (key, slot) pairs in dynamic shared memory, gather through the
+// scratch buffer.  Regions longer than kSortBig rank every key against all others.
 template <typename R>
-__global__ void __launch_bounds__(512) k_sort_big(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
-                                                  const int32_t *__restrict__ start,
-                                                  const int32_t *__restrict__ stay, SoA<R> d,
-                                                  uint32_t *__restrict__ key, SoA<R> tmp,
-                                                  uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
-                                                  const R *__restrict__ stay_lo, double *__restrict__ wsum) {
+__global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t) {
     extern __shared__ unsigned long long bk[];
     __shared__ R red_hi[16], red_lo[16];
-    const int32_t nbig = *count;
+    const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
+    const int32_t nbig = a.big[a.nleaf];
     for (int32_t li = blockIdx.x; li < nbig; li += gridDim.x) {
-        const int32_t L = list[li];
-        const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
-        const int32_t k = b1 - b0;
-        for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
-            tmp.u[p] = d.u[p]; tmp.v[p] = d.v[p]; tmp.vx[p] = d.vx[p]; tmp.vy[p] = d.vy[p];
-            tmp.vz[p] = d.vz[p]; tmp.w[p] = d.w[p]; tmp.id[p] = d.id[p]; tkey[p] = key[p];
+        const int32_t L = a.big[li];
+        int32_t b0, k, q0;
+        entering_region(a, L, b0, k, q0);
+        if (k < 0) continue;
+        for (int32_t p = b0 + threadIdx.x; p < b0 + k; p += blockDim.x) {
+            t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p];
+            t.vz[p] = d.vz[p]; t.w[p] = d.w[p]; t.id[p] = d.id[p]; a.tkey[p] = a.key[p]; a.taux[p] = a.aux[p];
         }
         __syncthreads();
         if (k <= kSortBig) {
             int32_t np2 = 1;
             while (np2 < k) np2 <<= 1;
             for (int32_t i = threadIdx.x; i < np2; i += blockDim.x)
-                bk[i] = i < k ? (((unsigned long long)tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
+                bk[i] = i < k ? (((unsigned long long)a.tkey[b0 + i] << 32) | (unsigned long long)i) : ~0ull;
             __syncthreads();
             for (int32_t kk = 2; kk <= np2; kk <<= 1) {
                 for (int32_t j = kk >> 1; j > 0; j >>= 1) {
@@ -562,79 +575,82 @@ __global__ void __launch_bounds__(512) k_sort_big(const int32_t *__restrict__ li
                 }
             }
             for (int32_t r = threadIdx.x; r < k; r += blockDim.x) {
-                const int32_t p = b0 + (int32_t)(bk[r] & 0xFFFFFFFFull), q = b0 + r;
-                d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
-                d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = (uint32_t)(bk[r] >> 32);
+                const int32_t p = b0 + (int32_t)(bk[r] & 0xFFFFFFFFull), q = q0 + r;
+                const uint32_t kk = (uint32_t)(bk[r] >> 32);
+                d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
+                d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
+                d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
             }
         } else {
-            for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
-                const uint32_t kk = tkey[p];
+            for (int32_t p = b0 + threadIdx.x; p < b0 + k; p += blockDim.x) {
+                const uint32_t kk = a.tkey[p];
                 int32_t rank = 0;
-                for (int32_t j = b0; j < b1; ++j) rank += (tkey[j] < kk) ? 1 : 0;
-                const int32_t q = b0 + rank;
-                d.u[q] = tmp.u[p]; d.v[q] = tmp.v[p]; d.vx[q] = tmp.vx[p]; d.vy[q] = tmp.vy[p];
-                d.vz[q] = tmp.vz[p]; d.w[q] = tmp.w[p]; d.id[q] = tmp.id[p]; key[q] = kk;
+                for (int32_t j = b0; j < b0 + k; ++j) rank += (a.tkey[j] < kk) ? 1 : 0;
+                const int32_t q = q0 + rank;
+                d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
+                d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
+                d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
             }
         }
         __syncthreads();
-        if (wsum) {  // entering weights in list order: per-thread Kahan, warps combined in order
+        if (a.wsum) {  // entering weights in list order: per-thread Kahan, warps combined in order
             R sum = 0, c = 0;
-            for (int32_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) kahan_add(sum, c, d.w[p]);
+            for (int32_t q = q0 + threadIdx.x; q < q0 + k; q += blockDim.x) kahan_add(sum, c, d.w[q]);
             R hi = sum, lo = -c;
             warp_two_sum(hi, lo);
             if ((threadIdx.x & 31) == 0) { red_hi[threadIdx.x >> 5] = hi; red_lo[threadIdx.x >> 5] = lo; }
             __syncthreads();
             if (threadIdx.x == 0) {
-                double t = (double)stay_hi[L] + (double)stay_lo[L];
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)red_hi[w] + (double)red_lo[w];
-                wsum[L] = t;
+                double tt = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += (double)red_hi[w] + (double)red_lo[w];
+                a.wsum[L] = tt;
             }
-            __syncthreads();
         }
+        if (threadIdx.x == 0) a.end[L] = q0 + k;
+        __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------------------------
-// Per-leaf sort of the entering slots [start + stay, start_next) by key (one warp per leaf).
-// Up to 32 entries sort in registers; longer runs go through the idle buffer `tmp`.
-// ------------------------------------------------------------------------------------
+// One warp per leaf: sorts the entering regions up to kSortSmem long (longer ones are
+// queued for k_sort_big), sets end[L] and, with stay sums, the leaf's deposit weight.
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_entering(int64_t nleaf, const int32_t *__restrict__ start,
-                                                      const int32_t *__restrict__ stay, SoA<R> d,
-                                                      uint32_t *__restrict__ key, SoA<R> tmp,
-                                                      uint32_t *__restrict__ tkey, const R *__restrict__ stay_hi,
-                                                      const R *__restrict__ stay_lo, double *__restrict__ wsum,
-                                                      int32_t *__restrict__ big_list, int32_t *__restrict__ big_count) {
+__global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<R> t) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
+    const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t L = warp; L < nleaf; L += nw) {
-        const int32_t b0 = start[L] + (stay ? stay[L] : 0), b1 = start[L + 1];
-        if (b1 - b0 > kSortSmem) {  // long region: k_sort_big sorts it and sums its weights
-            if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)L;
+    for (int64_t L = warp; L < a.nleaf; L += nw) {
+        int32_t b0, k, q0;
+        if (lane == 0) entering_region(a, L, b0, k, q0);
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
+        if (k < 0) continue;
+        if (k > kSortSmem) {  // long region: k_sort_big sorts it and sums its weights
+            if (lane == 0) a.big[atomicAdd(a.big + a.nleaf, 1)] = (int32_t)L;
             continue;
         }
-        sort_region(b0, b1, lane, d, key, tmp, tkey, sm_keys[threadIdx.x >> 5]);
-        if (wsum) {
+        if (k > 0) sort_region<R>(a, span, b0, k, q0, lane, d, t, sm_keys[threadIdx.x >> 5]);
+        if (a.wsum) {
             // the leaf's weight for the next deposit: staying sum + entering particles in order
             // (a few entering particles: one lane, in order; many: lanes, then an exact combine)
-            __syncwarp();
-            const int32_t k = b1 - b0;
+            const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
             if (k <= 16) {
                 if (lane == 0) {
                     R sum = 0, c = 0;
-                    for (int32_t p = b0; p < b1; ++p) kahan_add(sum, c, d.w[p]);
-                    wsum[L] = ((double)stay_hi[L] + (double)stay_lo[L]) + ((double)sum - (double)c);
+                    for (int32_t q = q0; q < q0 + k; ++q) kahan_add(sum, c, d.w[q]);
+                    a.wsum[L] = st + ((double)sum - (double)c);
                 }
             } else {
                 R sum = 0, c = 0;
-                for (int32_t p = b0 + lane; p < b1; p += 32) kahan_add(sum, c, d.w[p]);
+                for (int32_t q = q0 + lane; q < q0 + k; q += 32) kahan_add(sum, c, d.w[q]);
                 R hi = sum, lo = -c;
                 warp_two_sum(hi, lo);
-                if (lane == 0) wsum[L] = ((double)stay_hi[L] + (double)stay_lo[L]) + ((double)hi + (double)lo);
+                if (lane == 0) a.wsum[L] = st + ((double)hi + (double)lo);
             }
         }
+        if (lane == 0) a.end[L] = q0 + k;
     }
 }
 
@@ -680,45 +696,76 @@ __global__ void k_place_load(int64_t n, const double *__restrict__ x, const doub
     key[q] = (uint32_t)i;
 }
 
-// Read-back: absolute FP64 positions and leaf index per particle.
+// Read-back: absolute FP64 positions and leaf index per particle, at the particle's rank in
+// the concatenated lists (out0[L] = records before leaf L).
 template <typename R>
-__global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, double hf, int lmax,
-                       const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
-                       const uint8_t *__restrict__ lev, SoA<R> d, double *__restrict__ x, double *__restrict__ y,
-                       double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                       double *__restrict__ w, unsigned long long *__restrict__ id, uint32_t *__restrict__ leaf) {
+__global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                       const int32_t *__restrict__ out0, double hf, int lmax, const int32_t *__restrict__ ix,
+                       const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, SoA<R> d,
+                       double *__restrict__ x, double *__restrict__ y, double *__restrict__ vx,
+                       double *__restrict__ vy, double *__restrict__ vz, double *__restrict__ w,
+                       unsigned long long *__restrict__ id, uint32_t *__restrict__ leaf) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = warp; L < nleaf; L += nw) {
         const double s = (double)(1 << (lmax - lev[L]));
-        for (int32_t p = start[L] + lane; p < start[L + 1]; p += 32) {
-            x[p] = ((double)ix[L] + (double)d.u[p] * s) * hf;
-            y[p] = ((double)iy[L] + (double)d.v[p] * s) * hf;
-            vx[p] = (double)d.vx[p]; vy[p] = (double)d.vy[p]; vz[p] = (double)d.vz[p];
-            w[p] = (double)d.w[p];
-            id[p] = d.id[p];
-            leaf[p] = (uint32_t)L;
+        const int32_t p0 = start[L], o0 = out0[L];
+        for (int32_t p = p0 + lane; p < end[L]; p += 32) {
+            const int32_t o = o0 + (p - p0);
+            x[o] = ((double)ix[L] + (double)d.u[p] * s) * hf;
+            y[o] = ((double)iy[L] + (double)d.v[p] * s) * hf;
+            vx[o] = (double)d.vx[p]; vy[o] = (double)d.vy[p]; vz[o] = (double)d.vz[p];
+            w[o] = (double)d.w[p];
+            id[o] = d.id[p];
+            leaf[o] = (uint32_t)L;
         }
     }
 }
 
-// Order the entering regions of every leaf: long regions first (one block each), then the
-// warp-per-leaf pass (short regions, and the weight sums when wsum is given).
-template <typename R>
-void sort_lists(pic_ctx *ctx, int64_t nl, const int32_t *start, const int32_t *stay, SoA<R> d, uint32_t *key,
-                SoA<R> tmp, uint32_t *tkey, const R *shi, const R *slo, double *wsum, int32_t *list) {
-    // `list` holds nl + 1 ints: the long-region list and its counter at [nl]
-    GB_CUDA(cudaMemsetAsync(list + nl, 0, 4, ctx->stream));
-    k_sort_entering<R><<<warp_blocks(nl), kT, 0, ctx->stream>>>(nl, start, stay, d, key, tmp, tkey, shi, slo, wsum,
-                                                                list, list + nl);
+// Order the entering regions of every leaf: the warp-per-leaf pass (short regions, and the
+// weight sums when a.wsum is given), then the long regions (one block each).
+template <typename R> void sort_lists(pic_ctx *ctx, SortArgs a, SoA<R> d, SoA<R> t) {
+    GB_CUDA(cudaMemsetAsync(a.big + a.nleaf, 0, 4, ctx->stream));
+    k_sort_entering<R><<<warp_blocks(a.nleaf), kT, 0, ctx->stream>>>(a, d, t);
     const size_t smem = (size_t)kSortBig * sizeof(unsigned long long);
     GB_CUDA(cudaFuncSetAttribute(k_sort_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sort_big<R><<<152, 512, smem, ctx->stream>>>(list, list + nl, start, stay, d, key, tmp, tkey, shi, slo, wsum);
+    k_sort_big<R><<<152, 512, smem, ctx->stream>>>(a, d, t);
     count_launch(ctx, 2);
 }
 
-template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, int64_t step) {
+template <typename R> SortArgs sort_args(Instance &in, Species &sp) {
+    SortArgs a{};
+    a.nleaf = in.nleaf;
+    a.start = sp.start; a.stay = sp.stay; a.fill = sp.fill; a.end = sp.end; a.lim = sp.lim;
+    a.key = sp.key; a.aux = sp.aux; a.tkey = sp.key + sp.cap; a.taux = sp.aux + sp.cap;
+    a.span = nullptr;
+    a.spawn_base = nullptr;
+    a.next_id = in.d_next_id;
+    a.ion_bit = 0;
+    a.wsum = nullptr;
+    a.stay_hi = sp.stay_hi; a.stay_lo = sp.stay_lo;
+    a.big = sp.big;
+    a.err = in.d_err;
+    return a;
+}
+
+template <typename R> ListPut<R> list_put_args(Species &sp, int64_t nl) {
+    ListPut<R> o{};
+    o.d = soa<R>(sp, sp.cur);
+    o.key = sp.key; o.aux = sp.aux;
+    o.end = sp.end; o.lim = sp.lim;
+    o.fill = sp.fill;
+    o.moved = sp.moved;
+    o.nleaf = nl;
+    o.ovf = soa_ovf<R>(sp);
+    o.ovf_key = sp.ovf_key; o.ovf_aux = sp.ovf_aux; o.ovf_dest = sp.ovf_dest; o.ovf_slot = sp.ovf_slot;
+    o.ovf_n = sp.flags;
+    o.ovf_cap = (int32_t)sp.cap;
+    return o;
+}
+
+template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     const pic_config &c = in.cfg;
     Species &sp = in.sp[s];
     Level &g = in.lv[0];
@@ -731,16 +778,19 @@ template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, i
     a.py = c.bc_y == PIC_BC_PERIODIC;
     for (int l = 0; l <= kMaxLevel; ++l) a.dth[l] = (R)(c.dt / (in.h0 / (double)(1 << l)));
     a.qm_dt = (R)(c.q[s] / c.m[s] * c.dt);
-    a.start = sp.start;
+    a.start = sp.start; a.end = sp.end;
+    a.rank0 = sp.rank0;
+    a.ion_total = nullptr;
     a.map = g.map; a.ix = g.ix; a.iy = g.iy; a.lev = g.lev;
     a.stencil = (const R *)in.stencil;
-    a.in = soa<R>(sp, sp.cur);
-    a.out = soa<R>(sp, sp.cur ^ 1);
-    a.stay = sp.stay; a.inc = sp.inc; a.spawn = nullptr; a.inc_ion = nullptr;
-    a.key_out = sp.key;
-    a.start_new = sp.start_new;
-    a.stay_new = sp.stay;
-    a.fill = sp.fill;
+    a.d = soa<R>(sp, sp.cur);
+    a.self = list_put_args<R>(sp, in.nleaf);
+    a.ion = ListPut<R>{};
+    a.stay = sp.stay;
+    a.spawn = nullptr;
+    a.stay_hi = (R *)sp.stay_hi;
+    a.stay_lo = (R *)sp.stay_lo;
+    a.err = in.d_err;
     a.mcc = c.mcc ? 1 : 0;
     a.species = s;
     a.ng_dt = (R)(c.gas_density * c.dt);
@@ -757,17 +807,25 @@ template <typename R> PushArgs<R> push_args(pic_ctx *ctx, Instance &in, int s, i
     a.red_mn = (R)(c.neutral_mass / mt);
     a.g_partner_max = (R)(8.2 * std::sqrt(c.gas_temperature_ev * c.qe / c.neutral_mass));
     a.g_pad = (R)1.001;
+    a.p_pad = (R)1.0001;
     a.k0 = (uint32_t)(c.seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(c.seed >> 32);
     a.inst_word = (uint32_t)c.instance << 24;
-    a.cap = (int32_t)sp.cap;
-    a.stay_hi = (R *)sp.stay_hi;
-    a.stay_lo = (R *)sp.stay_lo;
-    a.ion_cap = in.cfg.n_species > 1 ? (int32_t)in.sp[1].cap : 0;
-    a.err = in.d_err;
     a.step = (uint32_t)step;
-    (void)ctx;
     return a;
+}
+
+// Per species before a push: no entering records yet, nothing in the overflow store, no
+// moved leaves, the tail not used up.
+__global__ void k_step_reset(int64_t nl, int32_t *__restrict__ fill, int32_t *__restrict__ flags,
+                             int32_t *__restrict__ moved) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nl) fill[i] = 0;
+    if (i == 0) {
+        flags[0] = 0;
+        flags[5] = 0;
+        moved[nl] = 0;
+    }
 }
 
 template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
@@ -781,17 +839,21 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
     {
-        Phase ph(ctx, PIC_PHASE_COUNT);
+        Phase ph(ctx, PIC_PHASE_MOVE);
         for (int s = 0; s < nsp; ++s) {
-            GB_CUDA(cudaMemsetAsync(in.sp[s].inc, 0, nl * 4, st));
-            GB_CUDA(cudaMemsetAsync(in.sp[s].fill, 0, nl * 4, st));
+            Species &sp = in.sp[s];
+            k_step_reset<<<blocks_for(nl), kT, 0, st>>>(nl, sp.fill, sp.flags, sp.moved);
+            count_launch(ctx);
+            list_ranks(ctx, sp, nl);
         }
         for (int s = 0; s < nsp; ++s) {
-            PushArgs<R> a = push_args<R>(ctx, in, s, step);
-            a.mode = 0;
+            PushArgs<R> a = push_args<R>(in, s, step);
             if (s == 0 && ionize) {
                 a.spawn = e.spawn;
-                a.inc_ion = ion ? ion->inc : nullptr;
+                if (ion) {
+                    a.ion = list_put_args<R>(*ion, nl);
+                    a.ion_total = ion->rank0 + nl;
+                }
             }
             k_push<R><<<pb, kT, 0, st>>>(a);
             count_launch(ctx);
@@ -799,88 +861,65 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     }
     {
         Phase ph(ctx, PIC_PHASE_SCAN);
-        for (int s = 0; s < nsp; ++s) {
-            Species &sp = in.sp[s];
-            k_add_counts<<<blocks_for(nl), kT, 0, st>>>(nl, sp.stay, sp.inc);  // inc := stay + inc
-            count_launch(ctx);
-            exclusive_scan_i32(ctx, sp.inc, sp.start_new, nl, sp.spawn_base + nl + 1);
-        }
         if (ionize) exclusive_scan_i32(ctx, e.spawn, e.spawn_base, nl, e.spawn_base + nl + 1 + scan_scratch_elems(nl));
+        for (int s = 0; s < nsp; ++s) place_overflow(ctx, in, s);
     }
     {
-        Phase ph(ctx, PIC_PHASE_MOVE);
-        for (int s = nsp - 1; s >= 0; --s) {
-            // ions first is not required; every write lands in its own slot
-            PushArgs<R> a = push_args<R>(ctx, in, s, step);
-            a.mode = 1;
-            if (s == 0 && ionize) {
+        Phase ph(ctx, PIC_PHASE_SORT);
+        for (int s = 0; s < nsp; ++s) {
+            Species &sp = in.sp[s];
+            SortArgs a = sort_args<R>(in, sp);
+            if (ionize) {
+                a.span = sp.rank0 + nl;  // the species total before the step
                 a.spawn_base = e.spawn_base;
-                a.next_id = in.d_next_id;
-                if (ion) {
-                    a.ion_out = soa<R>(*ion, ion->cur ^ 1);
-                    a.ion_key = ion->key;
-                    a.ion_start_new = ion->start_new;
-                    a.ion_stay = ion->stay;
-                    a.ion_start_old = ion->start;
-                    a.ion_fill = ion->fill;
-                }
             }
-            k_push<R><<<pb, kT, 0, st>>>(a);
-            count_launch(ctx);
+            a.ion_bit = s == 1 ? 1u : 0u;
+            a.wsum = sp.wsum;
+            sort_lists<R>(ctx, a, soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
+            sp.sums_valid = true;
         }
         if (ionize) {
             k_bump_next_id<<<1, 32, 0, st>>>(in.d_next_id, e.spawn_base + nl);
             count_launch(ctx);
         }
     }
-    {
-        Phase ph(ctx, PIC_PHASE_SORT);
-        for (int s = 0; s < nsp; ++s) {
-            Species &sp = in.sp[s];
-            // entering region of leaf L: [start_new[L] + stay[L], start_new[L + 1])
-            sort_lists<R>(ctx, nl, sp.start_new, sp.stay, soa<R>(sp, sp.cur ^ 1), sp.key, soa<R>(sp, sp.cur),
-                          sp.key + sp.cap, (const R *)sp.stay_hi, (const R *)sp.stay_lo, sp.wsum, sp.fill);
-            std::swap(sp.start, sp.start_new);
-            sp.cur ^= 1;
-            sp.sums_valid = true;
-        }
-    }
     check_launch("particle_step");
 }
 
-}  // namespace
-
-// Device memory of one species: the two record buffers, keys (2 x cap) and per-leaf arrays.
-void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
+// Give species s `cap` slots per buffer, keeping its lists (records, segments, ends).
+void grow_species(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
     Species &sp = in.sp[s];
-    DeviceArena &A = in.part_mem[s];
-    A.release_all();
+    if (cap >= (1ll << 31) - 1) fail(PIC_ECAPACITY, "particle slots beyond 2^31");
     const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
     const int64_t nl = in.nleaf;
-    sp.cap = cap;
-    for (int b = 0; b < 2; ++b) {
-        for (int k = 0; k < 6; ++k) sp.arr[b][k] = A.alloc(cap * rs + 64);
-        sp.id[b] = dalloc<uint32_t>(A, cap);
+    int32_t span = 0;  // first unused slot (segments and the tail)
+    GB_CUDA(cudaMemcpyAsync(&span, sp.flags + 4, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    DeviceArena old = in.part_mem[s];
+    Species os = sp;
+    in.part_mem[s].blocks.clear();
+    species_alloc(ctx, in, s, cap);
+    for (int k = 0; k < 6; ++k)
+        GB_CUDA(cudaMemcpyAsync(sp.arr[0][k], os.arr[os.cur][k], (size_t)span * rs, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.id[0], os.id[os.cur], (size_t)span * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.start, os.start, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.end, os.end, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.lim, os.lim, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(sp.spawn_base, os.spawn_base, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4,
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    if (os.sums_valid) {
+        GB_CUDA(cudaMemcpyAsync(sp.wsum, os.wsum, nl * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        sp.sums_valid = true;
     }
-    sp.key = dalloc<uint32_t>(A, 2 * cap);
-    sp.start = dalloc<int32_t>(A, nl + 1);
-    sp.start_new = dalloc<int32_t>(A, nl + 1);
-    sp.stay = dalloc<int32_t>(A, nl + 1);
-    sp.inc = dalloc<int32_t>(A, nl + 1);
-    sp.fill = dalloc<int32_t>(A, nl + 1);
-    sp.spawn = dalloc<int32_t>(A, nl + 1);
-    sp.stay_hi = A.alloc((nl + 1) * rs + 64);
-    sp.stay_lo = A.alloc((nl + 1) * rs + 64);
-    sp.wsum = dalloc<double>(A, nl + 1);
-    sp.sums_valid = false;
-    // spawn_base [nl + 1] | scan scratch | scan scratch
-    sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
-    GB_CUDA(cudaMemsetAsync(sp.start, 0, (nl + 1) * 4, ctx->stream));
-    GB_CUDA(cudaMemsetAsync(sp.spawn_base, 0, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4, ctx->stream));
-    sp.cur = 0;
-    sp.n = 0;
-    sp.n_upper = 0;
+    GB_CUDA(cudaMemcpyAsync(sp.flags, os.flags, 8 * 4, cudaMemcpyDeviceToDevice, ctx->stream));  // tail, statistics
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    sp.n = os.n;
+    sp.n_upper = os.n_upper;
+    old.release_all();
 }
+
+}  // namespace
 
 void walls_at(const Instance &in, int64_t step, double walls[4]) {
     const pic_config &c = in.cfg;
@@ -900,13 +939,17 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     unsigned long long next_id = 0;
     GB_CUDA(cudaMemcpyAsync(&next_id, in.d_next_id, 8, cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
-    int64_t cap = in.cfg.particle_capacity > 0 ? in.cfg.particle_capacity : std::max<int64_t>(2 * n + (1 << 16), 1 << 20);
-    if (cap < n) fail(PIC_ECAPACITY, "particle_capacity below the loaded population");
+    if (in.cfg.particle_capacity > 0 && in.cfg.particle_capacity < n)
+        fail(PIC_ECAPACITY, "particle_capacity below the loaded population");
+    // room for the population to double (every electron ionizing once) before a regrow
+    const int64_t cap = in.cfg.particle_capacity > 0 ? slots_for(in.cfg.particle_capacity, nl)
+                                                     : std::max<int64_t>(slots_for(2 * n + (1 << 16), nl), 1 << 20);
+    if (cap >= (1ll << 31) - 1) fail(PIC_ECAPACITY, "particle slots beyond 2^31");
     if (id)
         for (int64_t i = 0; i < n; ++i)
             if (id[i] >= (1ull << 32)) fail(PIC_EINVAL, "particle id >= 2^32");
     species_alloc(ctx, in, s, cap);
-    DeviceArena tmp;
+    DeviceArena tmp(&ctx->cache);
     double *d[6];
     const double *h[6] = {x, y, vx, vy, vz, w};
     for (int k = 0; k < 6; ++k) {
@@ -921,12 +964,13 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     int32_t *leaf = dalloc<int32_t>(tmp, n), *slot = dalloc<int32_t>(tmp, n);
     int32_t *err = dalloc<int32_t>(tmp, 1);
     GB_CUDA(cudaMemsetAsync(err, 0, 4, st));
-    GB_CUDA(cudaMemsetAsync(sp.inc, 0, nl * 4, st));
+    GB_CUDA(cudaMemsetAsync(sp.fill, 0, (nl + 1) * 4, st));
+    GB_CUDA(cudaMemsetAsync(sp.stay, 0, (nl + 1) * 4, st));
     Level &g = in.lv[0];
     const double hf = in.h0 / (double)(1 << in.lmax);
     if (n) {
         k_locate_load<<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], hf, in.nx0 << in.lmax, in.ny0 << in.lmax, g.map,
-                                                    leaf, sp.inc, slot, err);
+                                                    leaf, sp.fill, slot, err);
         count_launch(ctx);
     }
     int32_t herr = 0;
@@ -936,7 +980,11 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
         tmp.release_all();
         fail(PIC_EINVAL, "particle position outside the domain");
     }
-    exclusive_scan_i32(ctx, sp.inc, sp.start, nl, sp.spawn_base + nl + 1);
+    // segments with free slots; every loaded record enters its (empty) list: end = start,
+    // stay = 0, fill = count, then the entering sort orders each list by input index
+    lists_from_counts(ctx, sp, nl, sp.fill, sp.start, sp.end, sp.spawn_base + nl + 1);
+    lists_installed(ctx, sp, nl);
+    GB_CUDA(cudaMemcpyAsync(sp.end, sp.start, nl * 4, cudaMemcpyDeviceToDevice, st));
     const unsigned long long id0 = id ? 0ull : next_id;
     if (n) {
         if (in.cfg.precision == PIC_FP64)
@@ -948,13 +996,11 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
                                                               in.lmax, g.ix, g.iy, g.lev, leaf, slot, sp.start,
                                                               soa<float>(sp, 0), sp.key);
         count_launch(ctx);
-        if (in.cfg.precision == PIC_FP64)
-            sort_lists<double>(ctx, nl, sp.start, nullptr, soa<double>(sp, 0), sp.key, soa<double>(sp, 1),
-                               sp.key + sp.cap, nullptr, nullptr, nullptr, sp.fill);
-        else
-            sort_lists<float>(ctx, nl, sp.start, nullptr, soa<float>(sp, 0), sp.key, soa<float>(sp, 1),
-                              sp.key + sp.cap, nullptr, nullptr, nullptr, sp.fill);
     }
+    if (in.cfg.precision == PIC_FP64)
+        sort_lists<double>(ctx, sort_args<double>(in, sp), soa<double>(sp, 0), soa<double>(sp, 1));
+    else
+        sort_lists<float>(ctx, sort_args<float>(in, sp), soa<float>(sp, 0), soa<float>(sp, 1));
     unsigned long long nid = next_id;
     if (id) {
         for (int64_t i = 0; i < n; ++i) nid = std::max<unsigned long long>(nid, id[i] + 1);
@@ -977,6 +1023,7 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
     for (int s = 0; s < in.cfg.n_species; ++s) {
         if (!in.sp[s].start) continue;
         a.start[a.nsp] = in.sp[s].start;
+        a.end[a.nsp] = in.sp[s].end;
         a.w[a.nsp] = in.sp[s].arr[in.sp[s].cur][5];
         a.q[a.nsp] = in.cfg.q[s];
         ++a.nsp;
@@ -1004,45 +1051,42 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
 }
 
 // Make sure a step cannot overflow the particle buffers: the electron count can at most
-// double in one step (every electron ionizes once), the ion count grows by at most that.
+// double in one step (every electron ionizes once), the ion count grows by at most that, and
+// a re-layout gives every leaf its free slots again.
 void ensure_capacity(pic_ctx *ctx, Instance &in) {
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
-    if (!ionize) return;
     const int nsp = in.cfg.n_species;
-    const int64_t ne_up = in.sp[0].n_upper;
-    bool ok = 2 * ne_up <= in.sp[0].cap && (nsp < 2 || in.sp[1].n_upper + ne_up <= in.sp[1].cap);
+    const int64_t nl = in.nleaf;
+    auto worst = [&](int s) -> int64_t {
+        const int64_t ne = in.sp[0].n_upper;
+        if (!ionize) return in.sp[s].n_upper;
+        return s == 0 ? 2 * ne : in.sp[s].n_upper + ne;
+    };
+    const int64_t hard = in.cfg.particle_capacity;
+    bool ok = true;
+    for (int s = 0; s < nsp; ++s)
+        ok = ok && slots_for(worst(s), nl) <= in.sp[s].cap && (hard <= 0 || worst(s) <= hard);
     if (ok) return;
-    // read the exact counts
-    for (int s = 0; s < nsp; ++s) {
-        GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].start + in.nleaf, 4, cudaMemcpyDeviceToHost, ctx->stream));
-    }
+    // exact counts
+    count_totals(ctx, in);
+    for (int s = 0; s < nsp; ++s)
+        GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].flags + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     for (int s = 0; s < nsp; ++s) in.sp[s].n = in.sp[s].n_upper = in.cnt_host[s];
-    const int64_t ne = in.sp[0].n;
     for (int s = 0; s < nsp; ++s) {
         Species &sp = in.sp[s];
-        const int64_t need = s == 0 ? 2 * ne : sp.n + ne;
-        if (need <= sp.cap) continue;
-        if (in.cfg.particle_capacity > 0) fail(PIC_ECAPACITY, "particle population would exceed particle_capacity");
-        int64_t cap = std::max<int64_t>(2 * need, sp.cap * 2);
-        if (cap >= (1ll << 31)) fail(PIC_ECAPACITY, "particle population beyond 2^31");
-        // grow: copy the current records and list offsets into fresh buffers
-        const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
-        const int64_t n = sp.n, nl = in.nleaf;
-        DeviceArena old = in.part_mem[s];
-        Species os = sp;
-        in.part_mem[s].blocks.clear();
-        species_alloc(ctx, in, s, cap);
-        for (int k = 0; k < 6; ++k)
-            GB_CUDA(cudaMemcpyAsync(sp.arr[0][k], os.arr[os.cur][k], n * rs, cudaMemcpyDeviceToDevice, ctx->stream));
-        GB_CUDA(cudaMemcpyAsync(sp.id[0], os.id[os.cur], n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-        GB_CUDA(cudaMemcpyAsync(sp.start, os.start, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-        GB_CUDA(cudaMemcpyAsync(sp.spawn_base, os.spawn_base, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4,
-                                cudaMemcpyDeviceToDevice, ctx->stream));
-        GB_CUDA(cudaStreamSynchronize(ctx->stream));
-        sp.n = sp.n_upper = n;
-        old.release_all();
+        const int64_t need = worst(s);
+        if (hard > 0 && need > hard) fail(PIC_ECAPACITY, "particle population would exceed particle_capacity");
+        if (slots_for(need, nl) <= sp.cap) continue;
+        grow_species(ctx, in, s, std::max<int64_t>(slots_for(2 * need, nl), 2 * sp.cap));
     }
+}
+
+// Species s must hold `slots` slots (split/merge, adaptation): grow it if not.
+void ensure_slots(pic_ctx *ctx, Instance &in, int s, int64_t slots) {
+    Species &sp = in.sp[s];
+    if (slots <= sp.cap) return;
+    grow_species(ctx, in, s, std::max<int64_t>(slots + slots / 2, 2 * sp.cap));
 }
 
 void particle_step(pic_ctx *ctx, Instance &in, int64_t step) {
@@ -1056,26 +1100,39 @@ void particle_step(pic_ctx *ctx, Instance &in, int64_t step) {
     }
 }
 
+// Exact record totals into sp.n (one sync).
+void refresh_counts(pic_ctx *ctx, Instance &in) {
+    count_totals(ctx, in);
+    for (int s = 0; s < in.cfg.n_species; ++s)
+        if (in.sp[s].start)
+            GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].flags + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < in.cfg.n_species; ++s)
+        if (in.sp[s].start) in.sp[s].n = in.sp[s].n_upper = in.cnt_host[s];
+}
+
 void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, double *vx, double *vy,
                     double *vz, double *w, uint64_t *id, uint32_t *leaf) {
     Species &sp = in.sp[s];
     cudaStream_t st = ctx->stream;
-    const int64_t n = sp.n;
-    DeviceArena tmp;
+    const int64_t n = sp.n, nl = in.nleaf;
+    DeviceArena tmp(&ctx->cache);
     double *d[6];
     for (int k = 0; k < 6; ++k) d[k] = dalloc<double>(tmp, n);
     unsigned long long *did = dalloc<unsigned long long>(tmp, n);
     uint32_t *dleaf = dalloc<uint32_t>(tmp, n);
+    list_ranks(ctx, sp, nl);
+    const int32_t *out0 = sp.rank0;
     Level &g = in.lv[0];
     const double hf = in.h0 / (double)(1 << in.lmax);
     if (in.cfg.precision == PIC_FP64)
-        k_read<double><<<warp_blocks(in.nleaf), kT, 0, st>>>(in.nleaf, sp.start, hf, in.lmax, g.ix, g.iy, g.lev,
-                                                             soa<double>(sp, sp.cur), d[0], d[1], d[2], d[3], d[4],
-                                                             d[5], did, dleaf);
+        k_read<double><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, sp.end, out0, hf, in.lmax, g.ix, g.iy, g.lev,
+                                                       soa<double>(sp, sp.cur), d[0], d[1], d[2], d[3], d[4], d[5],
+                                                       did, dleaf);
     else
-        k_read<float><<<warp_blocks(in.nleaf), kT, 0, st>>>(in.nleaf, sp.start, hf, in.lmax, g.ix, g.iy, g.lev,
-                                                            soa<float>(sp, sp.cur), d[0], d[1], d[2], d[3], d[4], d[5],
-                                                            did, dleaf);
+        k_read<float><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, sp.end, out0, hf, in.lmax, g.ix, g.iy, g.lev,
+                                                      soa<float>(sp, sp.cur), d[0], d[1], d[2], d[3], d[4], d[5],
+                                                      did, dleaf);
     count_launch(ctx);
     double *h[6] = {x, y, vx, vy, vz, w};
     for (int k = 0; k < 6; ++k)

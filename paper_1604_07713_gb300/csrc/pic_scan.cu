@@ -36,7 +36,9 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *tota
     return before;
 }
 
-__global__ void k_tile_sums(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ part) {
+__global__ void k_tile_sums(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ part,
+                            const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int32_t s = 0;
 #pragma unroll
@@ -48,7 +50,9 @@ __global__ void k_tile_sums(const int32_t *__restrict__ in, int64_t n, int32_t *
 }
 
 // One block scans the tile totals in chunks, carrying the running sum.
-__global__ void k_scan_parts(int32_t *__restrict__ part, int64_t nparts, int32_t *__restrict__ total) {
+__global__ void k_scan_parts(int32_t *__restrict__ part, int64_t nparts, int32_t *__restrict__ total,
+                             const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     int32_t carry = 0;
     for (int64_t c0 = 0; c0 < nparts; c0 += kScanThreads) {
         const int64_t i = c0 + threadIdx.x;
@@ -62,7 +66,8 @@ __global__ void k_scan_parts(int32_t *__restrict__ part, int64_t nparts, int32_t
 }
 
 __global__ void k_tile_scan(const int32_t *__restrict__ in, int64_t n, const int32_t *__restrict__ part,
-                            int32_t *__restrict__ out) {
+                            int32_t *__restrict__ out, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int32_t v[kScanItems], s = 0;
 #pragma unroll
@@ -83,16 +88,19 @@ __global__ void k_tile_scan(const int32_t *__restrict__ in, int64_t n, const int
 int64_t scan_scratch_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
 
 // out[0..n-1] = exclusive prefix of in, out[n] = total.  scratch: scan_scratch_elems(n).
-// `in` and `out` may alias.
-void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *scratch) {
+// `in` and `out` may alias.  With a gate, the kernels do nothing while *gate == 0 (a
+// decision the device takes after the launches were queued).
+void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *scratch,
+                        const int32_t *gate) {
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 0) {
+        if (gate) fail(PIC_EINVAL, "gated scan of an empty array");
         GB_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), ctx->stream));
         return;
     }
-    k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch);
-    k_scan_parts<<<1, kScanThreads, 0, ctx->stream>>>(scratch, tiles, out + n);
-    k_tile_scan<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch, out);
+    k_tile_sums<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch, gate);
+    k_scan_parts<<<1, kScanThreads, 0, ctx->stream>>>(scratch, tiles, out + n, gate);
+    k_tile_scan<<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, scratch, out, gate);
     count_launch(ctx, 3);
     check_launch("exclusive_scan_i32");
 }

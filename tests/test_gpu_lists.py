@@ -1,0 +1,117 @@
+"""Cell lists with free slots (§3.1 list update) under overflow: a beam crosses into leaves
+whose free slots cannot take it, so the step stores the extra records in the overflow store
+and moves those leaves to the tail of the buffer, or, with a tight capacity, lays the
+species out again.  The result must not depend on that: cell-list order (ids), leaves and
+spawned ids bit-exact against the oracle, positions and velocities within rounding."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1604_07713_gb300 as G
+from paper_1604_07713_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    G.build()
+    O.build()
+
+
+def _beam_case(precision, ionize, seed=11):
+    """8 x 2 leaves of 1 mm, absorbing walls at x = 0 and 8 mm (0 V), periodic in y.
+    300 electrons at 100 eV moving +x by 1 mm per step from x in [1.2, 1.8] mm, on top of 5
+    electrons and 5 ions per leaf at rest-ish; with ionization, most beam electrons spawn a
+    pair per step."""
+    rng = np.random.default_rng(seed)
+    h = 1e-3
+    v = math.sqrt(2.0 * 100.0 * W.QE / W.ME)
+    dt = h / v
+    nb = 300
+    xb = (1.2 + 0.6 * rng.random(nb)) * h
+    yb = (0.05 + 1.9 * rng.random(nb)) * h
+    nbg = 5 * 16
+    parts = {}
+    for s, m in enumerate((W.ME, 4.0 * W.AMU)):
+        xg = (0.05 + 7.9 * rng.random(nbg)) * h
+        yg = (0.05 + 1.9 * rng.random(nbg)) * h
+        vt = math.sqrt(0.05 * W.QE / m)
+        vg = rng.standard_normal((3, nbg)) * vt
+        if s == 0:
+            x = np.concatenate([xb, xg]); y = np.concatenate([yb, yg])
+            vx = np.concatenate([np.full(nb, v), vg[0]])
+            vy = np.concatenate([np.zeros(nb), vg[1]]); vz = np.concatenate([np.zeros(nb), vg[2]])
+        else:
+            x, y, vx, vy, vz = xg, yg, vg[0], vg[1], vg[2]
+        parts[s] = dict(x=x, y=y, vx=vx, vy=vy, vz=vz, w=np.full(x.size, 1.0))
+    cfg = W.base_config(precision=precision, n_species=2, dt=dt, eps0=W.EPS0, q=[-W.QE, W.QE],
+                        m=[W.ME, 4.0 * W.AMU], qe=W.QE, mcc=1 if ionize else 0, bc_x=W.BC_DIRICHLET,
+                        bc_y=W.BC_PERIODIC, gas_density=1e22, gas_temperature_ev=0.026,
+                        neutral_mass=4.0 * W.AMU, sigma_el=1e-21, sigma_iz0=1e-19, eps_th_ev=24.6,
+                        mg_rel_tol=1e-13 if precision == W.FP64 else 1e-10)
+    mesh = dict(nx0=8, ny0=2, h0=h, lmax=0)
+    return cfg, mesh, parts
+
+
+def _run_pair(cfg, mesh, parts, steps):
+    M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, cfg["bc_x"], cfg["bc_y"])
+    sim = O.Sim(cfg, M)
+    for s in sorted(parts):
+        sim.load(s, **parts[s])
+    out = []
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s in sorted(parts):
+            ctx.load(s, **parts[s])
+        for _ in range(steps):
+            sim.step(1)
+            ctx.step(1)
+            out.append(([ctx.particles(s) for s in (0, 1)],
+                        [(sp.id.copy(), sp.leaf.copy(), sp.x.copy(), sp.vx.copy()) for sp in sim.species]))
+        stats = [G.pic_get_list_stats(ctx.ctx, 0, s) for s in (0, 1)]
+    return out, stats
+
+
+def _check(res, precision):
+    tol = 1e-12 if precision == W.FP64 else 1e-6
+    for g, o in res:
+        for s in (0, 1):
+            ids, leaf, x, vx = o[s]
+            assert np.array_equal(g[s]["id"], ids), f"species {s}: cell-list order / ids"
+            assert np.array_equal(g[s]["leaf"].astype(np.int64), leaf)
+            assert np.abs(g[s]["x"] - x).max() <= tol * 8e-3
+            assert np.abs(g[s]["vx"] - vx).max() <= tol * max(1.0, np.abs(vx).max())
+
+
+@pytest.mark.parametrize("precision", [W.FP32, W.FP64])
+def test_beam_overflow_moves_leaves_to_the_tail(precision):
+    cfg, mesh, parts = _beam_case(precision, ionize=False)
+    res, stats = _run_pair(cfg, mesh, parts, 3)
+    _check(res, precision)
+    # the beam really overflowed: ~150 records entered leaves with 16 + c // 4 free slots
+    g, _ = res[-1]
+    assert np.bincount(g[0]["leaf"].astype(np.int64), minlength=16).max() >= 100
+    relayouts, moves, overflowed = stats[0]
+    assert moves >= 3 and overflowed > 100 and relayouts == 0
+
+
+def test_beam_overflow_with_a_tight_capacity_lays_the_lists_out_again():
+    cfg, mesh, parts = _beam_case(W.FP64, ionize=False)
+    cfg["particle_capacity"] = parts[0]["x"].size + 40  # little room at the tail
+    res, stats = _run_pair(cfg, mesh, parts, 3)
+    _check(res, W.FP64)
+    assert stats[0][0] >= 1  # at least one re-layout of the electron lists
+
+
+def test_beam_overflow_with_ionization_spawn_ids_fp64():
+    cfg, mesh, parts = _beam_case(W.FP64, ionize=True)
+    n0 = [parts[s]["x"].size for s in (0, 1)]
+    res, stats = _run_pair(cfg, mesh, parts, 3)
+    _check(res, W.FP64)
+    g, _ = res[-1]
+    assert g[1]["id"].size - n0[1] > 150, "the beam must spawn many pairs"
+    assert np.unique(np.concatenate([g[0]["id"], g[1]["id"]])).size == g[0]["id"].size + g[1]["id"].size
+    assert stats[1][1] >= 2  # the spawned ions overflowed their leaves too
