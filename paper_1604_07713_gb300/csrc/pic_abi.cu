@@ -236,6 +236,10 @@ double collect_solver_stats(pic_ctx *ctx, Instance &in) {
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     in.mg_cycles = (int)in.red_host[4];
     in.mg_res = in.red_host[5];
+    if (in.mg_count_cycles) {  // kernels of the device-side cycle loop of the last solve
+        ctx->launches += (int64_t)in.mg_cycles * in.mg_cycle_nodes;
+        in.mg_count_cycles = false;
+    }
     return std::max(in.mg_res_max, in.red_host[6]);
 }
 

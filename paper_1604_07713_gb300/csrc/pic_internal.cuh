@@ -181,6 +181,8 @@ struct Instance {
     size_t small_smem = 0;               // and its dynamic shared memory
     cudaGraphExec_t mg_cycle = nullptr;  // multi-block meshes: one captured cycle (V-cycle,
     int64_t mg_cycle_nodes = 0;          // correction, residual, norm read-back) and its launches
+    int64_t mg_pre_nodes = 0;            // launches before the device-side cycle loop
+    bool mg_count_cycles = false;        // add the device loop's cycles to the launch count
     DeviceArena mesh_mem;        // freed on pic_set_mesh
     DeviceArena part_mem[2];     // freed on reload / regrow
 };
@@ -253,8 +255,10 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
                                             uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        // both halves of each 32 x 32 -> 64-bit product from one wide multiply
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
         k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;

@@ -32,10 +32,10 @@ inline unsigned warp_blocks(int64_t nw) {
 __global__ void k_seg_sizes(int64_t nl, const int32_t *__restrict__ a, const int32_t *__restrict__ b, int room,
                             int32_t *__restrict__ seg, const int32_t *__restrict__ gate) {
     if (gate && *gate == 0) return;
-    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nl) return;
-    const int32_t c = a[L] + (b ? b[L] : 0);
-    seg[L] = c + list_slack(c) + (room ? b[L] : 0);
+    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < nl; L += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = a[L] + (b ? b[L] : 0);
+        seg[L] = c + list_slack(c) + (room ? b[L] : 0);
+    }
 }
 
 // A re-layout whose inflow room does not fit the buffer lays out without it (flags[7]).
@@ -245,14 +245,17 @@ template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
                                            sp.key, sp.aux, sp.moved, nl, sp.flags);
     // tail used up: every list again, in leaf order (gated on flags[5])
     int32_t *scr = sp.spawn_base + nl + 1 + scan_scratch_elems(nl);
-    k_seg_sizes<<<blocks_for(nl), kT, 0, st>>>(nl, sp.stay, sp.fill, 1, sp.inc, sp.flags + 5);
+    // gated launches get small grids: a launch that returns at once still schedules every block
+    const unsigned gb = std::min<unsigned>(blocks_for(nl), 152u * 2u);
+    k_seg_sizes<<<gb, kT, 0, st>>>(nl, sp.stay, sp.fill, 1, sp.inc, sp.flags + 5);
     exclusive_scan_i32(ctx, sp.inc, sp.start_new, nl, scr, sp.flags + 5);
     k_relayout_fit<<<1, 32, 0, st>>>(sp.start_new, nl, sp.cap, sp.flags);
-    k_seg_sizes<<<blocks_for(nl), kT, 0, st>>>(nl, sp.stay, sp.fill, 0, sp.inc, sp.flags + 7);
+    k_seg_sizes<<<gb, kT, 0, st>>>(nl, sp.stay, sp.fill, 0, sp.inc, sp.flags + 7);
     exclusive_scan_i32(ctx, sp.inc, sp.start_new, nl, scr, sp.flags + 7);
     uint32_t *tkey = sp.key + sp.cap, *taux = sp.aux + sp.cap;
-    k_relayout_move<R><<<warp_blocks(nl), kT, 0, st>>>(nl, sp.start, sp.end, sp.lim, sp.stay, sp.fill, sp.start_new,
-                                                       sp.cap, d, sp.key, sp.aux, t, tkey, taux, sp.flags, in.d_err);
+    k_relayout_move<R><<<std::min<unsigned>(warp_blocks(nl), 152u * 8u), kT, 0, st>>>(
+        nl, sp.start, sp.end, sp.lim, sp.stay, sp.fill, sp.start_new, sp.cap, d, sp.key, sp.aux, t, tkey, taux,
+        sp.flags, in.d_err);
     k_relayout_ovf<R><<<152 * 4, kT, 0, st>>>(sp.stay, sp.start_new, nl, sp.cap, o, sp.ovf_key, sp.ovf_aux,
                                               sp.ovf_dest, sp.ovf_slot, t, tkey, taux, sp.flags);
     k_relayout_back<R><<<152 * 8, kT, 0, st>>>(nl, sp.start_new, sp.stay, sp.cap, t, tkey, taux, d, sp.key, sp.aux,

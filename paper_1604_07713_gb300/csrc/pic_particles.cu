@@ -50,6 +50,9 @@ __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ void m_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
 __device__ __forceinline__ void m_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+// a / b: FP32 with the fast reciprocal-based division (2 ulp), FP64 correctly rounded
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 template <typename R> __device__ __forceinline__ R below_one();
 template <> __device__ __forceinline__ float below_one<float>() { return 0.99999994f; }
@@ -205,6 +208,7 @@ template <typename R> struct PushArgs {
     int32_t *spawn;       // electrons with ionization: per leaf, spawning electrons
     R *stay_hi, *stay_lo; // compensated weight sum of each leaf's staying particles
     int32_t *err;
+    int self_wrap;        // some leaf spans a whole periodic direction (a particle may wrap back)
     // collisions
     int mcc, species;
     R ng_dt, sig_el, sig_iz0, eps_th, half_m_over_qe, two_qe_over_m, two_m_over_mn;
@@ -233,16 +237,123 @@ template <typename R> __device__ __forceinline__ void normals3(const U4 &r, R n[
     n[0] = r1 * c1; n[1] = r1 * s1; n[2] = r2 * c3;
 }
 
+// Work that only some particles of a warp have, deferred so that it runs 32 particles at a
+// time instead of with one or two lanes of a chunk: the location of a particle that left its
+// leaf and its list slot there, and every collision beyond the test (the scattering, the
+// ionization with its pair, the ion's partner draw and exact test).  A per-warp ring of
+// kQueue entries in shared memory holds them, in list order.
+constexpr int kQueue = 64;
+
+template <typename R> struct Queue {
+    R a[kQueue], b[kQueue];  // leaver: X, Y (old leaf's finest-lattice units); stayer: new u, v
+    R vx[kQueue], vy[kQueue], vz[kQueue], w[kQueue];
+    R U0[kQueue], U2[kQueue], U3[kQueue];
+    uint32_t id[kQueue], key[kQueue], info[kQueue];  // info: bit 0 collides / candidate, 1 spawns, rank << 2
+    int32_t L[kQueue], dst[kQueue], I[kQueue], J[kQueue];  // dst: a stayer's slot, -1 for a leaver
+};
+
+// Deferred work of queue entry e (one lane).
+template <typename R> __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R> &q, int e,
+                                                                   uint32_t span, uint32_t ion_span) {
+    R vx = q.vx[e], vy = q.vy[e], vz = q.vz[e];
+    const R w = q.w[e];
+    const uint32_t id = q.id[e], info = q.info[e];
+    const int32_t L = q.L[e], dst = q.dst[e];
+    R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+    if (info & 1u) {
+        const R v2 = vx * vx + vy * vy + vz * vz;
+        if (a.species == 0) {
+            const R eps = a.half_m_over_qe * v2;
+            const R speed = m_sqrt(v2);
+            const R U2 = q.U2[e];
+            if (info & 2u) {
+                const R rest = eps - a.eps_th;
+                const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
+                const U4 r1 = philox4x32_10(id, a.inst_word, a.step, 1u, a.k0, a.k1);
+                R d1[3], d2[3], nn[3];
+                iso_dir<R>(u24<R>(r1.x), u24<R>(r1.y), d1);
+                iso_dir<R>(u24<R>(r1.z), u24<R>(r1.w), d2);
+                const R s1 = m_sqrt(a.two_qe_over_m * e1), s2 = m_sqrt(a.two_qe_over_m * e2);
+                vx = s1 * d1[0]; vy = s1 * d1[1]; vz = s1 * d1[2];
+                sv[0] = s2 * d2[0]; sv[1] = s2 * d2[1]; sv[2] = s2 * d2[2];
+                const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
+                normals3<R>(r2, nn);
+                si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
+            } else {
+                R d[3];
+                iso_dir<R>(U2, q.U3[e], d);
+                const R cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
+                const R eps2 = eps * ((R)1 - a.two_m_over_mn * ((R)1 - cchi));
+                const R s2 = m_sqrt(a.two_qe_over_m * eps2);
+                vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
+            }
+        } else {
+            // the partner is drawn and the exact test decides (the test in the pass was a bound)
+            const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
+            R nn[3];
+            normals3<R>(r2, nn);
+            const R vnx = a.vt_gas * nn[0], vny = a.vt_gas * nn[1], vnz = a.vt_gas * nn[2];
+            const R gx = vx - vnx, gy = vy - vny, gz = vz - vnz;
+            const R gm = m_sqrt(gx * gx + gy * gy + gz * gz);
+            const R P = -m_expm1(-a.ng_dt * a.sig_el * gm);
+            if (q.U0[e] < P) {
+                R d[3];
+                iso_dir<R>(q.U2[e], q.U3[e], d);
+                const R cx = a.red_m * vx + a.red_mn * vnx, cy = a.red_m * vy + a.red_mn * vny,
+                        cz = a.red_m * vz + a.red_mn * vnz;
+                vx = cx + a.red_a * gm * d[0];
+                vy = cy + a.red_a * gm * d[1];
+                vz = cz + a.red_a * gm * d[2];
+            }
+        }
+    }
+    int32_t nl;
+    R u, v;
+    if (dst >= 0) {  // staying: the record is in place except its velocity
+        a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz;
+        nl = L;
+        u = q.a[e]; v = q.b[e];
+    } else {         // entering: locate, re-express the offsets in the new leaf, take a slot
+        const R X = q.a[e], Y = q.b[e];
+        const int32_t I = q.I[e], J = q.J[e];
+        nl = __ldg(a.map + (int64_t)J * a.NX + I);
+        const int32_t s2 = 1 << (a.lmax - a.lev[nl]);
+        const R inv_s2 = (R)1 / (R)s2;
+        // I - floor(X) is the old leaf's corner after the periodic wrap
+        R un2 = ((R)(I - (int32_t)m_floor(X) - a.ix[nl]) + X) * inv_s2;
+        R vn2 = ((R)(J - (int32_t)m_floor(Y) - a.iy[nl]) + Y) * inv_s2;
+        un2 = un2 < (R)0 ? (R)0 : (un2 >= (R)1 ? below_one<R>() : un2);
+        vn2 = vn2 < (R)0 ? (R)0 : (vn2 >= (R)1 ? below_one<R>() : vn2);
+        u = un2; v = vn2;
+        list_put(a.self, nl, u, v, vx, vy, vz, w, id, q.key[e], 0u, a.err);
+    }
+    if (info & 2u) {
+        // the pair's ids follow from the parent's spawn rank once all leaves are counted:
+        // the rank within the parent's leaf travels in the id word, the leaf in the aux word
+        const uint32_t rank = info >> 2;
+        list_put(a.self, nl, u, v, sv[0], sv[1], sv[2], w, rank, span + q.key[e], (uint32_t)L, a.err);
+        if (a.ion.fill)
+            list_put(a.ion, nl, u, v, si[0], si[1], si[2], w, rank, ion_span + q.key[e], (uint32_t)L, a.err);
+    }
+}
+
 // One warp per leaf (persistent warps).  A staying particle's record goes to slot
 // start[L] + its rank among the leaf's staying particles, which is never past its own slot,
 // so the leaf's own records are compacted in place; everything the warp reads of the next
 // chunk lies beyond every slot it writes in this one.  Entering and spawned records only go
 // to free slots past end[], which no warp reads during the pass.
 template <typename R>
-__global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
+__global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
+    extern __shared__ unsigned char push_smem[];
+    Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // order keys: an entering record's list rank before the step; a spawned record's is the
+    // species total plus its parent's rank, so it sorts after every entering record
+    const uint32_t span = (uint32_t)a.rank0[a.nleaf];
+    const uint32_t ion_span = a.ion_total ? (uint32_t)*a.ion_total : 0u;
+    int qhead = 0, qn = 0;  // ring of deferred entries
     // persistent warps: the next leaf's list bounds are fetched while this leaf runs
     int32_t np0 = 0, np1 = 0;
     if (warp < a.nleaf) { np0 = a.start[warp]; np1 = a.end[warp]; }
@@ -259,11 +370,7 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
             continue;
         }
         R ws_sum = 0, ws_c = 0;  // staying particles' weights, in list order per lane
-        // order keys: an entering record's list rank before the step; a spawned record's is
-        // the species total plus its parent's rank, so it sorts after every entering record
         const uint32_t key0 = (uint32_t)(a.rank0[L] - p0);
-        const uint32_t span = (uint32_t)a.rank0[a.nleaf];
-        const uint32_t ion_span = a.ion_total ? (uint32_t)*a.ion_total : 0u;
         const int lv = a.lev[L];
         const int32_t s = 1 << (a.lmax - lv);
         const int32_t lx = a.ix[L], ly = a.iy[L];
@@ -276,23 +383,23 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
         R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nwt = 0;
         uint32_t nid = 0;
         if (p0 + lane < p1) {
-            const int32_t q = p0 + lane;
-            nu = a.d.u[q]; nv = a.d.v[q]; nvx = a.d.vx[q]; nvy = a.d.vy[q]; nvz = a.d.vz[q];
-            nid = a.d.id[q]; nwt = a.d.w[q];
+            const int32_t qq = p0 + lane;
+            nu = a.d.u[qq]; nv = a.d.v[qq]; nvx = a.d.vx[qq]; nvy = a.d.vy[qq]; nvz = a.d.vz[qq];
+            nid = a.d.id[qq]; nwt = a.d.w[qq];
         }
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
             const bool live = p < p1;
-            bool alive = false, stays = false, spawns = false;
-            int32_t nl = -1;
+            bool alive = false, stays = false, spawns = false, coll = false;
             R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nwt;
             uint32_t id = nid;
             if (p + 32 < p1) {
-                const int32_t q = p + 32;
-                nu = a.d.u[q]; nv = a.d.v[q]; nvx = a.d.vx[q]; nvy = a.d.vy[q]; nvz = a.d.vz[q];
-                nid = a.d.id[q]; nwt = a.d.w[q];
+                const int32_t qq = p + 32;
+                nu = a.d.u[qq]; nv = a.d.v[qq]; nvx = a.d.vx[qq]; nvy = a.d.vy[qq]; nvz = a.d.vz[qq];
+                nid = a.d.id[qq]; nwt = a.d.w[qq];
             }
-            R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+            R X = 0, Y = 0, U0 = 0, U2 = 0, U3 = 0;
+            int32_t I = 0, J = 0;
             if (live) {
                 // gather: bilinear in the leaf's corner field
                 const R w00 = ((R)1 - u) * ((R)1 - v), w10 = u * ((R)1 - v), w01 = ((R)1 - u) * v, w11 = u * v;
@@ -301,119 +408,85 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
                 // leapfrog kick and drift in leaf units
                 vx += a.qm_dt * ex;
                 vy += a.qm_dt * ey;
-                R un = u + vx * dth, vn = v + vy * dth;
+                const R un = u + vx * dth, vn = v + vy * dth;
                 alive = true;
                 if (un >= (R)0 && un < (R)1 && vn >= (R)0 && vn < (R)1) {
                     stays = true;
-                    nl = L;
                     u = un; v = vn;
                 } else {
-                    // locate on the finest lattice relative to this leaf, then re-express
-                    const R X = un * (R)s, Y = vn * (R)s;  // exact: s is a power of two
-                    const R fx = m_floor(X), fy = m_floor(Y);
-                    int32_t I = lx + (int32_t)fx, J = ly + (int32_t)fy;
-                    int32_t wx = 0, wy = 0;
+                    // the finest-lattice cell, wrapped or absorbed at the walls
+                    X = un * (R)s; Y = vn * (R)s;  // exact: s is a power of two
+                    I = lx + (int32_t)m_floor(X); J = ly + (int32_t)m_floor(Y);
                     if (I < 0 || I >= a.NX) {
                         if (!a.px) alive = false;
-                        else { wx = I < 0 ? a.NX : -a.NX; I += wx; if (I < 0 || I >= a.NX) alive = false; }
+                        else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) alive = false; }
                     }
                     if (J < 0 || J >= a.NY) {
                         if (!a.py) alive = false;
-                        else { wy = J < 0 ? a.NY : -a.NY; J += wy; if (J < 0 || J >= a.NY) alive = false; }
+                        else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) alive = false; }
                     }
-                    if (alive) {
-                        nl = __ldg(a.map + (int64_t)J * a.NX + I);
-                        const int32_t s2 = 1 << (a.lmax - a.lev[nl]);
-                        const R inv_s2 = (R)1 / (R)s2;
-                        R un2 = ((R)(lx + wx - a.ix[nl]) + X) * inv_s2;
-                        R vn2 = ((R)(ly + wy - a.iy[nl]) + Y) * inv_s2;
-                        un2 = un2 < (R)0 ? (R)0 : (un2 >= (R)1 ? below_one<R>() : un2);
-                        vn2 = vn2 < (R)0 ? (R)0 : (vn2 >= (R)1 ? below_one<R>() : vn2);
-                        u = un2; v = vn2;
-                        stays = nl == L;
+                    // a leaf as wide as a periodic domain can take its own particle back
+                    if (a.self_wrap && alive && I >= lx && I < lx + s && J >= ly && J < ly + s) {
+                        const R inv = (R)1 / (R)s;
+                        R un2 = ((R)(I - (int32_t)m_floor(X) - lx) + X) * inv;
+                        R vn2 = ((R)(J - (int32_t)m_floor(Y) - ly) + Y) * inv;
+                        u = un2 < (R)0 ? (R)0 : (un2 >= (R)1 ? below_one<R>() : un2);
+                        v = vn2 < (R)0 ? (R)0 : (vn2 >= (R)1 ? below_one<R>() : vn2);
+                        stays = true;
                     }
                 }
-                const R v2 = vx * vx + vy * vy + vz * vz;
                 if (alive && a.mcc) {
+                    const R v2 = vx * vx + vy * vy + vz * vz;
                     const U4 r0 = philox4x32_10(id, a.inst_word, a.step, 0u, a.k0, a.k1);
-                    const R U0 = u24<R>(r0.x), U1 = u24<R>(r0.y), U2 = u24<R>(r0.z), U3 = u24<R>(r0.w);
+                    U0 = u24<R>(r0.x);
+                    U2 = u24<R>(r0.z); U3 = u24<R>(r0.w);
                     if (a.species == 0) {
                         const R eps = a.half_m_over_qe * v2;
-                        const R speed = m_sqrt(v2);
-                        const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - a.eps_th / eps) : (R)0;
+                        const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - m_div(a.eps_th, eps)) : (R)0;
                         const R st = a.sig_el + siz;
-                        const R xc = a.ng_dt * st * speed;
+                        const R xc = a.ng_dt * st * m_sqrt(v2);
                         // 1 - exp(-x) <= x: a uniform at or above x (with a rounding margin)
                         // already means no collision, without evaluating the exponential
-                        if (U0 < xc * a.p_pad && U0 < -m_expm1(-xc)) {
-                            if (U1 * st < siz) {
-                                const R rest = eps - a.eps_th;
-                                const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
-                                const U4 r1 = philox4x32_10(id, a.inst_word, a.step, 1u, a.k0, a.k1);
-                                R d1[3], d2[3], nn[3];
-                                iso_dir<R>(u24<R>(r1.x), u24<R>(r1.y), d1);
-                                iso_dir<R>(u24<R>(r1.z), u24<R>(r1.w), d2);
-                                const R s1 = m_sqrt(a.two_qe_over_m * e1), s2 = m_sqrt(a.two_qe_over_m * e2);
-                                vx = s1 * d1[0]; vy = s1 * d1[1]; vz = s1 * d1[2];
-                                sv[0] = s2 * d2[0]; sv[1] = s2 * d2[1]; sv[2] = s2 * d2[2];
-                                const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
-                                normals3<R>(r2, nn);
-                                si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
-                                spawns = true;
-                            } else {
-                                R d[3];
-                                iso_dir<R>(U2, U3, d);
-                                const R cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
-                                const R eps2 = eps * ((R)1 - a.two_m_over_mn * ((R)1 - cchi));
-                                const R s2 = m_sqrt(a.two_qe_over_m * eps2);
-                                vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
-                            }
-                        }
-                    } else if (U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad) {
-                        // The Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms) and
-                        // 1 - exp(-x) <= x, so U0 above x at |v| + that bound already means no
-                        // collision; below it, the partner is drawn and the exact test decides.
-                        const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
-                        R nn[3];
-                        normals3<R>(r2, nn);
-                        const R vnx = a.vt_gas * nn[0], vny = a.vt_gas * nn[1], vnz = a.vt_gas * nn[2];
-                        const R gx = vx - vnx, gy = vy - vny, gz = vz - vnz;
-                        const R gm = m_sqrt(gx * gx + gy * gy + gz * gz);
-                        const R P = -m_expm1(-a.ng_dt * a.sig_el * gm);
-                        if (U0 < P) {
-                            R d[3];
-                            iso_dir<R>(U2, U3, d);
-                            const R cx = a.red_m * vx + a.red_mn * vnx, cy = a.red_m * vy + a.red_mn * vny,
-                                    cz = a.red_m * vz + a.red_mn * vnz;
-                            vx = cx + a.red_a * gm * d[0];
-                            vy = cy + a.red_a * gm * d[1];
-                            vz = cz + a.red_a * gm * d[2];
-                        }
+                        coll = U0 < xc * a.p_pad && U0 < -m_expm1(-xc);
+                        spawns = coll && u24<R>(r0.y) * st < siz;
+                    } else {
+                        // the Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms)
+                        // and 1 - exp(-x) <= x: a candidate below this bound gets the exact test
+                        coll = U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad;
                     }
                 }
             }
             const uint32_t stay_mask = __ballot_sync(0xFFFFFFFFu, live && alive && stays);
-            const uint32_t spawn_mask = __ballot_sync(0xFFFFFFFFu, live && spawns);
-            if (live && alive) {
-                if (stays) {
-                    const int32_t dst = p0 + stay_run + __popc(stay_mask & lanemask_lt());
-                    kahan_add(ws_sum, ws_c, w);
-                    a.d.u[dst] = u; a.d.v[dst] = v;
-                    a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz;
-                    if (dst != p) { a.d.w[dst] = w; a.d.id[dst] = id; }
-                } else {
-                    list_put(a.self, nl, u, v, vx, vy, vz, w, id, key0 + (uint32_t)p, 0u, a.err);
-                }
+            const uint32_t spawn_mask = __ballot_sync(0xFFFFFFFFu, spawns);
+            const bool defer = live && alive && (!stays || coll);
+            const uint32_t defer_mask = __ballot_sync(0xFFFFFFFFu, defer);
+            int32_t dst = -1;
+            if (live && alive && stays) {
+                dst = p0 + stay_run + __popc(stay_mask & lanemask_lt());
+                kahan_add(ws_sum, ws_c, w);
+                a.d.u[dst] = u; a.d.v[dst] = v;
+                if (!coll) { a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz; }
+                if (dst != p) { a.d.w[dst] = w; a.d.id[dst] = id; }
             }
-            if (spawns) {
-                // the pair's ids follow from the parent's spawn rank once all leaves are counted:
-                // the rank within this leaf travels in the id word, the leaf in the aux word
-                const uint32_t rank = (uint32_t)(spawn_run + __popc(spawn_mask & lanemask_lt()));
-                list_put(a.self, nl, u, v, sv[0], sv[1], sv[2], w, rank, span + key0 + (uint32_t)p, (uint32_t)L,
-                         a.err);
-                if (a.ion.fill)
-                    list_put(a.ion, nl, u, v, si[0], si[1], si[2], w, rank, ion_span + key0 + (uint32_t)p,
-                             (uint32_t)L, a.err);
+            if (defer_mask) {
+                if (defer) {
+                    const int e = (qhead + qn + __popc(defer_mask & lanemask_lt())) & (kQueue - 1);
+                    q.a[e] = stays ? u : X; q.b[e] = stays ? v : Y;
+                    q.vx[e] = vx; q.vy[e] = vy; q.vz[e] = vz; q.w[e] = w;
+                    q.U0[e] = U0; q.U2[e] = U2; q.U3[e] = U3;
+                    q.id[e] = id; q.key[e] = key0 + (uint32_t)p;
+                    q.info[e] = (coll ? 1u : 0u) | (spawns ? 2u : 0u) |
+                                ((uint32_t)(spawn_run + __popc(spawn_mask & lanemask_lt())) << 2);
+                    q.L[e] = L; q.dst[e] = dst; q.I[e] = I; q.J[e] = J;
+                }
+                qn += __popc(defer_mask);
+                if (qn >= 32) {
+                    __syncwarp();
+                    run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span);
+                    __syncwarp();
+                    qhead = (qhead + 32) & (kQueue - 1);
+                    qn -= 32;
+                }
             }
             stay_run += __popc(stay_mask);
             spawn_run += __popc(spawn_mask);
@@ -426,6 +499,8 @@ __global__ void __launch_bounds__(kT, 4) k_push(PushArgs<R> a) {
             a.stay_hi[L] = hi; a.stay_lo[L] = lo;
         }
     }
+    __syncwarp();
+    if (lane < qn) run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span);
 }
 
 __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__restrict__ spawn_total) {
@@ -450,6 +525,7 @@ struct SortArgs {
     double *wsum;                       // with stay sums: the leaf's weight for the next deposit
     const void *stay_hi, *stay_lo;
     int32_t *big;                       // long regions for k_sort_big, count at big[nleaf]
+    int32_t *med;                       // medium regions for k_sort_medium, count at med[nleaf]
     int32_t *err;
 };
 
@@ -611,38 +687,101 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
     }
 }
 
-// One warp per leaf: sorts the entering regions up to kSortSmem long (longer ones are
-// queued for k_sort_big), sets end[L] and, with stay sums, the leaf's deposit weight.
+constexpr int kSortLane = 8;  // entering regions up to this long are sorted by one lane
+
+// One lane sorts a short entering region [b0, b0 + k), k <= kSortLane: ranks of the keys
+// (unrolled, in registers), then every record to q0 + its rank (through the scratch buffer
+// when source and destination overlap).
+template <typename R>
+__device__ __forceinline__ void sort_short(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0,
+                                           SoA<R> d, SoA<R> t) {
+    uint32_t key[kSortLane];
+#pragma unroll
+    for (int i = 0; i < kSortLane; ++i) key[i] = i < k ? a.key[b0 + i] : 0xFFFFFFFFu;
+    int rank[kSortLane];
+#pragma unroll
+    for (int i = 0; i < kSortLane; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < kSortLane; ++j) r += (key[j] < key[i]) ? 1 : 0;
+        rank[i] = r;
+    }
+    const bool overlap = q0 + k > b0;
+    if (overlap) {
+#pragma unroll
+        for (int i = 0; i < kSortLane; ++i)
+            if (i < k) {
+                const int32_t p = b0 + i;
+                t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p]; t.vz[p] = d.vz[p];
+                t.w[p] = d.w[p]; t.id[p] = d.id[p];
+            }
+    }
+    const SoA<R> src = overlap ? t : d;
+#pragma unroll
+    for (int i = 0; i < kSortLane; ++i)
+        if (i < k) {
+            const int32_t p = b0 + i, q = q0 + rank[i];
+            const R u = src.u[p], v = src.v[p], vx = src.vx[p], vy = src.vy[p], vz = src.vz[p], w = src.w[p];
+            const uint32_t id = spawn_id(a, span, key[i], key[i] >= span ? a.aux[p] : 0u, src.id[p]);
+            d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
+        }
+}
+
+// The leaf's weight for the next deposit: staying sum + entering particles in order (a few
+// entering particles: one lane, in order; many: lanes, then an exact combine).
+template <typename R> __device__ __forceinline__ double leaf_weight_seq(const SortArgs &a, int64_t L, SoA<R> d,
+                                                                        int32_t q0, int32_t k) {
+    const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
+    R sum = 0, c = 0;
+    for (int32_t q = q0; q < q0 + k; ++q) kahan_add(sum, c, d.w[q]);
+    return st + ((double)sum - (double)c);
+}
+
+// Entering regions of every leaf, 32 leaves per warp pass: short regions are sorted by the
+// leaf's own lane; medium ones (up to kSortSmem) are queued for k_sort_medium, long ones for
+// k_sort_big.  Sets end[L] and, with stay sums, the leaf's deposit weight.
 template <typename R>
 __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<R> t) {
+    const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
+    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < a.nleaf;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b0, k, q0;
+        entering_region(a, L, b0, k, q0);
+        if (k < 0) continue;
+        if (k <= kSortLane) {
+            if (k > 0) sort_short<R>(a, span, b0, k, q0, d, t);
+            if (a.wsum) a.wsum[L] = leaf_weight_seq<R>(a, L, d, q0, k);
+            a.end[L] = q0 + k;
+        } else if (k <= kSortSmem) {
+            a.med[atomicAdd(a.med + a.nleaf, 1)] = (int32_t)L;
+        } else {
+            a.big[atomicAdd(a.big + a.nleaf, 1)] = (int32_t)L;
+        }
+    }
+}
+
+// Medium entering regions (kSortLane < k <= kSortSmem): one warp per listed leaf.
+template <typename R>
+__global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R> t) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t L = warp; L < a.nleaf; L += nw) {
+    const int32_t nmed = a.med[a.nleaf];
+    for (int64_t i = warp; i < nmed; i += nw) {
+        const int64_t L = a.med[i];
         int32_t b0, k, q0;
         if (lane == 0) entering_region(a, L, b0, k, q0);
         b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
-        if (k < 0) continue;
-        if (k > kSortSmem) {  // long region: k_sort_big sorts it and sums its weights
-            if (lane == 0) a.big[atomicAdd(a.big + a.nleaf, 1)] = (int32_t)L;
-            continue;
-        }
-        if (k > 0) sort_region<R>(a, span, b0, k, q0, lane, d, t, sm_keys[threadIdx.x >> 5]);
+        sort_region<R>(a, span, b0, k, q0, lane, d, t, sm_keys[threadIdx.x >> 5]);
         if (a.wsum) {
-            // the leaf's weight for the next deposit: staying sum + entering particles in order
-            // (a few entering particles: one lane, in order; many: lanes, then an exact combine)
-            const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
             if (k <= 16) {
-                if (lane == 0) {
-                    R sum = 0, c = 0;
-                    for (int32_t q = q0; q < q0 + k; ++q) kahan_add(sum, c, d.w[q]);
-                    a.wsum[L] = st + ((double)sum - (double)c);
-                }
+                if (lane == 0) a.wsum[L] = leaf_weight_seq<R>(a, L, d, q0, k);
             } else {
+                const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
                 R sum = 0, c = 0;
                 for (int32_t q = q0 + lane; q < q0 + k; q += 32) kahan_add(sum, c, d.w[q]);
                 R hi = sum, lo = -c;
@@ -727,11 +866,13 @@ __global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, const i
 // weight sums when a.wsum is given), then the long regions (one block each).
 template <typename R> void sort_lists(pic_ctx *ctx, SortArgs a, SoA<R> d, SoA<R> t) {
     GB_CUDA(cudaMemsetAsync(a.big + a.nleaf, 0, 4, ctx->stream));
-    k_sort_entering<R><<<warp_blocks(a.nleaf), kT, 0, ctx->stream>>>(a, d, t);
+    GB_CUDA(cudaMemsetAsync(a.med + a.nleaf, 0, 4, ctx->stream));
+    k_sort_entering<R><<<blocks_for(a.nleaf), kT, 0, ctx->stream>>>(a, d, t);
+    k_sort_medium<R><<<std::min<unsigned>(warp_blocks(a.nleaf), 152u * 8u), kT, 0, ctx->stream>>>(a, d, t);
     const size_t smem = (size_t)kSortBig * sizeof(unsigned long long);
     GB_CUDA(cudaFuncSetAttribute(k_sort_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sort_big<R><<<152, 512, smem, ctx->stream>>>(a, d, t);
-    count_launch(ctx, 2);
+    count_launch(ctx, 3);
 }
 
 template <typename R> SortArgs sort_args(Instance &in, Species &sp) {
@@ -746,6 +887,7 @@ template <typename R> SortArgs sort_args(Instance &in, Species &sp) {
     a.wsum = nullptr;
     a.stay_hi = sp.stay_hi; a.stay_lo = sp.stay_lo;
     a.big = sp.big;
+    a.med = sp.moved;  // the moved-leaf list is free once the overflow repairs ran
     a.err = in.d_err;
     return a;
 }
@@ -791,6 +933,7 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     a.stay_hi = (R *)sp.stay_hi;
     a.stay_lo = (R *)sp.stay_lo;
     a.err = in.d_err;
+    a.self_wrap = (a.px && in.nx0 == 1) || (a.py && in.ny0 == 1);
     a.mcc = c.mcc ? 1 : 0;
     a.species = s;
     a.ng_dt = (R)(c.gas_density * c.dt);
@@ -833,8 +976,18 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     const int nsp = in.cfg.n_species;
     const int64_t nl = in.nleaf;
     const unsigned wb = warp_blocks(nl);
-    // the push kernel runs persistent warps: 4 resident blocks per SM (64 registers)
-    const unsigned pb = std::min<unsigned>(wb, 152u * 4u);
+    // the push kernel runs persistent warps: as many blocks as are resident at once
+    const size_t push_smem = (size_t)(kT / 32) * sizeof(Queue<R>);
+    static int resident = 0, sms = 0;  // per process: one device model, one kernel per R
+    if (!resident) {
+        GB_CUDA(cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_smem));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_push<R>, kT, push_smem));
+        int dev = 0;
+        GB_CUDA(cudaGetDevice(&dev));
+        GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (resident < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
+    }
+    const unsigned pb = std::min<unsigned>(wb, (unsigned)(resident * sms));
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
@@ -855,7 +1008,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                     a.ion_total = ion->rank0 + nl;
                 }
             }
-            k_push<R><<<pb, kT, 0, st>>>(a);
+            k_push<R><<<pb, kT, push_smem, st>>>(a);
             count_launch(ctx);
         }
     }

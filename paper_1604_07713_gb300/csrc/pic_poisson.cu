@@ -59,12 +59,33 @@ __global__ void k_residual64(int64_t n, const int32_t *__restrict__ col, const d
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
 }
 
+// out = sums of the block partials (one warp: lanes in a fixed order, then a fixed tree,
+// so the result does not depend on timing).
 __global__ void k_finish_sums(int nparts, const double *__restrict__ part, double *__restrict__ out) {
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < nparts; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }
-        out[0] = a; out[1] = b;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < nparts; k += 32) { a += part[2 * k]; b += part[2 * k + 1]; }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
     }
+    if (lane == 0) { out[0] = a; out[1] = b; }
+}
+
+// After a residual norm: the solve's statistics and whether another cycle runs (the
+// condition of the graph's WHILE node).  first = 1 before the first cycle.
+__global__ void k_mg_decide(cudaGraphConditionalHandle h, const double *__restrict__ sums, double tol, int maxc,
+                            double *__restrict__ stats, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double rr = sums[0], bb = sums[1];
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    const double cyc = first ? 0.0 : stats[0] + 1.0;
+    const bool done = rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= (double)maxc;
+    stats[0] = cyc;
+    stats[1] = rel;
+    if (done) stats[2] = fmax(stats[2], rel);
+    cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
 // Zero-mean projections for a fully periodic (singular) problem: area weights a = s^2.
@@ -866,17 +887,15 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
         k_project<<<blocks_for(n), kT, 0, s>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.bvec, 0);
         count_launch(ctx, 3);
     }
-    double rel = 0.0;
-    int cyc = 0;
     const int maxc = std::max(1, in.cfg.mg_max_cycles);
-    // launches go to ctx->stream, which is the capture stream while the cycle is captured
-    auto issue_residual = [&]() {
+    // launches go to ctx->stream, which is the capture stream while the solve is captured
+    auto issue_residual = [&](int first, cudaGraphConditionalHandle h) {
         k_residual64<<<kRedBlocks, kT, 0, ctx->stream>>>(n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b, in.red);
         k_finish_sums<<<1, 32, 0, ctx->stream>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
-        count_launch(ctx, 2);
-        GB_CUDA(cudaMemcpyAsync(in.red_host, in.red + 2 * kRedBlocks, 16, cudaMemcpyDeviceToHost, ctx->stream));
+        k_mg_decide<<<1, 32, 0, ctx->stream>>>(h, in.red + 2 * kRedBlocks, in.cfg.mg_rel_tol, maxc, in.mg_stats, first);
+        count_launch(ctx, 3);
     };
-    auto issue_cycle = [&]() {
+    auto issue_cycle = [&](cudaGraphConditionalHandle h) {
         vcycle(ctx, in, 0, singular);
         k_add_correction<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.x, in.phi);
         count_launch(ctx);
@@ -886,44 +905,67 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
             k_project<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
             count_launch(ctx, 3);
         }
-        issue_residual();
+        issue_residual(0, h);
     };
     if (!in.mg_cycle) {
-        // capture one cycle on a private stream (the context's stream may be the legacy
-        // default stream, which cannot be captured); replay it on the context's stream
+        // The whole solve as one graph: the residual of the warm start, then a WHILE node
+        // whose body is one cycle (V-cycle, correction, FP64 residual); the residual's last
+        // kernel decides on the device whether the body runs again, so the host never waits.
+        // Captured on a private stream (the context's stream may be the legacy default
+        // stream, which cannot be captured) and replayed on the context's stream.
         cudaStream_t cs;
         GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaStream_t saved = ctx->stream;
         const int64_t l0 = ctx->launches;
         ctx->stream = cs;
         cudaGraph_t graph = nullptr;
-        cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e1 == cudaSuccess) {
-            issue_cycle();
-            e1 = cudaStreamEndCapture(cs, &graph);
+        cudaGraphConditionalHandle h = 0;
+        cudaError_t e = cudaGraphCreate(&graph, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                                                cudaStreamCaptureModeThreadLocal);
+        cudaGraphNodeParams np = {};
+        if (e == cudaSuccess) {
+            issue_residual(1, h);
+            cudaStreamCaptureStatus status;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &nd);
+            cudaGraphNode_t wn = nullptr;
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&wn, graph, deps, nullptr, nd, &np);
+            if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1,
+                                                                          cudaStreamSetCaptureDependencies);
+            cudaGraph_t g2 = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &g2);
+            if (e == cudaSuccess) e = e2;
+        }
+        in.mg_pre_nodes = ctx->launches - l0;
+        if (e == cudaSuccess) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                issue_cycle(h);
+                cudaGraph_t b2 = nullptr;
+                e = cudaStreamEndCapture(cs, &b2);
+            }
         }
         ctx->stream = saved;
-        in.mg_cycle_nodes = ctx->launches - l0;
+        in.mg_cycle_nodes = ctx->launches - l0 - in.mg_pre_nodes;
         ctx->launches = l0;
         cudaStreamDestroy(cs);
-        GB_CUDA(e1);
-        GB_CUDA(cudaGraphInstantiate(&in.mg_cycle, graph, 0));
-        cudaGraphDestroy(graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&in.mg_cycle, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        GB_CUDA(e);
     }
-    issue_residual();
-    for (;;) {
-        GB_CUDA(cudaStreamSynchronize(s));
-        const double rr = in.red_host[0], bb = in.red_host[1];
-        rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
-        if (rel <= in.cfg.mg_rel_tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
-        GB_CUDA(cudaGraphLaunch(in.mg_cycle, s));
-        count_launch(ctx, in.mg_cycle_nodes);
-        ++cyc;
-    }
+    GB_CUDA(cudaGraphLaunch(in.mg_cycle, s));
+    count_launch(ctx, in.mg_pre_nodes);  // the cycles' launches are counted when the stats are read
+    in.mg_on_device = true;
+    in.mg_count_cycles = true;
     check_launch("poisson_solve");
-    in.mg_cycles = cyc;
-    in.mg_res = rel;
-    in.mg_res_max = std::max(in.mg_res_max, rel);
 }
 
 }  // namespace gbpic
