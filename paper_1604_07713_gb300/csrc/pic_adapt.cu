@@ -257,6 +257,118 @@ __global__ void k_adapt_move(int64_t n, const int32_t *__restrict__ start, const
     }
 }
 
+// Slots a coarsened quartet's list takes at the tail (its first sibling only; 0 elsewhere).
+__global__ void k_adapt_tail_need(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                                  const int32_t *__restrict__ kind, const int32_t *__restrict__ group,
+                                  int32_t *__restrict__ need) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    int32_t v = 0;
+    if (kind[l] == 2 && group[l] == (int32_t)l) {
+        int32_t c = 0;
+        for (int i = 0; i < 4; ++i) c += end[l + i] - start[l + i];
+        v = c + list_slack(c);
+    }
+    need[l] = v;
+}
+
+// The lists of the new leaves, in place (one warp per old leaf):
+// - an unchanged leaf keeps its segment;
+// - a refined leaf's records are partitioned by quadrant inside its own segment (through the
+//   scratch buffer), in list order, offsets re-expressed; its free slots are shared out;
+// - a coarsened quartet's lists go, one after another in Morton order, to a segment at the
+//   tail (tail0 + the scanned slot need of the quartets before it), offsets re-expressed.
+template <typename R>
+__global__ void k_adapt_inplace(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                                const int32_t *__restrict__ lim, const int32_t *__restrict__ kind,
+                                const int32_t *__restrict__ group, const int32_t *__restrict__ new_of,
+                                const uint32_t *__restrict__ morton, const int32_t *__restrict__ ncnt,
+                                const int32_t *__restrict__ tail_off, int32_t tail0, SoA<R> d, SoA<R> t,
+                                int32_t *__restrict__ nstart, int32_t *__restrict__ nend,
+                                int32_t *__restrict__ nlim) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = warp; l < n; l += nw) {
+        const int k = kind[l];
+        const int32_t p0 = start[l], p1 = end[l];
+        if (k == 0) {
+            if (lane == 0) {
+                const int32_t o = new_of[l];
+                nstart[o] = p0; nend[o] = p1; nlim[o] = lim[l];
+            }
+        } else if (k == 1) {
+            for (int32_t p = p0 + lane; p < p1; p += 32) {
+                t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p]; t.vz[p] = d.vz[p];
+                t.w[p] = d.w[p]; t.id[p] = d.id[p];
+            }
+            __syncwarp();
+            const int32_t o = new_of[l];
+            int32_t off[4], cnt[4];
+            const int32_t extra = (lim[l] - p0 - (p1 - p0)) / 4;  // free slots shared out
+            int32_t acc = p0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                cnt[c] = ncnt[o + c];
+                off[c] = acc;
+                acc += cnt[c] + extra;
+            }
+            if (lane < 4) {
+                nstart[o + lane] = off[lane];
+                nend[o + lane] = off[lane] + cnt[lane];
+                nlim[o + lane] = lane == 3 ? lim[l] : off[lane] + cnt[lane] + extra;
+            }
+            int32_t run[4] = {0, 0, 0, 0};
+            for (int32_t c0 = p0; c0 < p1; c0 += 32) {
+                const int32_t p = c0 + lane;
+                const bool live = p < p1;
+                R u = 0, v = 0;
+                int ch = -1;
+                if (live) {
+                    u = t.u[p];
+                    v = t.v[p];
+                    ch = (u >= (R)0.5 ? 1 : 0) + (v >= (R)0.5 ? 2 : 0);
+                }
+                int32_t rank = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, ch == c);
+                    if (ch == c) rank = run[c] + __popc(m & lanemask_lt());
+                    run[c] += __popc(m);
+                }
+                if (live) {
+                    int32_t q = 0;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (ch == c) q = off[c] + rank;
+                    d.u[q] = (R)2 * u - (R)(ch & 1);
+                    d.v[q] = (R)2 * v - (R)(ch >> 1);
+                    d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p]; d.vz[q] = t.vz[p]; d.w[q] = t.w[p]; d.id[q] = t.id[p];
+                }
+            }
+        } else if (group[l] == (int32_t)l) {
+            const int32_t base = tail0 + tail_off[l];
+            int32_t q0 = base;
+            for (int i = 0; i < 4; ++i) {
+                const int64_t li = l + i;
+                const int32_t a0 = start[li], a1 = end[li];
+                const R cx = (R)(morton[li] & 1u), cy = (R)((morton[li] >> 1) & 1u);
+                for (int32_t p = a0 + lane; p < a1; p += 32) {
+                    const int32_t q = q0 + (p - a0);
+                    d.u[q] = (cx + d.u[p]) * (R)0.5;
+                    d.v[q] = (cy + d.v[p]) * (R)0.5;
+                    d.vx[q] = d.vx[p]; d.vy[q] = d.vy[p]; d.vz[q] = d.vz[p]; d.w[q] = d.w[p]; d.id[q] = d.id[p];
+                }
+                q0 += a1 - a0;
+            }
+            if (lane == 0) {
+                const int32_t o = new_of[l], c = q0 - base;
+                nstart[o] = base; nend[o] = q0; nlim[o] = base + c + list_slack(c);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Split / merge
 // ------------------------------------------------------------------------------------
@@ -273,16 +385,21 @@ __device__ __forceinline__ int split_rounds(int32_t c, int32_t ppc_min) {
     return r;
 }
 
-__global__ void k_sm_count(SMArgs a, int32_t *__restrict__ ncnt, int32_t *__restrict__ nids,
-                           int32_t *__restrict__ merge_flag) {
+// Per leaf: records after the step, new ids, merge / split flags, and the tail slots a
+// split leaf takes when its segment cannot hold its children.
+__global__ void k_sm_count(SMArgs a, const int32_t *__restrict__ lim, int32_t *__restrict__ ncnt,
+                           int32_t *__restrict__ nids, int32_t *__restrict__ merge_flag,
+                           int32_t *__restrict__ split_flag, int32_t *__restrict__ tail_need) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= a.n) return;
     const int32_t c = a.end[l] - a.start[l];
-    int32_t nc = c, ni = 0, mf = 0;
+    int32_t nc = c, ni = 0, mf = 0, sf = 0, tn = 0;
     if (c > 0 && c < a.ppc_min) {
         const int r = split_rounds(c, a.ppc_min);
         nc = c << (2 * r);
         ni = nc - c;
+        sf = 1;
+        if (nc > lim[l] - a.start[l]) tn = nc + list_slack(nc);
     } else if (c > a.ppc_max) {
         nc = a.ppc_target;
         mf = 1;
@@ -290,34 +407,37 @@ __global__ void k_sm_count(SMArgs a, int32_t *__restrict__ ncnt, int32_t *__rest
     ncnt[l] = nc;
     nids[l] = ni;
     merge_flag[l] = mf;
+    split_flag[l] = sf;
+    tail_need[l] = tn;
 }
 
-// Unchanged and split leaves (one warp per leaf; merge leaves are left to k_sm_merge).
+// Split leaves, in place (one warp per listed leaf): the parents are copied to the scratch
+// buffer, then each child k of parent j is written at slot j 4^r + k of the leaf's list,
+// in its own segment or, when that is too small, in a segment at the tail.
 template <typename R>
-__global__ void k_sm_write(SMArgs a, const int32_t *__restrict__ nstart, const int32_t *__restrict__ idbase,
-                           unsigned long long id0, SoA<R> s, SoA<R> d) {
+__global__ void k_sm_split(SMArgs a, const int32_t *__restrict__ slist, int32_t ns, int32_t *__restrict__ start,
+                           int32_t *__restrict__ end, int32_t *__restrict__ lim,
+                           const int32_t *__restrict__ tail_need, const int32_t *__restrict__ tail_off, int32_t tail0,
+                           const int32_t *__restrict__ idbase, unsigned long long id0, SoA<R> d, SoA<R> t) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t l = warp; l < a.n; l += nw) {
-        const int32_t p0 = a.start[l], p1 = a.end[l], c = p1 - p0;
-        if (c == 0 || c > a.ppc_max) continue;
-        const int32_t q0 = nstart[l];
-        if (c >= a.ppc_min) {
-            for (int32_t p = p0 + lane; p < p1; p += 32) {
-                const int32_t q = q0 + (p - p0);
-                d.u[q] = s.u[p]; d.v[q] = s.v[p]; d.vx[q] = s.vx[p]; d.vy[q] = s.vy[p]; d.vz[q] = s.vz[p];
-                d.w[q] = s.w[p]; d.id[q] = s.id[p];
-            }
-            continue;
+    for (int64_t i = warp; i < ns; i += nw) {
+        const int32_t l = slist[i];
+        const int32_t p0 = start[l], p1 = end[l], c = p1 - p0;
+        for (int32_t p = p0 + lane; p < p1; p += 32) {
+            t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p]; t.vz[p] = d.vz[p];
+            t.w[p] = d.w[p]; t.id[p] = d.id[p];
         }
+        __syncwarp();
         const int r = split_rounds(c, a.ppc_min);
         const int32_t kids = 1 << (2 * r);
+        const int32_t q0 = tail_need[l] > 0 ? tail0 + tail_off[l] : p0;
         // one child per lane-iteration: child k of parent j, k in depth-first (base-4) order
-        for (int32_t t = lane; t < c * kids; t += 32) {
-            const int32_t j = t / kids, k = t - j * kids;
+        for (int32_t tt = lane; tt < c * kids; tt += 32) {
+            const int32_t j = tt / kids, k = tt - j * kids;
             const int32_t p = p0 + j;
-            R u = s.u[p], v = s.v[p], w = s.w[p];
+            R u = t.u[p], v = t.v[p], w = t.w[p];
             for (int lvl = r - 1; lvl >= 0; --lvl) {
                 const int digit = (k >> (2 * lvl)) & 3;
                 R m = u < (R)1 - u ? u : (R)1 - u;
@@ -329,10 +449,16 @@ __global__ void k_sm_write(SMArgs a, const int32_t *__restrict__ nstart, const i
                 v = (digit & 2) ? v + dd : v - dd;
                 w = w * (R)0.25;
             }
-            const int32_t q = q0 + t;
-            d.u[q] = u; d.v[q] = v; d.vx[q] = s.vx[p]; d.vy[q] = s.vy[p]; d.vz[q] = s.vz[p]; d.w[q] = w;
-            d.id[q] = k == 0 ? s.id[p] : (uint32_t)(id0 + (unsigned long long)idbase[l] +
+            const int32_t q = q0 + tt;
+            d.u[q] = u; d.v[q] = v; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p]; d.vz[q] = t.vz[p]; d.w[q] = w;
+            d.id[q] = k == 0 ? t.id[p] : (uint32_t)(id0 + (unsigned long long)idbase[l] +
                                                     (unsigned long long)j * (kids - 1) + (k - 1));
+        }
+        __syncwarp();
+        if (lane == 0) {
+            start[l] = q0;
+            end[l] = q0 + c * kids;
+            if (tail_need[l] > 0) lim[l] = q0 + tail_need[l];
         }
     }
 }
@@ -360,9 +486,11 @@ __device__ __forceinline__ int bin_of(double e, double lo, double rng) {
 constexpr int kMergeMax = 12288;  // particles of one leaf sorted in shared memory
 
 // One block per merging leaf: sort by (energy bin, id), cut into ppc_target groups, merge.
+// The merged records are written to the scratch buffer at the leaf's slots, then copied back
+// in place, so no source record is overwritten before it is read.
 template <typename R>
 __global__ void __launch_bounds__(512) k_sm_merge(SMArgs a, const int32_t *__restrict__ mlist, int32_t nm,
-                                                  const int32_t *__restrict__ nstart, R half_m, SoA<R> s, SoA<R> d,
+                                                  int32_t *__restrict__ end, R half_m, SoA<R> s, SoA<R> d,
                                                   int32_t *__restrict__ err) {
     extern __shared__ unsigned long long keys[];  // (bin << 32 | id) , index in the low word after
     __shared__ R red_lo[16], red_hi[16];
@@ -422,7 +550,7 @@ __global__ void __launch_bounds__(512) k_sm_merge(SMArgs a, const int32_t *__res
         }
         // groups: the first (c mod T) of size q + 1, the rest q
         const int32_t T = a.ppc_target, q = c / T, rem = c - q * T;
-        const int32_t o0 = nstart[l];
+        const int32_t o0 = p0;
         for (int32_t g = threadIdx.x; g < T; g += blockDim.x) {
             const int32_t b0 = g < rem ? g * (q + 1) : rem * (q + 1) + (g - rem) * q;
             const int32_t sz = g < rem ? q + 1 : q;
@@ -444,6 +572,13 @@ __global__ void __launch_bounds__(512) k_sm_merge(SMArgs a, const int32_t *__res
             d.id[o] = idmin;
         }
         __syncthreads();
+        for (int32_t g = threadIdx.x; g < T; g += blockDim.x) {
+            const int32_t o = o0 + g;
+            s.u[o] = d.u[o]; s.v[o] = d.v[o]; s.vx[o] = d.vx[o]; s.vy[o] = d.vy[o]; s.vz[o] = d.vz[o];
+            s.w[o] = d.w[o]; s.id[o] = d.id[o];
+        }
+        if (threadIdx.x == 0) end[l] = o0 + T;
+        __syncthreads();
     }
 }
 
@@ -460,15 +595,30 @@ int32_t read_i32(pic_ctx *ctx, const int32_t *d) {
     return h;
 }
 
-// Re-allocate one species' per-leaf arrays for a new leaf count; the records stay.
+// Re-allocate one species' per-leaf arrays for a new leaf count; the records stay.  With
+// nlim, the segments are taken as given (anywhere in the buffer) and the tail starts at
+// `tail`; without, they are in leaf order (lim[L] = start[L + 1]).
 void species_relist(pic_ctx *ctx, Instance &in, int s, int64_t nl, const int32_t *new_start,
-                    const int32_t *new_end) {
+                    const int32_t *new_end, const int32_t *nlim = nullptr, int32_t tail = 0) {
     Species &sp = in.sp[s];
     species_leaf_arrays(ctx, in, s, nl);
     GB_CUDA(cudaMemcpyAsync(sp.start, new_start, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     GB_CUDA(cudaMemcpyAsync(sp.end, new_end, (nl + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-    lists_installed(ctx, sp, nl);
+    if (nlim) {
+        GB_CUDA(cudaMemcpyAsync(sp.lim, nlim, nl * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        GB_CUDA(cudaMemcpyAsync(sp.flags + 4, &tail, 4, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        lists_installed(ctx, sp, nl);
+    }
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+// Lists whose tail has used up more than a quarter of the buffer are laid out again first,
+// so that repairs and adaptation do not keep growing the buffers.
+void compact_if_crowded(pic_ctx *ctx, Instance &in, int s) {
+    Species &sp = in.sp[s];
+    const int32_t tail = read_i32(ctx, sp.flags + 4);
+    if ((int64_t)tail > sp.cap - sp.cap / 4) species_compact(ctx, in, s);
 }
 
 template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n_old, int64_t n_new,
@@ -477,22 +627,30 @@ template <typename R> void adapt_particles(pic_ctx *ctx, Instance &in, int64_t n
     cudaStream_t st = ctx->stream;
     for (int s = 0; s < in.cfg.n_species; ++s) {
         Species &sp = in.sp[s];
-        // the new lists take at most slots_for(records, new leaves) slots
-        ensure_slots(ctx, in, s, slots_for(sp.n_upper, n_new));
+        compact_if_crowded(ctx, in, s);
         int32_t *ncnt = dalloc<int32_t>(T, n_new + 1);
-        int32_t *nstart = dalloc<int32_t>(T, n_new + 1), *nend = dalloc<int32_t>(T, n_new + 1);
-        int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(n_new));
+        int32_t *need = dalloc<int32_t>(T, n_old + 1);
+        int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(std::max(n_old, n_new)));
         GB_CUDA(cudaMemsetAsync(ncnt, 0, (n_new + 1) * 4, st));
         k_adapt_count<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, kind, group, new_of,
                                                            soa<R>(sp, sp.cur), ncnt);
-        count_launch(ctx);
-        lists_from_counts(ctx, sp, n_new, ncnt, nstart, nend, scr);
-        k_adapt_move<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, kind, group, new_of, morton_old,
-                                                          nstart, soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
+        k_adapt_tail_need<<<blocks_for(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, kind, group, need);
+        count_launch(ctx, 2);
+        exclusive_scan_i32(ctx, need, need, n_old, scr);
+        // the coarsened quartets' lists go to the tail: make room for them first
+        int32_t h[2] = {0, 0};
+        GB_CUDA(cudaMemcpyAsync(&h[0], sp.flags + 4, 4, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(&h[1], need + n_old, 4, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        ensure_slots(ctx, in, s, (int64_t)h[0] + h[1]);
+        int32_t *nstart = dalloc<int32_t>(T, n_new + 1), *nend = dalloc<int32_t>(T, n_new + 1);
+        int32_t *nlim = dalloc<int32_t>(T, n_new + 1);
+        k_adapt_inplace<R><<<warp_blocks(n_old), kT, 0, st>>>(n_old, sp.start, sp.end, sp.lim, kind, group, new_of,
+                                                             morton_old, ncnt, need, h[0], soa<R>(sp, sp.cur),
+                                                             soa<R>(sp, sp.cur ^ 1), nstart, nend, nlim);
         count_launch(ctx);
         check_launch("adapt_particles");
-        species_relist(ctx, in, s, n_new, nstart, nend);
-        sp.cur ^= 1;
+        species_relist(ctx, in, s, n_new, nstart, nend, nlim, h[0] + h[1]);
     }
 }
 
@@ -507,47 +665,57 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
     GB_CUDA(cudaMemsetAsync(err, 0, 4, st));
     for (int s = 0; s < in.cfg.n_species; ++s) {
         Species &sp = in.sp[s];
+        compact_if_crowded(ctx, in, s);
         int32_t *ncnt = dalloc<int32_t>(T, nl + 1), *nids = dalloc<int32_t>(T, nl + 1);
-        int32_t *mflag = dalloc<int32_t>(T, nl + 1);
-        int32_t *nstart = dalloc<int32_t>(T, nl + 1), *nend = dalloc<int32_t>(T, nl + 1);
+        int32_t *mflag = dalloc<int32_t>(T, nl + 1), *sflag = dalloc<int32_t>(T, nl + 1);
+        int32_t *tneed = dalloc<int32_t>(T, nl + 1), *toff = dalloc<int32_t>(T, nl + 1);
         int32_t *idb = dalloc<int32_t>(T, nl + 1);
         int32_t *mpos = dalloc<int32_t>(T, nl + 1), *mlist = dalloc<int32_t>(T, nl + 1);
+        int32_t *spos = dalloc<int32_t>(T, nl + 1), *slist = dalloc<int32_t>(T, nl + 1);
         int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(nl));
         {
             SMArgs a{nl, sp.start, sp.end, in.cfg.ppc_min, in.cfg.ppc_max, in.cfg.ppc_target};
-            k_sm_count<<<blocks_for(nl), kT, 0, st>>>(a, ncnt, nids, mflag);
+            k_sm_count<<<blocks_for(nl), kT, 0, st>>>(a, sp.lim, ncnt, nids, mflag, sflag, tneed);
             count_launch(ctx);
         }
-        lists_from_counts(ctx, sp, nl, ncnt, nstart, nend, scr);
         exclusive_scan_i32(ctx, nids, idb, nl, scr);
         exclusive_scan_i32(ctx, mflag, mpos, nl, scr);
-        int32_t tot[3];
-        GB_CUDA(cudaMemcpyAsync(&tot[0], nstart + nl, 4, cudaMemcpyDeviceToHost, st));
+        exclusive_scan_i32(ctx, sflag, spos, nl, scr);
+        exclusive_scan_i32(ctx, tneed, toff, nl, scr);
+        int32_t tot[5];
+        GB_CUDA(cudaMemcpyAsync(&tot[0], toff + nl, 4, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaMemcpyAsync(&tot[1], idb + nl, 4, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaMemcpyAsync(&tot[2], mpos + nl, 4, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(&tot[3], spos + nl, 4, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(&tot[4], sp.flags + 4, 4, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaStreamSynchronize(st));
         if (in.cfg.particle_capacity > 0 && sp.n_upper + tot[1] > in.cfg.particle_capacity)
             fail(PIC_ECAPACITY, "split would exceed the particle capacity");
-        ensure_slots(ctx, in, s, tot[0]);  // may move the lists to larger buffers
+        // split leaves whose segment is too small go to the tail: make room first (may move
+        // the lists to larger buffers)
+        ensure_slots(ctx, in, s, (int64_t)tot[4] + tot[0]);
         SMArgs a{nl, sp.start, sp.end, in.cfg.ppc_min, in.cfg.ppc_max, in.cfg.ppc_target};
         k_compact_flags<<<blocks_for(nl), kT, 0, st>>>(nl, mflag, mpos, mlist);
-        k_sm_write<R><<<warp_blocks(nl), kT, 0, st>>>(a, nstart, idb, next_id, soa<R>(sp, sp.cur),
-                                                      soa<R>(sp, sp.cur ^ 1));
+        k_compact_flags<<<blocks_for(nl), kT, 0, st>>>(nl, sflag, spos, slist);
         count_launch(ctx, 2);
+        if (tot[3] > 0) {
+            k_sm_split<R><<<std::min<unsigned>(warp_blocks(tot[3]), 152u * 8u), kT, 0, st>>>(
+                a, slist, tot[3], sp.start, sp.end, sp.lim, tneed, toff, tot[4], idb, next_id, soa<R>(sp, sp.cur),
+                soa<R>(sp, sp.cur ^ 1));
+            count_launch(ctx);
+        }
         if (tot[2] > 0) {
             const size_t smem = 16384 * sizeof(unsigned long long);  // keys, padded to 2^14 >= kMergeMax
             GB_CUDA(cudaFuncSetAttribute(k_sm_merge<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_sm_merge<R><<<std::min<int32_t>(tot[2], 1024), 512, smem, st>>>(
-                a, mlist, tot[2], nstart, (R)(0.5 * in.cfg.m[s]), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1), err);
+                a, mlist, tot[2], sp.end, (R)(0.5 * in.cfg.m[s]), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1), err);
             count_launch(ctx);
         }
         check_launch("split_merge");
+        const int32_t tail = tot[4] + tot[0];  // the split leaves moved to the tail took up to here
+        GB_CUDA(cudaMemcpyAsync(sp.flags + 4, &tail, 4, cudaMemcpyHostToDevice, st));
         if (read_i32(ctx, err)) fail(PIC_EINVAL, "a leaf holds more particles than one merge block sorts (12288)");
         next_id += (unsigned long long)tot[1];
-        GB_CUDA(cudaMemcpyAsync(sp.start, nstart, (nl + 1) * 4, cudaMemcpyDeviceToDevice, st));
-        GB_CUDA(cudaMemcpyAsync(sp.end, nend, (nl + 1) * 4, cudaMemcpyDeviceToDevice, st));
-        lists_installed(ctx, sp, nl);
-        sp.cur ^= 1;
         sp.sums_valid = false;
     }
     GB_CUDA(cudaMemcpyAsync(in.d_next_id, &next_id, 8, cudaMemcpyHostToDevice, st));

@@ -318,6 +318,7 @@ void lists_installed(pic_ctx *ctx, Species &sp, int64_t nl);  // lim, tail after
 void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl);       // rank0 from start / end
 void count_totals(pic_ctx *ctx, Instance &in);  // flags[1] of every species, device side
 void place_overflow(pic_ctx *ctx, Instance &in, int s);  // tail moves, else re-layout
+void species_compact(pic_ctx *ctx, Instance &in, int s);  // leaf-order re-layout, tail freed
 // pic_adapt.cu
 void adapt_mesh(pic_ctx *ctx, Instance &in);
 void split_merge(pic_ctx *ctx, Instance &in);

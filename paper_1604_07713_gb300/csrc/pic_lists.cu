@@ -232,18 +232,13 @@ __global__ void k_relayout_back(int64_t nl, const int32_t *__restrict__ start_ne
     }
 }
 
-template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
+// Every list of species s laid out again in leaf order with fresh free slots (the kernels
+// return at once unless flags[5] is set).
+template <typename R> void relayout_lists(pic_ctx *ctx, Instance &in, int s) {
     Species &sp = in.sp[s];
     cudaStream_t st = ctx->stream;
     const int64_t nl = in.nleaf;
     const SoA<R> d = soa<R>(sp, sp.cur), t = soa<R>(sp, sp.cur ^ 1);
-    const SoA<R> o = soa_ovf<R>(sp);
-    // leaves out of free slots move to the tail
-    k_move_to_tail<R><<<152 * 4, kT, 0, st>>>(sp.moved, nl, sp.cap, sp.start, sp.end, sp.lim, sp.stay, sp.fill, d,
-                                              sp.key, sp.aux, sp.flags);
-    k_place_ovf<R><<<152 * 2, kT, 0, st>>>(sp.end, sp.cap, o, sp.ovf_key, sp.ovf_aux, sp.ovf_dest, sp.ovf_slot, d,
-                                           sp.key, sp.aux, sp.moved, nl, sp.flags);
-    // tail used up: every list again, in leaf order (gated on flags[5])
     int32_t *scr = sp.spawn_base + nl + 1 + scan_scratch_elems(nl);
     // gated launches get small grids: a launch that returns at once still schedules every block
     const unsigned gb = std::min<unsigned>(blocks_for(nl), 152u * 2u);
@@ -256,12 +251,45 @@ template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
     k_relayout_move<R><<<std::min<unsigned>(warp_blocks(nl), 152u * 8u), kT, 0, st>>>(
         nl, sp.start, sp.end, sp.lim, sp.stay, sp.fill, sp.start_new, sp.cap, d, sp.key, sp.aux, t, tkey, taux,
         sp.flags, in.d_err);
-    k_relayout_ovf<R><<<152 * 4, kT, 0, st>>>(sp.stay, sp.start_new, nl, sp.cap, o, sp.ovf_key, sp.ovf_aux,
-                                              sp.ovf_dest, sp.ovf_slot, t, tkey, taux, sp.flags);
+    k_relayout_ovf<R><<<152 * 4, kT, 0, st>>>(sp.stay, sp.start_new, nl, sp.cap, soa_ovf<R>(sp), sp.ovf_key,
+                                              sp.ovf_aux, sp.ovf_dest, sp.ovf_slot, t, tkey, taux, sp.flags);
     k_relayout_back<R><<<152 * 8, kT, 0, st>>>(nl, sp.start_new, sp.stay, sp.cap, t, tkey, taux, d, sp.key, sp.aux,
                                                sp.start, sp.end, sp.lim, sp.flags);
-    count_launch(ctx, 8);
-    check_launch("place_overflow");
+    count_launch(ctx, 6);
+    check_launch("relayout_lists");
+}
+
+template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
+    Species &sp = in.sp[s];
+    cudaStream_t st = ctx->stream;
+    const int64_t nl = in.nleaf;
+    const SoA<R> d = soa<R>(sp, sp.cur);
+    const SoA<R> o = soa_ovf<R>(sp);
+    // leaves out of free slots move to the tail
+    k_move_to_tail<R><<<152 * 4, kT, 0, st>>>(sp.moved, nl, sp.cap, sp.start, sp.end, sp.lim, sp.stay, sp.fill, d,
+                                              sp.key, sp.aux, sp.flags);
+    k_place_ovf<R><<<152 * 2, kT, 0, st>>>(sp.end, sp.cap, o, sp.ovf_key, sp.ovf_aux, sp.ovf_dest, sp.ovf_slot, d,
+                                           sp.key, sp.aux, sp.moved, nl, sp.flags);
+    count_launch(ctx, 2);
+    // tail used up: every list again, in leaf order (gated on flags[5])
+    relayout_lists<R>(ctx, in, s);
+}
+
+// Host-driven compaction: every record counts as staying, nothing enters.
+__global__ void k_compact_prep(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                               int32_t *__restrict__ stay, int32_t *__restrict__ fill, int32_t *__restrict__ flags) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < nl) {
+        stay[L] = end[L] - start[L];
+        fill[L] = 0;
+    }
+    if (L == 0) {
+        flags[0] = 0;
+        flags[5] = 1;
+    }
+}
+__global__ void k_compact_done(int32_t *__restrict__ flags) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) flags[5] = 0;
 }
 }  // namespace
 
@@ -374,6 +402,19 @@ void count_totals(pic_ctx *ctx, Instance &in) {
 void place_overflow(pic_ctx *ctx, Instance &in, int s) {
     if (in.cfg.precision == PIC_FP64) place_impl<double>(ctx, in, s);
     else place_impl<float>(ctx, in, s);
+}
+
+// Lay species s's lists out again in leaf order with fresh free slots (frees the tail).
+void species_compact(pic_ctx *ctx, Instance &in, int s) {
+    Species &sp = in.sp[s];
+    const int64_t nl = in.nleaf;
+    k_compact_prep<<<blocks_for(nl), kT, 0, ctx->stream>>>(nl, sp.start, sp.end, sp.stay, sp.fill, sp.flags);
+    count_launch(ctx);
+    if (in.cfg.precision == PIC_FP64) relayout_lists<double>(ctx, in, s);
+    else relayout_lists<float>(ctx, in, s);
+    k_compact_done<<<1, 32, 0, ctx->stream>>>(sp.flags);
+    count_launch(ctx);
+    sp.sums_valid = false;
 }
 
 }  // namespace gbpic

@@ -102,3 +102,21 @@ def test_adapt_split_merge_dyadic_exact_decisions(precision):
         _compare(sim, ctx, 1e-6 if precision == W.FP32 else 1e-13)
         c = ctx.fields(G.PIC_FIELD_COUNT_E)
         assert c[c > 0].min() >= 8 and c.max() <= 128
+
+
+def test_adapt_with_crowded_lists_lays_them_out_first_fp64():
+    # a hard capacity equal to the population leaves almost no tail: the adaptation first
+    # lays every list out again (a compaction), then refines / coarsens in place
+    cfg, mesh, parts = _dyadic_case(W.FP64)
+    cfg.update(ppc_min=1, ppc_max=1 << 20, particle_capacity=parts[0]["x"].size)
+    sim, ctx = _pair(cfg, mesh, parts)
+    with ctx:
+        sim.fields(); ctx.compute_fields()
+        st = sim.adapt()
+        ctx.adapt()
+        assert st["mesh"]["refined"] > 0 and st["mesh"]["coarsened"] > 0
+        _compare(sim, ctx, 1e-13)
+        assert G.pic_get_list_stats(ctx.ctx, 0, 0)[0] >= 1  # the compaction ran
+        sim.step(2)
+        ctx.step(2)
+        _compare(sim, ctx, 1e-11)
