@@ -193,9 +193,36 @@ Instance &get_inst(pic_ctx *ctx, int32_t inst) {
     return ctx->inst[inst];
 }
 
+void reset_solver_stats(pic_ctx *ctx, Instance &in) {
+    in.mg_res_max = 0.0;
+    if (in.mg_stats) GB_CUDA(cudaMemsetAsync(in.mg_stats + 2, 0, 8, ctx->stream));
+}
+
+// Worst relative residual of the solves since the last reset (synchronises the stream).
+double collect_solver_stats(pic_ctx *ctx, Instance &in) {
+    if (!in.mg_on_device || !in.mg_stats) return in.mg_res_max;
+    GB_CUDA(cudaMemcpyAsync(in.red_host + 4, in.mg_stats, 3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    in.mg_cycles = (int)in.red_host[4];
+    in.mg_res = in.red_host[5];
+    if (in.mg_count_cycles) {  // kernels of the device-side cycle loop of the last solve
+        ctx->launches += (int64_t)in.mg_cycles * in.mg_cycle_nodes;
+        in.mg_count_cycles = false;
+    }
+    return std::max(in.mg_res_max, in.red_host[6]);
+}
+
+void ensure_species(pic_ctx *ctx, Instance &in) {
+    // a species never loaded is an empty population
+    for (int s = 0; s < in.cfg.n_species; ++s)
+        if (!in.sp[s].start) species_alloc(ctx, in, s, 1 << 16);
+}
+
+}  // namespace
+
 // Field half of a step for every instance: deposits, then one batched launch for all
 // instances whose meshes fit one block (one block each), other instances one by one.
-void fields_all(pic_ctx *ctx, int64_t step) {
+void gbpic::fields_all(pic_ctx *ctx, int64_t step) {
     std::vector<std::array<double, 4>> walls(ctx->inst.size());
     for (size_t i = 0; i < ctx->inst.size(); ++i) walls_at(ctx->inst[i], step, walls[i].data());
     {
@@ -224,32 +251,6 @@ void fields_all(pic_ctx *ctx, int64_t step) {
     }
 }
 
-void reset_solver_stats(pic_ctx *ctx, Instance &in) {
-    in.mg_res_max = 0.0;
-    if (in.mg_stats) GB_CUDA(cudaMemsetAsync(in.mg_stats + 2, 0, 8, ctx->stream));
-}
-
-// Worst relative residual of the solves since the last reset (synchronises the stream).
-double collect_solver_stats(pic_ctx *ctx, Instance &in) {
-    if (!in.mg_on_device || !in.mg_stats) return in.mg_res_max;
-    GB_CUDA(cudaMemcpyAsync(in.red_host + 4, in.mg_stats, 3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    GB_CUDA(cudaStreamSynchronize(ctx->stream));
-    in.mg_cycles = (int)in.red_host[4];
-    in.mg_res = in.red_host[5];
-    if (in.mg_count_cycles) {  // kernels of the device-side cycle loop of the last solve
-        ctx->launches += (int64_t)in.mg_cycles * in.mg_cycle_nodes;
-        in.mg_count_cycles = false;
-    }
-    return std::max(in.mg_res_max, in.red_host[6]);
-}
-
-void ensure_species(pic_ctx *ctx, Instance &in) {
-    // a species never loaded is an empty population
-    for (int s = 0; s < in.cfg.n_species; ++s)
-        if (!in.sp[s].start) species_alloc(ctx, in, s, 1 << 16);
-}
-
-}  // namespace
 
 pic_status gbpic::guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg) {
     return guarded(ctx, [&]() -> pic_status { return fn(arg); });
@@ -283,6 +284,11 @@ pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out)
             GB_CUDA(cudaMalloc(&in.d_err, 4));
             GB_CUDA(cudaMemset(in.d_err, 0, 4));
         }
+        // device step counter and wall potentials (read by captured ensemble steps)
+        GB_CUDA(cudaMalloc(&ctx->d_step, 8));
+        GB_CUDA(cudaMemset(ctx->d_step, 0, 8));
+        GB_CUDA(cudaMalloc(&ctx->d_walls, 4 * 8 * (size_t)n_instances));
+        for (int i = 0; i < n_instances; ++i) ctx->inst[i].d_walls = ctx->d_walls + 4 * i;
         ctx->precision = cfg[0].precision;
         return PIC_OK;
     });
@@ -312,6 +318,14 @@ pic_status pic_destroy(pic_ctx *ctx) {
         cudaEventDestroy(r.b);
     }
     ctx->batch_mem.release_all();
+    graph_release(ctx);
+    for (auto st : ctx->fork) cudaStreamDestroy(st);
+    for (auto ev : ctx->fork_ev) cudaEventDestroy(ev);
+    if (ctx->d_step) cudaFree(ctx->d_step);
+    if (ctx->d_walls) cudaFree(ctx->d_walls);
+    if (ctx->report_dev) cudaFree(ctx->report_dev);
+    if (ctx->report_tab) cudaFree(ctx->report_tab);
+    if (ctx->report_host) cudaFreeHost(ctx->report_host);
     ctx->cache.trim();
     for (auto &e : ctx->cache.cls) cudaFree(e.first);  // blocks an arena still held
     delete ctx;
@@ -395,26 +409,23 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
         pic_status st = PIC_OK;
         for (int32_t k = 0; k < n_steps; ++k) {
             for (Instance &in : ctx->inst) ensure_capacity(ctx, in);
-            fields_all(ctx, ctx->step);
-            for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
+            if (graph_step_possible(ctx)) {
+                graph_step(ctx);  // an ensemble in steady state: the whole step as one graph replay
+            } else {
+                fields_all(ctx, ctx->step);
+                for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
+            }
             ++ctx->step;
         }
+        // exact record totals (the next steps' capacity bound), consistency flags and solver
+        // statistics of every instance, in one read-back
+        report_all(ctx);
         for (Instance &in : ctx->inst) {
-            // exact record totals (the next steps' capacity bound) and the consistency flag
-            count_totals(ctx, in);
-            for (int s = 0; s < in.cfg.n_species; ++s)
-                GB_CUDA(cudaMemcpyAsync(in.cnt_host + s, in.sp[s].flags + 1, 4, cudaMemcpyDeviceToHost,
-                                        ctx->stream));
-            GB_CUDA(cudaMemcpyAsync(in.cnt_host + 8, in.d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
-        }
-        GB_CUDA(cudaStreamSynchronize(ctx->stream));
-        for (Instance &in : ctx->inst) {
-            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
-            if (in.cnt_host[8] != 0) {
+            if (in.mg_worst > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+            if (in.report_err != 0) {
                 ctx->poisoned = true;
                 fail(PIC_ESTATE, "particle bookkeeping violated a slot bound (overflow store or re-layout)");
             }
-            for (int s = 0; s < in.cfg.n_species; ++s) in.sp[s].n = in.sp[s].n_upper = in.cnt_host[s];
         }
         if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
         return st;

@@ -172,6 +172,9 @@ struct Instance {
     int64_t next_id = 0;                     // host mirror (exact after a sync)
     unsigned long long *d_next_id = nullptr; // device counter of the next particle id
     int32_t *d_err = nullptr;                // device-side consistency flag (0 = fine)
+    double *d_walls = nullptr;               // the context's wall array for this instance (4)
+    int32_t report_err = 0;                  // consistency flag read by the last report
+    double mg_worst = 0;                     // worst relative residual of the solves since the reset
     int mg_cycles = 0;
     double mg_res = 0;
     double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
@@ -213,6 +216,19 @@ struct pic_ctx {
     size_t batch_smem = 0;
     gbpic::DeviceArena batch_mem;
     gbpic::BlockCache cache;  // device blocks released by this context, for reuse
+    // captured multi-instance step (pic_graph.cu)
+    bool capturing = false;          // launches are being captured: read step and walls on the device
+    int64_t *d_step = nullptr;       // device copy of the step number
+    double *d_walls = nullptr;       // per instance: the 4 wall potentials of the current step
+    int64_t lists_epoch = 0;         // bumped whenever list buffers or per-leaf arrays are re-allocated
+    cudaGraphExec_t step_graph = nullptr;
+    int64_t graph_mesh_epoch = -1, graph_lists_epoch = -1;
+    int64_t graph_nodes = 0;         // kernel launches of one replay
+    std::vector<cudaStream_t> fork;  // branches of the captured step
+    std::vector<cudaEvent_t> fork_ev;
+    void *report_dev = nullptr, *report_host = nullptr;  // end-of-call report, one entry per instance
+    void *report_tab = nullptr;      // device table the report kernel reads
+    int64_t report_epoch = -1;
 };
 
 namespace gbpic {
@@ -302,7 +318,8 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
                     const double *y, const double *vx, const double *vy, const double *vz,
                     const double *w, const uint64_t *id);
 void deposit(pic_ctx *ctx, Instance &in, const double walls[4]);
-void particle_step(pic_ctx *ctx, Instance &in, int64_t step);
+void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping = true);
+void particle_bookkeeping(Instance &in);  // host-side bounds after a step's launches
 void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, double *vx,
                     double *vy, double *vz, double *w, uint64_t *id, uint32_t *leaf);
 void ensure_capacity(pic_ctx *ctx, Instance &in);
@@ -318,6 +335,12 @@ void lists_installed(pic_ctx *ctx, Species &sp, int64_t nl);  // lim, tail after
 void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl);       // rank0 from start / end
 void count_totals(pic_ctx *ctx, Instance &in);  // flags[1] of every species, device side
 void place_overflow(pic_ctx *ctx, Instance &in, int s);  // tail moves, else re-layout
+// pic_graph.cu
+bool graph_step_possible(pic_ctx *ctx);
+void graph_step(pic_ctx *ctx);            // one step of every instance as one graph replay
+void graph_release(pic_ctx *ctx);
+void report_all(pic_ctx *ctx);            // exact totals, error flags, solver stats of every instance (syncs)
+void fields_all(pic_ctx *ctx, int64_t step);
 void species_compact(pic_ctx *ctx, Instance &in, int s);  // leaf-order re-layout, tail freed
 // pic_adapt.cu
 void adapt_mesh(pic_ctx *ctx, Instance &in);

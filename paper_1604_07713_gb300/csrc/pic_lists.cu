@@ -295,6 +295,7 @@ __global__ void k_compact_done(int32_t *__restrict__ flags) {
 
 // Per-leaf arrays of one species for nl leaves (segments empty).
 void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
+    ++ctx->lists_epoch;
     Species &sp = in.sp[s];
     DeviceArena &A = in.part_mem[s];
     void *olds[] = {sp.start, sp.end, sp.lim, sp.rank0, sp.start_new, sp.stay, sp.inc, sp.fill, sp.big,
@@ -328,6 +329,7 @@ void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
 
 // Buffers of one species with `cap` slots each, and its per-leaf arrays (no records).
 void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
+    ++ctx->lists_epoch;
     Species &sp = in.sp[s];
     DeviceArena &A = in.part_mem[s];
     A.release_all();

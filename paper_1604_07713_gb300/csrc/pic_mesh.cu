@@ -248,6 +248,7 @@ template <typename T> struct FieldView {
     T inv_hf;  // 1 / (lattice cell side)
     int bcx, bcy;
     double wall[4];
+    const double *wall_dev;  // non-null: the wall potentials are read from here (captured steps)
 
     __device__ __forceinline__ T inv_h(int32_t c) const { return inv_hf * ((T)1 / (T)L.side(c)); }
 
@@ -331,6 +332,8 @@ template <typename R>
 __global__ void k_node_e(int64_t n, FieldView<R> F, R *__restrict__ stencil) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * n) return;
+    if (F.wall_dev)
+        for (int k = 0; k < 4; ++k) F.wall[k] = F.wall_dev[k];
     const int32_t l = (int32_t)(t >> 2);
     const int c = (int)(t & 3);
     const int32_t s = F.L.side(l);
@@ -520,17 +523,23 @@ template <typename T> FieldView<T> field_view(const Instance &in, const double w
     F.inv_hf = (T)((double)(1 << in.lmax) / in.h0);
     F.bcx = in.cfg.bc_x; F.bcy = in.cfg.bc_y;
     for (int k = 0; k < 4; ++k) F.wall[k] = walls[k];
+    F.wall_dev = nullptr;
     return F;
 }
 
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {
     Level &g = in.lv[0];
-    if (in.cfg.precision == PIC_FP64)
-        k_node_e<double><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, field_view<double>(in, walls),
-                                                                     (double *)in.stencil);
-    else
-        k_node_e<float><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, field_view<float>(in, walls),
-                                                                    (float *)in.stencil);
+    // a captured step reads the wall potentials of its time from the device
+    const double *wd = ctx->capturing ? in.d_walls : nullptr;
+    if (in.cfg.precision == PIC_FP64) {
+        FieldView<double> F = field_view<double>(in, walls);
+        F.wall_dev = wd;
+        k_node_e<double><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, F, (double *)in.stencil);
+    } else {
+        FieldView<float> F = field_view<float>(in, walls);
+        F.wall_dev = wd;
+        k_node_e<float><<<blocks_for(4 * g.n), kT, 0, ctx->stream>>>(g.n, F, (float *)in.stencil);
+    }
     count_launch(ctx);
     check_launch("node_e");
 }

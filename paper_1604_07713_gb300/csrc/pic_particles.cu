@@ -96,6 +96,7 @@ struct DepositArgs {
     double hf, rho_bg, inv_eps0;
     const double *bcw;
     double wall[4];
+    const double *wall_dev;  // non-null: the wall potentials are read from here (captured steps)
     double *charge, *b;
 };
 
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
             const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
             a.charge[L] = total;
             double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
-            for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * a.wall[k];
+            for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * (a.wall_dev ? a.wall_dev[k] : a.wall[k]);
             a.b[L] = bl;
         }
     }
@@ -141,7 +142,7 @@ __global__ void k_deposit_sums(DepositArgs a, const double *__restrict__ ws0, co
     const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
     a.charge[L] = total;
     double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
-    for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * a.wall[k];
+    for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * (a.wall_dev ? a.wall_dev[k] : a.wall[k]);
     a.b[L] = bl;
 }
 
@@ -217,6 +218,7 @@ template <typename R> struct PushArgs {
     R g_partner_max, g_pad;  // ions: bound on the partner speed (8.2 v_t), rounding margin
     R p_pad;                 // rounding margin of the linear bound on the collision probability
     uint32_t k0, k1, inst_word, step;
+    const int64_t *step_dev;  // non-null: the step number is read from here (captured steps)
 };
 
 template <typename R> __device__ __forceinline__ void iso_dir(R uc, R up, R d[3]) {
@@ -254,7 +256,7 @@ template <typename R> struct Queue {
 
 // Deferred work of queue entry e (one lane).
 template <typename R> __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R> &q, int e,
-                                                                   uint32_t span, uint32_t ion_span) {
+                                                                   uint32_t span, uint32_t ion_span, uint32_t step) {
     R vx = q.vx[e], vy = q.vy[e], vz = q.vz[e];
     const R w = q.w[e];
     const uint32_t id = q.id[e], info = q.info[e];
@@ -269,14 +271,14 @@ template <typename R> __device__ __forceinline__ void run_deferred(const PushArg
             if (info & 2u) {
                 const R rest = eps - a.eps_th;
                 const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
-                const U4 r1 = philox4x32_10(id, a.inst_word, a.step, 1u, a.k0, a.k1);
+                const U4 r1 = philox4x32_10(id, a.inst_word, step, 1u, a.k0, a.k1);
                 R d1[3], d2[3], nn[3];
                 iso_dir<R>(u24<R>(r1.x), u24<R>(r1.y), d1);
                 iso_dir<R>(u24<R>(r1.z), u24<R>(r1.w), d2);
                 const R s1 = m_sqrt(a.two_qe_over_m * e1), s2 = m_sqrt(a.two_qe_over_m * e2);
                 vx = s1 * d1[0]; vy = s1 * d1[1]; vz = s1 * d1[2];
                 sv[0] = s2 * d2[0]; sv[1] = s2 * d2[1]; sv[2] = s2 * d2[2];
-                const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
+                const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.k0, a.k1);
                 normals3<R>(r2, nn);
                 si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
             } else {
@@ -289,7 +291,7 @@ template <typename R> __device__ __forceinline__ void run_deferred(const PushArg
             }
         } else {
             // the partner is drawn and the exact test decides (the test in the pass was a bound)
-            const U4 r2 = philox4x32_10(id, a.inst_word, a.step, 2u, a.k0, a.k1);
+            const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.k0, a.k1);
             R nn[3];
             normals3<R>(r2, nn);
             const R vnx = a.vt_gas * nn[0], vny = a.vt_gas * nn[1], vnz = a.vt_gas * nn[2];
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
     // species total plus its parent's rank, so it sorts after every entering record
     const uint32_t span = (uint32_t)a.rank0[a.nleaf];
     const uint32_t ion_span = a.ion_total ? (uint32_t)*a.ion_total : 0u;
+    const uint32_t step = a.step_dev ? (uint32_t)*a.step_dev : a.step;
     int qhead = 0, qn = 0;  // ring of deferred entries
     // persistent warps: the next leaf's list bounds are fetched while this leaf runs
     int32_t np0 = 0, np1 = 0;
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
                 }
                 if (alive && a.mcc) {
                     const R v2 = vx * vx + vy * vy + vz * vz;
-                    const U4 r0 = philox4x32_10(id, a.inst_word, a.step, 0u, a.k0, a.k1);
+                    const U4 r0 = philox4x32_10(id, a.inst_word, step, 0u, a.k0, a.k1);
                     U0 = u24<R>(r0.x);
                     U2 = u24<R>(r0.z); U3 = u24<R>(r0.w);
                     if (a.species == 0) {
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
                 qn += __popc(defer_mask);
                 if (qn >= 32) {
                     __syncwarp();
-                    run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span);
+                    run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span, step);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
         }
     }
     __syncwarp();
-    if (lane < qn) run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span);
+    if (lane < qn) run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span, step);
 }
 
 __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__restrict__ spawn_total) {
@@ -870,7 +873,11 @@ template <typename R> void sort_lists(pic_ctx *ctx, SortArgs a, SoA<R> d, SoA<R>
     k_sort_entering<R><<<blocks_for(a.nleaf), kT, 0, ctx->stream>>>(a, d, t);
     k_sort_medium<R><<<std::min<unsigned>(warp_blocks(a.nleaf), 152u * 8u), kT, 0, ctx->stream>>>(a, d, t);
     const size_t smem = (size_t)kSortBig * sizeof(unsigned long long);
-    GB_CUDA(cudaFuncSetAttribute(k_sort_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static bool attr = false;  // per R, set once (not while a step is being captured)
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(k_sort_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
     k_sort_big<R><<<152, 512, smem, ctx->stream>>>(a, d, t);
     count_launch(ctx, 3);
 }
@@ -955,6 +962,7 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     a.k1 = (uint32_t)(c.seed >> 32);
     a.inst_word = (uint32_t)c.instance << 24;
     a.step = (uint32_t)step;
+    a.step_dev = nullptr;
     return a;
 }
 
@@ -1001,6 +1009,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         }
         for (int s = 0; s < nsp; ++s) {
             PushArgs<R> a = push_args<R>(in, s, step);
+            if (ctx->capturing) a.step_dev = ctx->d_step;  // a captured step reads its number on the device
             if (s == 0 && ionize) {
                 a.spawn = e.spawn;
                 if (ion) {
@@ -1188,6 +1197,7 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
     a.inv_eps0 = 1.0 / in.cfg.eps0;
     a.bcw = in.lv[0].bcw;
     for (int k = 0; k < 4; ++k) a.wall[k] = walls[k];
+    a.wall_dev = ctx->capturing ? in.d_walls : nullptr;  // a captured step: the step's own walls
     a.charge = in.charge;
     a.b = in.bvec;
     bool sums = true;
@@ -1242,9 +1252,14 @@ void ensure_slots(pic_ctx *ctx, Instance &in, int s, int64_t slots) {
     grow_species(ctx, in, s, std::max<int64_t>(slots + slots / 2, 2 * sp.cap));
 }
 
-void particle_step(pic_ctx *ctx, Instance &in, int64_t step) {
+void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping) {
     if (in.cfg.precision == PIC_FP64) step_impl<double>(ctx, in, step);
     else step_impl<float>(ctx, in, step);
+    if (bookkeeping) particle_bookkeeping(in);
+}
+
+// Upper bounds of the populations after a step: every electron may have ionized once.
+void particle_bookkeeping(Instance &in) {
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     if (ionize) {
         const int64_t ne = in.sp[0].n_upper;

@@ -96,3 +96,29 @@ def test_invalid_input_is_refused():
         with pytest.raises(G.PicError) as e:
             ctx.set_mesh(0, 2, 1, 1.0, np.array(root), np.array(morton), np.array(level))
         assert e.value.status == G.PIC_EINVAL
+
+
+def test_ensemble_steps_replay_one_graph_and_match_uncaptured_steps():
+    # from the second step on, the steps of an ensemble in steady state are one graph replay;
+    # the result is the same, bit for bit, as stepping without the graph (one instance alone)
+    cases = [_ccp(32, 10, 4, 150.0, 1e21), _ccp(40, 12, 5, 250.0, 2e21)]
+    for i, (cfg, _, _) in enumerate(cases):
+        cfg["instance"] = i
+    with G.Context([c[0] for c in cases]) as ctx:
+        for i, (cfg, mesh, parts) in enumerate(cases):
+            ctx.set_mesh_dict(mesh, inst=i)
+            for s in sorted(parts):
+                ctx.load(s, **parts[s], inst=i)
+        ctx.step(1)
+        G.pic_set_timing(ctx.ctx, True)
+        for _ in range(3):
+            ctx.step(1)
+        ph = G.pic_get_timing(ctx.ctx)
+        G.pic_set_timing(ctx.ctx, False)
+        assert ph["graph"][1] > 0 and ph["move"][1] == 0  # replays, no uncaptured particle step
+        batched = [[ctx.particles(s, inst=i) for s in (0, 1)] for i in range(len(cases))]
+    for i, (cfg, mesh, parts) in enumerate(cases):
+        alone = _run_alone(cfg, mesh, parts, 4)
+        for s in (0, 1):
+            for k in ("id", "x", "vx", "w"):
+                assert np.array_equal(batched[i][s][k], alone[s][k]), (i, s, k)
