@@ -995,7 +995,10 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         if (resident < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
     }
-    const unsigned pb = std::min<unsigned>(wb, (unsigned)(resident * sms));
+    // a captured ensemble step runs instances on parallel branches: a push that takes a
+    // quarter of the GPU lets four instances' pushes run side by side
+    const unsigned full = (unsigned)(resident * sms);
+    const unsigned pb = std::min<unsigned>(wb, ctx->capturing ? std::max(1u, full / 4) : full);
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
