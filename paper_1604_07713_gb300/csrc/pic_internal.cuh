@@ -265,19 +265,32 @@ __host__ __device__ inline uint32_t compact2(uint32_t v) {
     return v;
 }
 
-// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, Weyl key schedule.
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, Weyl key schedule.  The ten
+// round keys of each word, (k + r W) mod 2^32, are computed once on the host (philox_keys), so
+// a kernel that takes them as a parameter applies each as an operand of the round's XOR.
 struct U4 { uint32_t x, y, z, w; };
+struct PhiloxKeys { uint32_t k0[10], k1[10]; };
+inline PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K{};
+    uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0;
+        K.k1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                            uint32_t k0, uint32_t k1) {
+                                            const PhiloxKeys &K) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         // both halves of each 32 x 32 -> 64-bit product from one wide multiply
         const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
         const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
         const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        const uint32_t n0 = hi1 ^ c1 ^ K.k0[r], n2 = hi0 ^ c3 ^ K.k1[r];
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
     }
     return U4{c0, c1, c2, c3};
 }

@@ -217,7 +217,8 @@ template <typename R> struct PushArgs {
     R red_a, red_m, red_mn;  // ions: M / (m + M), m / (m + M), M / (m + M)
     R g_partner_max, g_pad;  // ions: bound on the partner speed (8.2 v_t), rounding margin
     R p_pad;                 // rounding margin of the linear bound on the collision probability
-    uint32_t k0, k1, inst_word, step;
+    PhiloxKeys keys;  // round keys of the seed
+    uint32_t inst_word, step;
     const int64_t *step_dev;  // non-null: the step number is read from here (captured steps)
 };
 
@@ -241,66 +242,83 @@ template <typename R> __device__ __forceinline__ void normals3(const U4 &r, R n[
 
 // Work that only some particles of a warp have, deferred so that it runs 32 particles at a
 // time instead of with one or two lanes of a chunk: the location of a particle that left its
-// leaf and its list slot there, and every collision beyond the test (the scattering, the
-// ionization with its pair, the ion's partner draw and exact test).  A per-warp ring of
-// kQueue entries in shared memory holds them, in list order.
+// leaf and its list slot there, and every collision beyond the bound test of the pass (the
+// exact test, the scattering, the ionization with its pair, the ion's partner draw).  A
+// per-warp ring of kQueue entries in shared memory holds them, in list order.
 constexpr int kQueue = 64;
 
 template <typename R> struct Queue {
     R a[kQueue], b[kQueue];  // leaver: X, Y (old leaf's finest-lattice units); stayer: new u, v
     R vx[kQueue], vy[kQueue], vz[kQueue], w[kQueue];
-    R U0[kQueue], U2[kQueue], U3[kQueue];
-    uint32_t id[kQueue], key[kQueue], info[kQueue];  // info: bit 0 collides / candidate, 1 spawns, rank << 2
+    uint32_t r[4][kQueue];  // collision candidates: the four purpose-0 Philox words
+    uint32_t id[kQueue], key[kQueue], cand[kQueue];
     int32_t L[kQueue], dst[kQueue], I[kQueue], J[kQueue];  // dst: a stayer's slot, -1 for a leaver
 };
 
-// Deferred work of queue entry e (one lane).
-template <typename R> __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R> &q, int e,
-                                                                   uint32_t span, uint32_t ion_span, uint32_t step) {
-    R vx = q.vx[e], vy = q.vy[e], vz = q.vz[e];
-    const R w = q.w[e];
-    const uint32_t id = q.id[e], info = q.info[e];
-    const int32_t L = q.L[e], dst = q.dst[e];
+// Deferred work of queue entry e; all 32 lanes call it (`valid`: the lane has an entry).
+// Electrons that spawn are ranked among their leaf's spawning particles in list order: the
+// entries are in list order, and (run_leaf, run_count) carry the count of the last leaf of
+// the previous batch, whose entries may continue in this one.
+template <typename R>
+__device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R> &q, int e, bool valid, uint32_t span,
+                                             uint32_t ion_span, uint32_t step, int32_t &run_leaf, int32_t &run_count) {
+    R vx = 0, vy = 0, vz = 0, w = 0;
+    uint32_t id = 0, cand = 0;
+    int32_t L = -1, dst = -1;
+    if (valid) {
+        vx = q.vx[e]; vy = q.vy[e]; vz = q.vz[e]; w = q.w[e];
+        id = q.id[e]; cand = q.cand[e];
+        L = q.L[e]; dst = q.dst[e];
+    }
     R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
-    if (info & 1u) {
+    bool spawns = false;
+    if (cand) {
         const R v2 = vx * vx + vy * vy + vz * vz;
+        const R U0 = u24<R>(q.r[0][e]);
         if (a.species == 0) {
+            // the exact test, from the same quantities as the bound of the pass
             const R eps = a.half_m_over_qe * v2;
-            const R speed = m_sqrt(v2);
-            const R U2 = q.U2[e];
-            if (info & 2u) {
-                const R rest = eps - a.eps_th;
-                const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
-                const U4 r1 = philox4x32_10(id, a.inst_word, step, 1u, a.k0, a.k1);
-                R d1[3], d2[3], nn[3];
-                iso_dir<R>(u24<R>(r1.x), u24<R>(r1.y), d1);
-                iso_dir<R>(u24<R>(r1.z), u24<R>(r1.w), d2);
-                const R s1 = m_sqrt(a.two_qe_over_m * e1), s2 = m_sqrt(a.two_qe_over_m * e2);
-                vx = s1 * d1[0]; vy = s1 * d1[1]; vz = s1 * d1[2];
-                sv[0] = s2 * d2[0]; sv[1] = s2 * d2[1]; sv[2] = s2 * d2[2];
-                const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.k0, a.k1);
-                normals3<R>(r2, nn);
-                si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
-            } else {
-                R d[3];
-                iso_dir<R>(U2, q.U3[e], d);
-                const R cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
-                const R eps2 = eps * ((R)1 - a.two_m_over_mn * ((R)1 - cchi));
-                const R s2 = m_sqrt(a.two_qe_over_m * eps2);
-                vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
+            const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - m_div(a.eps_th, eps)) : (R)0;
+            const R st = a.sig_el + siz;
+            const R xc = a.ng_dt * st * m_sqrt(v2);
+            if (U0 < -m_expm1(-xc)) {
+                spawns = u24<R>(q.r[1][e]) * st < siz;
+                const R speed = m_sqrt(v2);
+                const R U2 = u24<R>(q.r[2][e]);
+                if (spawns) {
+                    const R rest = eps - a.eps_th;
+                    const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
+                    const U4 r1 = philox4x32_10(id, a.inst_word, step, 1u, a.keys);
+                    R d1[3], d2[3], nn[3];
+                    iso_dir<R>(u24<R>(r1.x), u24<R>(r1.y), d1);
+                    iso_dir<R>(u24<R>(r1.z), u24<R>(r1.w), d2);
+                    const R s1 = m_sqrt(a.two_qe_over_m * e1), s2 = m_sqrt(a.two_qe_over_m * e2);
+                    vx = s1 * d1[0]; vy = s1 * d1[1]; vz = s1 * d1[2];
+                    sv[0] = s2 * d2[0]; sv[1] = s2 * d2[1]; sv[2] = s2 * d2[2];
+                    const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.keys);
+                    normals3<R>(r2, nn);
+                    si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
+                } else {
+                    R d[3];
+                    iso_dir<R>(U2, u24<R>(q.r[3][e]), d);
+                    const R cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
+                    const R eps2 = eps * ((R)1 - a.two_m_over_mn * ((R)1 - cchi));
+                    const R s2 = m_sqrt(a.two_qe_over_m * eps2);
+                    vx = s2 * d[0]; vy = s2 * d[1]; vz = s2 * d[2];
+                }
             }
         } else {
             // the partner is drawn and the exact test decides (the test in the pass was a bound)
-            const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.k0, a.k1);
+            const U4 r2 = philox4x32_10(id, a.inst_word, step, 2u, a.keys);
             R nn[3];
             normals3<R>(r2, nn);
             const R vnx = a.vt_gas * nn[0], vny = a.vt_gas * nn[1], vnz = a.vt_gas * nn[2];
             const R gx = vx - vnx, gy = vy - vny, gz = vz - vnz;
             const R gm = m_sqrt(gx * gx + gy * gy + gz * gz);
             const R P = -m_expm1(-a.ng_dt * a.sig_el * gm);
-            if (q.U0[e] < P) {
+            if (U0 < P) {
                 R d[3];
-                iso_dir<R>(q.U2[e], q.U3[e], d);
+                iso_dir<R>(u24<R>(q.r[2][e]), u24<R>(q.r[3][e]), d);
                 const R cx = a.red_m * vx + a.red_mn * vnx, cy = a.red_m * vy + a.red_mn * vny,
                         cz = a.red_m * vz + a.red_mn * vnz;
                 vx = cx + a.red_a * gm * d[0];
@@ -309,6 +327,21 @@ template <typename R> __device__ __forceinline__ void run_deferred(const PushArg
             }
         }
     }
+    // spawn ranks and per-leaf spawn counts (valid lanes form a prefix of the warp)
+    uint32_t rank = 0;
+    const uint32_t smask = __ballot_sync(0xFFFFFFFFu, spawns);
+    const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+    const int32_t Llast = __shfl_sync(0xFFFFFFFFu, L, 31 - __clz(vmask));
+    const uint32_t same_last = __ballot_sync(0xFFFFFFFFu, valid && L == Llast);
+    if (smask) {
+        const uint32_t same = __match_any_sync(0xFFFFFFFFu, L);
+        const uint32_t before = smask & same & lanemask_lt();
+        rank = (L == run_leaf ? (uint32_t)run_count : 0u) + __popc(before);
+        if (spawns && before == 0) atomicAdd(a.spawn + L, __popc(smask & same));
+    }
+    run_count = (Llast == run_leaf ? run_count : 0) + __popc(smask & same_last);
+    run_leaf = Llast;
+    if (!valid) return;
     int32_t nl;
     R u, v;
     if (dst >= 0) {  // staying: the record is in place except its velocity
@@ -329,10 +362,9 @@ template <typename R> __device__ __forceinline__ void run_deferred(const PushArg
         u = un2; v = vn2;
         list_put(a.self, nl, u, v, vx, vy, vz, w, id, q.key[e], 0u, a.err);
     }
-    if (info & 2u) {
+    if (spawns) {
         // the pair's ids follow from the parent's spawn rank once all leaves are counted:
         // the rank within the parent's leaf travels in the id word, the leaf in the aux word
-        const uint32_t rank = info >> 2;
         list_put(a.self, nl, u, v, sv[0], sv[1], sv[2], w, rank, span + q.key[e], (uint32_t)L, a.err);
         if (a.ion.fill)
             list_put(a.ion, nl, u, v, si[0], si[1], si[2], w, rank, ion_span + q.key[e], (uint32_t)L, a.err);
@@ -357,19 +389,33 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
     const uint32_t ion_span = a.ion_total ? (uint32_t)*a.ion_total : 0u;
     const uint32_t step = a.step_dev ? (uint32_t)*a.step_dev : a.step;
     int qhead = 0, qn = 0;  // ring of deferred entries
-    // persistent warps: the next leaf's list bounds are fetched while this leaf runs
+    int32_t run_leaf = -1, run_count = 0;  // spawn count of the last leaf seen by the deferred work
+    // Persistent warps, software-pipelined: the next chunk's records are loaded while this
+    // chunk computes, and during a leaf's last chunk that is the first chunk of the warp's
+    // next leaf (whose list bounds are fetched when this leaf starts).  The next leaf's slots
+    // are disjoint from every slot this warp writes while it finishes this leaf.
+    R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nwt = 0;
+    uint32_t nid = 0;
+    auto fetch = [&](int32_t qq) {
+        nu = a.d.u[qq]; nv = a.d.v[qq]; nvx = a.d.vx[qq]; nvy = a.d.vy[qq]; nvz = a.d.vz[qq];
+        nid = a.d.id[qq]; nwt = a.d.w[qq];
+    };
     int32_t np0 = 0, np1 = 0;
-    if (warp < a.nleaf) { np0 = a.start[warp]; np1 = a.end[warp]; }
+    if (warp < a.nleaf) {
+        np0 = a.start[warp]; np1 = a.end[warp];
+        if (np0 + lane < np1) fetch(np0 + lane);
+    }
     for (int64_t Lw = warp; Lw < a.nleaf; Lw += nw) {
         const int32_t L = (int32_t)Lw;
         const int32_t p0 = np0, p1 = np1;
+        np0 = np1 = 0;
         if (Lw + nw < a.nleaf) { np0 = a.start[Lw + nw]; np1 = a.end[Lw + nw]; }
         if (p0 == p1) {
             if (lane == 0) {
                 a.stay[L] = 0;
-                if (a.spawn) a.spawn[L] = 0;
                 a.stay_hi[L] = (R)0; a.stay_lo[L] = (R)0;
             }
+            if (np0 + lane < np1) fetch(np0 + lane);
             continue;
         }
         R ws_sum = 0, ws_c = 0;  // staying particles' weights, in list order per lane
@@ -381,27 +427,17 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
         R E[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) E[k] = a.stencil[8 * (int64_t)L + k];
-        int32_t stay_run = 0, spawn_run = 0;
-        // software pipeline: the next chunk's record is loaded while this chunk computes
-        R nu = 0, nv = 0, nvx = 0, nvy = 0, nvz = 0, nwt = 0;
-        uint32_t nid = 0;
-        if (p0 + lane < p1) {
-            const int32_t qq = p0 + lane;
-            nu = a.d.u[qq]; nv = a.d.v[qq]; nvx = a.d.vx[qq]; nvy = a.d.vy[qq]; nvz = a.d.vz[qq];
-            nid = a.d.id[qq]; nwt = a.d.w[qq];
-        }
+        int32_t stay_run = 0;
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
             const bool live = p < p1;
-            bool alive = false, stays = false, spawns = false, coll = false;
+            bool alive = false, stays = false, cand = false;
             R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nwt;
             uint32_t id = nid;
-            if (p + 32 < p1) {
-                const int32_t qq = p + 32;
-                nu = a.d.u[qq]; nv = a.d.v[qq]; nvx = a.d.vx[qq]; nvy = a.d.vy[qq]; nvz = a.d.vz[qq];
-                nid = a.d.id[qq]; nwt = a.d.w[qq];
-            }
-            R X = 0, Y = 0, U0 = 0, U2 = 0, U3 = 0;
+            if (p + 32 < p1) fetch(p + 32);
+            else if (c0 + 32 >= p1 && np0 + lane < np1) fetch(np0 + lane);
+            R X = 0, Y = 0;
+            U4 r0{0u, 0u, 0u, 0u};
             int32_t I = 0, J = 0;
             if (live) {
                 // gather: bilinear in the leaf's corner field
@@ -440,35 +476,32 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
                 }
                 if (alive && a.mcc) {
                     const R v2 = vx * vx + vy * vy + vz * vz;
-                    const U4 r0 = philox4x32_10(id, a.inst_word, step, 0u, a.k0, a.k1);
-                    U0 = u24<R>(r0.x);
-                    U2 = u24<R>(r0.z); U3 = u24<R>(r0.w);
+                    r0 = philox4x32_10(id, a.inst_word, step, 0u, a.keys);
+                    const R U0 = u24<R>(r0.x);
                     if (a.species == 0) {
                         const R eps = a.half_m_over_qe * v2;
                         const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - m_div(a.eps_th, eps)) : (R)0;
                         const R st = a.sig_el + siz;
                         const R xc = a.ng_dt * st * m_sqrt(v2);
                         // 1 - exp(-x) <= x: a uniform at or above x (with a rounding margin)
-                        // already means no collision, without evaluating the exponential
-                        coll = U0 < xc * a.p_pad && U0 < -m_expm1(-xc);
-                        spawns = coll && u24<R>(r0.y) * st < siz;
+                        // means no collision; below it the deferred work makes the exact test
+                        cand = U0 < xc * a.p_pad;
                     } else {
                         // the Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms)
                         // and 1 - exp(-x) <= x: a candidate below this bound gets the exact test
-                        coll = U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad;
+                        cand = U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad;
                     }
                 }
             }
             const uint32_t stay_mask = __ballot_sync(0xFFFFFFFFu, live && alive && stays);
-            const uint32_t spawn_mask = __ballot_sync(0xFFFFFFFFu, spawns);
-            const bool defer = live && alive && (!stays || coll);
+            const bool defer = live && alive && (!stays || cand);
             const uint32_t defer_mask = __ballot_sync(0xFFFFFFFFu, defer);
             int32_t dst = -1;
             if (live && alive && stays) {
                 dst = p0 + stay_run + __popc(stay_mask & lanemask_lt());
                 kahan_add(ws_sum, ws_c, w);
                 a.d.u[dst] = u; a.d.v[dst] = v;
-                if (!coll) { a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz; }
+                if (!cand) { a.d.vx[dst] = vx; a.d.vy[dst] = vy; a.d.vz[dst] = vz; }
                 if (dst != p) { a.d.w[dst] = w; a.d.id[dst] = id; }
             }
             if (defer_mask) {
@@ -476,34 +509,34 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
                     const int e = (qhead + qn + __popc(defer_mask & lanemask_lt())) & (kQueue - 1);
                     q.a[e] = stays ? u : X; q.b[e] = stays ? v : Y;
                     q.vx[e] = vx; q.vy[e] = vy; q.vz[e] = vz; q.w[e] = w;
-                    q.U0[e] = U0; q.U2[e] = U2; q.U3[e] = U3;
+                    q.cand[e] = cand ? 1u : 0u;
+                    if (cand) {
+                        q.r[0][e] = r0.x; q.r[2][e] = r0.z; q.r[3][e] = r0.w;
+                        if (a.species == 0) q.r[1][e] = r0.y;
+                    }
                     q.id[e] = id; q.key[e] = key0 + (uint32_t)p;
-                    q.info[e] = (coll ? 1u : 0u) | (spawns ? 2u : 0u) |
-                                ((uint32_t)(spawn_run + __popc(spawn_mask & lanemask_lt())) << 2);
                     q.L[e] = L; q.dst[e] = dst; q.I[e] = I; q.J[e] = J;
                 }
                 qn += __popc(defer_mask);
                 if (qn >= 32) {
                     __syncwarp();
-                    run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span, step);
+                    run_deferred(a, q, (qhead + lane) & (kQueue - 1), true, span, ion_span, step, run_leaf, run_count);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
                 }
             }
             stay_run += __popc(stay_mask);
-            spawn_run += __popc(spawn_mask);
         }
         R hi = ws_sum, lo = -ws_c;
         warp_two_sum(hi, lo);
         if (lane == 0) {
             a.stay[L] = stay_run;
-            if (a.spawn) a.spawn[L] = spawn_run;
             a.stay_hi[L] = hi; a.stay_lo[L] = lo;
         }
     }
     __syncwarp();
-    if (lane < qn) run_deferred(a, q, (qhead + lane) & (kQueue - 1), span, ion_span, step);
+    if (qn > 0) run_deferred(a, q, (qhead + lane) & (kQueue - 1), lane < qn, span, ion_span, step, run_leaf, run_count);
 }
 
 __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__restrict__ spawn_total) {
@@ -958,8 +991,7 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     a.g_partner_max = (R)(8.2 * std::sqrt(c.gas_temperature_ev * c.qe / c.neutral_mass));
     a.g_pad = (R)1.001;
     a.p_pad = (R)1.0001;
-    a.k0 = (uint32_t)(c.seed & 0xFFFFFFFFu);
-    a.k1 = (uint32_t)(c.seed >> 32);
+    a.keys = philox_keys(c.seed);
     a.inst_word = (uint32_t)c.instance << 24;
     a.step = (uint32_t)step;
     a.step_dev = nullptr;
@@ -967,11 +999,14 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
 }
 
 // Per species before a push: no entering records yet, nothing in the overflow store, no
-// moved leaves, the tail not used up.
+// moved leaves, the tail not used up, and (electrons with ionization) no spawns counted.
 __global__ void k_step_reset(int64_t nl, int32_t *__restrict__ fill, int32_t *__restrict__ flags,
-                             int32_t *__restrict__ moved) {
+                             int32_t *__restrict__ moved, int32_t *__restrict__ spawn) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nl) fill[i] = 0;
+    if (i < nl) {
+        fill[i] = 0;
+        if (spawn) spawn[i] = 0;
+    }
     if (i == 0) {
         flags[0] = 0;
         flags[5] = 0;
@@ -1006,7 +1041,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         Phase ph(ctx, PIC_PHASE_MOVE);
         for (int s = 0; s < nsp; ++s) {
             Species &sp = in.sp[s];
-            k_step_reset<<<blocks_for(nl), kT, 0, st>>>(nl, sp.fill, sp.flags, sp.moved);
+            k_step_reset<<<blocks_for(nl), kT, 0, st>>>(nl, sp.fill, sp.flags, sp.moved,
+                                                        s == 0 && ionize ? sp.spawn : nullptr);
             count_launch(ctx);
             list_ranks(ctx, sp, nl);
         }
