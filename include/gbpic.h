@@ -78,7 +78,7 @@ enum {
 /* Phases timed by pic_get_timing (CUDA events on the context's stream). */
 enum {
     PIC_PHASE_DEPOSIT = 0, PIC_PHASE_POISSON = 1, PIC_PHASE_NODE_E = 2,
-    PIC_PHASE_COUNT = 3,        /* not timed any more: the push has no counting pass */
+    PIC_PHASE_LISTS = 3,        /* per step before the push: list ranks, fill and flag reset */
     PIC_PHASE_SCAN = 4, PIC_PHASE_MOVE = 5, PIC_PHASE_SORT = 6, PIC_PHASE_ADAPT = 7,
     PIC_PHASE_SPLIT_MERGE = 8,
     PIC_PHASE_GRAPH = 9,        /* whole steps of an ensemble replayed as one CUDA graph */

@@ -24,7 +24,7 @@ PIC_BC_PERIODIC, PIC_BC_DIRICHLET, PIC_BC_NEUMANN = 0, 1, 2
 PIC_ADAPT_MESH, PIC_ADAPT_PARTICLES = 1, 2
 PIC_FIELD_PHI, PIC_FIELD_RHO, PIC_FIELD_COUNT_E, PIC_FIELD_COUNT_I, PIC_FIELD_NODE_E, \
     PIC_FIELD_EMAG = range(6)
-PHASES = ["deposit", "poisson", "node_e", "count", "scan", "move", "sort", "adapt", "split_merge", "graph"]
+PHASES = ["deposit", "poisson", "node_e", "lists", "scan", "move", "sort", "adapt", "split_merge", "graph"]
 PIC_N_PHASES = len(PHASES)
 
 EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_load_particles",

@@ -180,6 +180,7 @@ struct Instance {
     double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
     bool mg_on_device = false;     // last solve ran its loop on the device (stats below)
     double *mg_stats = nullptr;    // device: [cycles, rel. residual, max rel. since reset]
+    float *coarse_inv = nullptr;         // coarsest multigrid level: dense inverse (small levels)
     void *small_item = nullptr;          // meshes that fit one block: the solve's work item
     size_t small_smem = 0;               // and its dynamic shared memory
     cudaGraphExec_t mg_cycle = nullptr;  // multi-block meshes: one captured cycle (V-cycle,

@@ -217,6 +217,9 @@ template <typename R> struct PushArgs {
     R red_a, red_m, red_mn;  // ions: M / (m + M), m / (m + M), M / (m + M)
     R g_partner_max, g_pad;  // ions: bound on the partner speed (8.2 v_t), rounding margin
     R p_pad;                 // rounding margin of the linear bound on the collision probability
+    // the bound test of the pass: electrons sigma_el / sc, sigma_iz0 / sc, (n dt sc p_pad)^2 with
+    // sc the larger nonzero cross section scale; ions 1 / (n dt sigma_el g_pad p_pad)
+    R bnd_el, bnd_iz, bnd_q, bnd_inv;
     PhiloxKeys keys;  // round keys of the seed
     uint32_t inst_word, step;
     const int64_t *step_dev;  // non-null: the step number is read from here (captured steps)
@@ -478,18 +481,21 @@ __global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
                     const R v2 = vx * vx + vy * vy + vz * vz;
                     r0 = philox4x32_10(id, a.inst_word, step, 0u, a.keys);
                     const R U0 = u24<R>(r0.x);
+                    // 1 - exp(-x) <= x: a uniform at or above the bound x (with a rounding
+                    // margin) means no collision; below it the deferred work makes the exact test
                     if (a.species == 0) {
+                        // x = n dt sigma(eps) |v| with eps sigma(eps) = sc T(eps), squared so that
+                        // neither a root nor a division is needed: U0 < x pad iff
+                        // (U0 eps)^2 < (n dt sc pad)^2 v^2 T^2 (a zero uniform always goes on)
                         const R eps = a.half_m_over_qe * v2;
-                        const R siz = eps > a.eps_th ? a.sig_iz0 * ((R)1 - m_div(a.eps_th, eps)) : (R)0;
-                        const R st = a.sig_el + siz;
-                        const R xc = a.ng_dt * st * m_sqrt(v2);
-                        // 1 - exp(-x) <= x: a uniform at or above x (with a rounding margin)
-                        // means no collision; below it the deferred work makes the exact test
-                        cand = U0 < xc * a.p_pad;
+                        const R T = a.bnd_el * eps + a.bnd_iz * (eps > a.eps_th ? eps - a.eps_th : (R)0);
+                        const R ue = U0 * eps;
+                        cand = ue * ue < a.bnd_q * v2 * (T * T) || r0.x < 256u;
                     } else {
-                        // the Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms)
-                        // and 1 - exp(-x) <= x: a candidate below this bound gets the exact test
-                        cand = U0 < a.ng_dt * a.sig_el * a.g_pad * (m_sqrt(v2) + a.g_partner_max) * a.p_pad;
+                        // the Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms):
+                        // U0 < B (|v| + g) iff U0 / B - g < 0 or (U0 / B - g)^2 < v^2
+                        const R x = U0 * a.bnd_inv - a.g_partner_max;
+                        cand = x < (R)0 || x * x < v2;
                     }
                 }
             }
@@ -991,6 +997,15 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     a.g_partner_max = (R)(8.2 * std::sqrt(c.gas_temperature_ev * c.qe / c.neutral_mass));
     a.g_pad = (R)1.001;
     a.p_pad = (R)1.0001;
+    {
+        const double sc = c.sigma_el > 0.0 ? c.sigma_el : (c.sigma_iz0 > 0.0 ? c.sigma_iz0 : 1.0);
+        const double A = c.gas_density * c.dt * sc * 1.0001;
+        a.bnd_el = (R)(c.sigma_el / sc);
+        a.bnd_iz = (R)(c.sigma_iz0 / sc);
+        a.bnd_q = (R)(A * A);
+        const double B = c.gas_density * c.dt * c.sigma_el * 1.001 * 1.0001;
+        a.bnd_inv = B > 0.0 ? (R)(1.0 / B) : (R)INFINITY;
+    }
     a.keys = philox_keys(c.seed);
     a.inst_word = (uint32_t)c.instance << 24;
     a.step = (uint32_t)step;
@@ -1038,7 +1053,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
     {
-        Phase ph(ctx, PIC_PHASE_MOVE);
+        Phase ph(ctx, PIC_PHASE_LISTS);
         for (int s = 0; s < nsp; ++s) {
             Species &sp = in.sp[s];
             k_step_reset<<<blocks_for(nl), kT, 0, st>>>(nl, sp.fill, sp.flags, sp.moved,
@@ -1046,6 +1061,9 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
             count_launch(ctx);
             list_ranks(ctx, sp, nl);
         }
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_MOVE);
         for (int s = 0; s < nsp; ++s) {
             PushArgs<R> a = push_args<R>(in, s, step);
             if (ctx->capturing) a.step_dev = ctx->d_step;  // a captured step reads its number on the device

@@ -296,6 +296,7 @@ struct SmallDesc {
     SmallLevel lv[kMaxSmallLevels];
     int32_t off_cg;  // smem offset of the coarsest CG vectors r, p, q (3 n)
     int32_t smem_floats;
+    const float *cinv;  // coarsest level: dense inverse (n x n, row-major), or null (CG)
 };
 
 // Neighbour sum s and diagonal d of row i, so that (A x)_i = d x_i - s.  Uniform levels:
@@ -303,7 +304,8 @@ struct SmallDesc {
 template <typename T>
 __device__ __forceinline__ T uni_row(int nx, int ny, uint32_t magic, int bcx, int bcy, const T *x, int i, T &d) {
     const int iy = (int)__umulhi((uint32_t)i, magic), ix = i - iy * nx;
-    T s = 0, dd = 0;
+    T s = 0;
+    int dd = 0;  // counted in integers: the diagonal is converted once
     if (ix > 0) { s += x[i - 1]; dd += 1; }
     else if (bcx == PIC_BC_PERIODIC) { s += x[i + nx - 1]; dd += 1; }
     else if (bcx == PIC_BC_DIRICHLET) dd += 2;
@@ -316,7 +318,7 @@ __device__ __forceinline__ T uni_row(int nx, int ny, uint32_t magic, int bcx, in
     if (iy < ny - 1) { s += x[i + nx]; dd += 1; }
     else if (bcy == PIC_BC_PERIODIC) { s += x[i - (ny - 1) * nx]; dd += 1; }
     else if (bcy == PIC_BC_DIRICHLET) dd += 2;
-    d = dd;
+    d = (T)dd;
     return s;
 }
 
@@ -526,6 +528,28 @@ __device__ void sm_coarse_cg(const SmallDesc &D, const SmallLevel &L, float *x, 
     __syncthreads();
 }
 
+// Coarsest level by its dense inverse C (at most kDirectN cells): x = C (b - mean(b)) with
+// the mean taken out when the mesh is periodic in both directions (C then inverts
+// A + 1 1^T / n, which maps a zero-mean right-hand side to the zero-mean solution).  Warp w
+// forms rows w, w + 32, ...; all threads of the block call it.
+__device__ void sm_coarse_direct(const SmallDesc &D, const SmallLevel &L, float *x, const float *b, bool singular,
+                                 float *red) {
+    const int n = L.n, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    float mb = 0.0f;
+    if (singular) {
+        float sb = 0.0f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sb += b[i];
+        mb = sm_block_sumf(sb, red) / (float)n;
+    }
+    for (int r = threadIdx.x >> 5; r < n; r += nwarp) {
+        float acc = 0.0f;
+        for (int c = lane; c < n; c += 32) acc = fmaf(__ldg(D.cinv + r * n + c), b[c] - mb, acc);
+        acc = warp_sumf(acc);
+        if (lane == 0) x[r] = acc;
+    }
+    __syncthreads();
+}
+
 // V-cycle over the shared-memory levels; b of the first level must be in place, x of the
 // first level holds the correction on return.
 __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *red) {
@@ -564,7 +588,8 @@ __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *r
         const SmallLevel &L = D.lv[last];
         float *x = sm + L.off, *b = x + L.n;
         float *r = sm + D.off_cg;
-        sm_coarse_cg(D, L, x, b, r, r + L.n, r + 2 * L.n, singular, red);
+        if (D.cinv) sm_coarse_direct(D, L, x, b, singular, red);
+        else sm_coarse_cg(D, L, x, b, r, r + L.n, r + 2 * L.n, singular, red);
     }
     for (int g = last - 1; g >= 0; --g) {
         const SmallLevel &L = D.lv[g], &Cc = D.lv[g + 1];
@@ -746,6 +771,7 @@ SmallDesc small_desc(const Instance &in, int g0) {
     D.off_cg = off;
     off += 3 * (int32_t)in.lv.back().n + 8;
     D.smem_floats = off;
+    D.cinv = in.coarse_inv;
     return D;
 }
 
@@ -789,6 +815,86 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
 }
 }  // namespace
 
+namespace {
+constexpr int kDirectN = 64;  // coarsest levels up to this size are solved by a dense inverse
+
+// Dense inverse of the coarsest level's operator as the shared-memory V-cycle applies it
+// (uniform levels: the 5-point stencil with the wall rules; otherwise the ELL rows with the
+// diagonal 1 / dinv rounded to FP32), plus 1 1^T / n when the mesh is periodic in both
+// directions.  Gauss-Jordan with partial pivoting in FP64; null (the CG is used) for a
+// level larger than kDirectN cells or a singular matrix.
+float *coarse_inverse(pic_ctx *ctx, Instance &in, bool singular) {
+    const Level &L = in.lv.back();
+    const int n = (int)L.n;
+    if (n > kDirectN || n < 1) return nullptr;
+    std::vector<double> A((size_t)n * n, 0.0);
+    auto at = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+    if (L.lmax == 0) {
+        const int nx = L.nx0, ny = L.ny0, bx = in.cfg.bc_x, by = in.cfg.bc_y;
+        for (int i = 0; i < n; ++i) {
+            const int ix = i % nx, iy = i / nx;
+            auto face = [&](bool inside, int j, int bc) {
+                if (inside || bc == PIC_BC_PERIODIC) { at(i, j) -= 1.0; at(i, i) += 1.0; }
+                else if (bc == PIC_BC_DIRICHLET) at(i, i) += 2.0;
+            };
+            face(ix > 0, ix > 0 ? i - 1 : i + nx - 1, bx);
+            face(ix < nx - 1, ix < nx - 1 ? i + 1 : i - nx + 1, bx);
+            face(iy > 0, iy > 0 ? i - nx : i + (ny - 1) * nx, by);
+            face(iy < ny - 1, iy < ny - 1 ? i + nx : i - (ny - 1) * nx, by);
+        }
+    } else {
+        std::vector<int32_t> col((size_t)kEll * n);
+        std::vector<float> val((size_t)kEll * n), dinv(n);
+        GB_CUDA(cudaMemcpyAsync(col.data(), L.col, col.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CUDA(cudaMemcpyAsync(val.data(), L.val, val.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CUDA(cudaMemcpyAsync(dinv.data(), L.dinv, dinv.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int i = 0; i < n; ++i) {
+            at(i, i) += (double)(1.0f / dinv[i]);
+            for (int j = 0; j < kEll; ++j) {
+                const int32_t c = col[(size_t)j * n + i];
+                if (c >= 0) at(i, c) += (double)val[(size_t)j * n + i];
+            }
+        }
+    }
+    if (singular)
+        for (double &a : A) a += 1.0 / n;
+    // Gauss-Jordan on [A | I]
+    std::vector<double> Inv((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Inv[(size_t)i * n + i] = 1.0;
+    double amax = 0.0;
+    for (double a : A) amax = std::max(amax, std::fabs(a));
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(at(i, k)) > std::fabs(at(piv, k))) piv = i;
+        if (!(std::fabs(at(piv, k)) > 1e-12 * amax)) return nullptr;
+        if (piv != k)
+            for (int j = 0; j < n; ++j) {
+                std::swap(at(k, j), at(piv, j));
+                std::swap(Inv[(size_t)k * n + j], Inv[(size_t)piv * n + j]);
+            }
+        const double p = 1.0 / at(k, k);
+        for (int j = 0; j < n; ++j) { at(k, j) *= p; Inv[(size_t)k * n + j] *= p; }
+        for (int i = 0; i < n; ++i) {
+            if (i == k) continue;
+            const double f = at(i, k);
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                at(i, j) -= f * at(k, j);
+                Inv[(size_t)i * n + j] -= f * Inv[(size_t)k * n + j];
+            }
+        }
+    }
+    std::vector<float> C((size_t)n * n);
+    for (size_t t = 0; t < C.size(); ++t) C[t] = (float)Inv[t];
+    float *d = dalloc<float>(in.mesh_mem, C.size());
+    GB_CUDA(cudaMemcpyAsync(d, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    return d;
+}
+}  // namespace
+
 void poisson_setup(pic_ctx *ctx, Instance &in) {
     if (in.mg_cycle) {
         cudaGraphExecDestroy(in.mg_cycle);
@@ -813,6 +919,7 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     // coarsest-level CG needs three extra vectors: give it its own buffers
     Level &c = in.lv.back();
     c.t = dalloc<float>(A, 3 * c.n + 16);
+    in.coarse_inv = coarse_inverse(ctx, in, in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC);
     // meshes whose every level fits one block: the whole solve is one block's work item
     in.small_item = nullptr;
     if (small_from(in) == 0) {
