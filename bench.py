@@ -325,6 +325,10 @@ def run_gpu(args):
         if adapt_every and (k + 1) % adapt_every == 0:
             ctx.adapt()
 
+    # launch shapes chosen by the library's autotuner (setup, untimed: its steps are ordinary
+    # steps under candidate shapes, and no result depends on the shape)
+    tuned_steps = ctx.autotune(args.autotune_steps, allow_notconv=True) if args.autotune_steps > 0 else 0
+    tuning = dict(ctx.tuning(), steps=tuned_steps)
     for k in range(args.warmup):
         one_step(k)
     torch.cuda.synchronize()
@@ -404,7 +408,7 @@ def run_gpu(args):
              "list_tail_moves_since_load": [m for _, m, _ in list_stats],
              "particles_mean": int(particle_steps / args.steps),
              "particles_end": int(final["n_e"] + final["n_i"]), "leaves_end": int(final["n_leaves"]),
-             "poisson_cycles_last": int(final["mg_cycles"])}
+             "poisson_cycles_last": int(final["mg_cycles"]), "autotune": tuning}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32", "data": "synthetic",
@@ -481,6 +485,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune-steps", type=int, default=20,
+                    help="steps the launch-shape autotuner may run during setup (0: default shapes)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

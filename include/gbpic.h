@@ -235,6 +235,26 @@ GBPIC_API pic_status pic_get_list_stats(pic_ctx *ctx, int32_t inst, int32_t spec
 GBPIC_API pic_status pic_read_emag_noalloc(pic_ctx *ctx, int32_t inst, double *out, int64_t cap,
                                            int64_t *n_out);
 
+/* Launch-shape autotuner (no counterpart in the paper: the launch shapes are this
+ * implementation's).  Runs up to max_steps ordinary steps of every instance (they advance the
+ * simulation exactly as pic_step does: no result depends on a launch shape), two steps per
+ * candidate configuration, times each step with CUDA events on the context's stream and keeps
+ * the fastest configuration (a candidate replaces the best one only when at least 2 % faster)
+ * for the context's later steps.  The candidates, searched
+ * one coordinate at a time: the push kernel's block size (128 or 256 threads) and its
+ * resident blocks per SM; for an ensemble whose steps replay as one CUDA graph, also the
+ * share of the GPU each instance's push takes inside the graph (1, 1/2, 1/4, 1/8) and the
+ * number of parallel graph branches (8, 16, 32).  *steps_used (may be NULL) receives the
+ * steps run (at most max_steps; fewer when the candidates or the steps run out).  Status as
+ * pic_step. */
+GBPIC_API pic_status pic_autotune(pic_ctx *ctx, int32_t max_steps, int32_t *steps_used);
+
+/* The configuration the autotuner chose (or the defaults: 256 threads, all resident blocks,
+ * graph share 1/4, 16 branches), and the best step time it measured (0 if never tuned).
+ * Any pointer may be NULL. */
+GBPIC_API pic_status pic_get_tuning(const pic_ctx *ctx, int32_t *push_threads, int32_t *push_blocks_per_sm,
+                                    int32_t *graph_push_div, int32_t *graph_branches, double *best_ms);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 GBPIC_API const char *pic_last_error(void);
 

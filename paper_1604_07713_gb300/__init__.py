@@ -31,7 +31,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_
             "pic_step", "pic_compute_fields", "pic_adapt", "pic_read_fields", "pic_read_mesh",
             "pic_read_particles", "pic_get_counts", "pic_get_step", "pic_set_step",
             "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_get_list_stats", "pic_read_emag_noalloc",
-            "pic_last_error"]
+            "pic_autotune", "pic_get_tuning", "pic_last_error"]
 
 
 class PicConfig(C.Structure):
@@ -111,6 +111,7 @@ def _declare(L):
         "pic_get_timing": [_p, _p, _p, _i32], "pic_get_launch_count": [_p, _p],
         "pic_get_list_stats": [_p, _i32, _i32, _p, _p, _p],
         "pic_read_emag_noalloc": [_p, _i32, _p, _i64, _p],
+        "pic_autotune": [_p, _i32, _p], "pic_get_tuning": [_p, _p, _p, _p, _p, _p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -249,6 +250,26 @@ def pic_get_list_stats(ctx, inst=0, species=0):
     return r.value, m.value, o.value
 
 
+def pic_autotune(ctx, max_steps, allow_notconv=False):
+    """Run up to max_steps steps, one launch configuration each; keep the fastest.  Returns the
+    steps run."""
+    used = C.c_int32(0)
+    _call("pic_autotune", ctx, max_steps, C.byref(used),
+          ok=(PIC_OK, PIC_ENOTCONV) if allow_notconv else (PIC_OK,))
+    return used.value
+
+
+def pic_get_tuning(ctx):
+    """The launch configuration in use: push block size, push blocks per SM (256-thread units,
+    0 = all resident), the GPU share of a push inside a captured ensemble step (1 / div), the
+    captured step's parallel branches, and the best step time the tuner measured (ms)."""
+    nt, bps, div, br = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    ms = C.c_double()
+    _call("pic_get_tuning", ctx, C.byref(nt), C.byref(bps), C.byref(div), C.byref(br), C.byref(ms))
+    return dict(push_threads=nt.value, push_blocks_per_sm=bps.value, graph_push_div=div.value,
+                graph_branches=br.value, best_step_ms=ms.value)
+
+
 def pic_get_launch_count(ctx):
     n = C.c_int64()
     _call("pic_get_launch_count", ctx, C.byref(n))
@@ -326,3 +347,9 @@ class Context:
 
     def counts(self, inst=0):
         return pic_get_counts(self.ctx, inst)
+
+    def autotune(self, max_steps=12, allow_notconv=False):
+        return pic_autotune(self.ctx, max_steps, allow_notconv)
+
+    def tuning(self):
+        return pic_get_tuning(self.ctx)

@@ -256,6 +256,25 @@ pic_status gbpic::guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg
     return guarded(ctx, [&]() -> pic_status { return fn(arg); });
 }
 
+namespace {
+// After a call's steps: exact record totals (the next steps' capacity bound), consistency
+// flags and solver statistics of every instance, in one read-back.
+pic_status end_of_steps(pic_ctx *ctx) {
+    report_all(ctx);
+    pic_status st = PIC_OK;
+    for (Instance &in : ctx->inst) {
+        if (in.mg_worst > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+        if (in.report_err != 0) {
+            ctx->poisoned = true;
+            fail(PIC_ESTATE, "particle bookkeeping violated a slot bound (overflow store or re-layout)");
+        }
+    }
+    if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
+    return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out) {
@@ -305,6 +324,7 @@ pic_status pic_destroy(pic_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (Instance &in : ctx->inst) {
         if (in.mg_cycle) cudaGraphExecDestroy(in.mg_cycle);
+        repairs_release(in);
         in.mesh_mem.release_all();
         in.part_mem[0].release_all();
         in.part_mem[1].release_all();
@@ -406,30 +426,102 @@ pic_status pic_step(pic_ctx *ctx, int32_t n_steps) {
             ensure_species(ctx, in);
             reset_solver_stats(ctx, in);
         }
-        pic_status st = PIC_OK;
-        for (int32_t k = 0; k < n_steps; ++k) {
-            for (Instance &in : ctx->inst) ensure_capacity(ctx, in);
-            if (graph_step_possible(ctx)) {
-                graph_step(ctx);  // an ensemble in steady state: the whole step as one graph replay
-            } else {
-                fields_all(ctx, ctx->step);
-                for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
-            }
-            ++ctx->step;
-        }
-        // exact record totals (the next steps' capacity bound), consistency flags and solver
-        // statistics of every instance, in one read-back
-        report_all(ctx);
-        for (Instance &in : ctx->inst) {
-            if (in.mg_worst > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
-            if (in.report_err != 0) {
-                ctx->poisoned = true;
-                fail(PIC_ESTATE, "particle bookkeeping violated a slot bound (overflow store or re-layout)");
-            }
-        }
-        if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
-        return st;
+        for (int32_t k = 0; k < n_steps; ++k) one_step(ctx);
+        return end_of_steps(ctx);
     });
+}
+
+// Launch-shape autotuner: one ordinary step per candidate configuration, timed with events
+// on the context's stream; coordinate search, the best configuration kept.
+pic_status pic_autotune(pic_ctx *ctx, int32_t max_steps, int32_t *steps_used) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        if (max_steps < 0) fail(PIC_EINVAL, "max_steps < 0");
+        for (Instance &in : ctx->inst) {
+            if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+            ensure_species(ctx, in);
+            reset_solver_stats(ctx, in);
+        }
+        int32_t used = 0;
+        // an ensemble reaches the state in which its steps replay as one graph after a step
+        if (used < max_steps && !graph_step_possible(ctx)) {
+            one_step(ctx);
+            ++used;
+        }
+        const bool graph = graph_step_possible(ctx);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        GB_CUDA(cudaEventCreate(&e0));
+        GB_CUDA(cudaEventCreate(&e1));
+        Tuning best = ctx->tune;
+        double best_ms = 0.0;
+        bool have = false;
+        // a candidate runs kReps timed steps (the faster counts: the first replay of a fresh
+        // capture can be slower) and replaces the best one only if at least 2 % faster
+        constexpr int kReps = 2;
+        auto trial = [&](Tuning t) {
+            if (used + kReps > max_steps) return;
+            if (have && t.push_threads == best.push_threads && t.push_bps == best.push_bps &&
+                t.graph_div == best.graph_div && t.branches == best.branches)
+                return;  // measured already
+            t.epoch = ctx->tune.epoch + 1;
+            ctx->tune = t;
+            if (graph) graph_prepare(ctx);
+            double ms = 0.0;
+            for (int r = 0; r < kReps; ++r) {
+                GB_CUDA(cudaEventRecord(e0, ctx->stream));
+                one_step(ctx);
+                GB_CUDA(cudaEventRecord(e1, ctx->stream));
+                GB_CUDA(cudaEventSynchronize(e1));
+                float m = 0.0f;
+                GB_CUDA(cudaEventElapsedTime(&m, e0, e1));
+                ms = r == 0 ? m : std::min(ms, (double)m);
+                ++used;
+            }
+            if (!have || ms < 0.98 * best_ms) {
+                best_ms = ms;
+                best = t;
+                have = true;
+            }
+        };
+        try {
+            for (int nt : {256, 128}) { Tuning t = best; t.push_threads = nt; trial(t); }
+            if (graph) {
+                for (int div : {4, 1, 2, 8}) { Tuning t = best; t.graph_div = div; trial(t); }
+                for (int br : {16, 8, 32}) { Tuning t = best; t.branches = br; trial(t); }
+            } else {
+                for (int bps : {0, 2, 1}) { Tuning t = best; t.push_bps = bps; trial(t); }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (have) {
+            best.best_ms = best_ms;
+            best.epoch = ctx->tune.epoch + 1;
+            ctx->tune = best;
+        }
+        if (steps_used) *steps_used = used;
+        return end_of_steps(ctx);
+    });
+}
+
+pic_status pic_get_tuning(const pic_ctx *ctx, int32_t *push_threads, int32_t *push_blocks_per_sm,
+                          int32_t *graph_push_div, int32_t *graph_branches, double *best_ms) {
+    if (!ctx) {
+        set_error("null context");
+        return PIC_EINVAL;
+    }
+    const Tuning &t = ctx->tune;
+    if (push_threads) *push_threads = t.push_threads;
+    if (push_blocks_per_sm) *push_blocks_per_sm = t.push_bps;
+    if (graph_push_div) *graph_push_div = t.graph_div;
+    if (graph_branches) *graph_branches = t.branches;
+    if (best_ms) *best_ms = t.best_ms;
+    set_error("");
+    return PIC_OK;
 }
 
 pic_status pic_adapt(pic_ctx *ctx, int32_t flags) {

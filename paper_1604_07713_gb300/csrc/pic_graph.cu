@@ -21,7 +21,6 @@ namespace gbpic {
 
 namespace {
 constexpr int kT = 256;
-constexpr int kBranches = 16;  // parallel branches of a captured step
 
 // One entry per instance: what the end-of-call report reads.
 struct ReportTab {
@@ -66,10 +65,14 @@ __global__ void k_report(const ReportTab *__restrict__ tab, Report *__restrict__
     }
 }
 
+// The parallel branches of a captured step (their number is a tuned launch shape).
 void ensure_branches(pic_ctx *ctx) {
-    if (!ctx->fork.empty()) return;
-    ctx->fork.resize(kBranches);
-    ctx->fork_ev.resize(kBranches + 1);
+    const size_t nb = (size_t)std::max(1, ctx->tune.branches);
+    if (ctx->fork.size() == nb) return;
+    for (auto &s : ctx->fork) cudaStreamDestroy(s);
+    for (auto &e : ctx->fork_ev) cudaEventDestroy(e);
+    ctx->fork.assign(nb, nullptr);
+    ctx->fork_ev.assign(nb + 1, nullptr);
     for (auto &s : ctx->fork) GB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     for (auto &e : ctx->fork_ev) GB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
@@ -108,7 +111,7 @@ void capture_step(pic_ctx *ctx) {
         // deposits, branch per instance
         fork_from(ctx, cs);
         for (int i = 0; i < n; ++i) {
-            ctx->stream = ctx->fork[i % kBranches];
+            ctx->stream = ctx->fork[i % ctx->fork.size()];
             deposit(ctx, ctx->inst[i], walls[i].data());
         }
         ctx->stream = cs;
@@ -124,7 +127,7 @@ void capture_step(pic_ctx *ctx) {
         // corner fields and particle steps, branch per instance
         fork_from(ctx, cs);
         for (int i = 0; i < n; ++i) {
-            ctx->stream = ctx->fork[i % kBranches];
+            ctx->stream = ctx->fork[i % ctx->fork.size()];
             node_e(ctx, ctx->inst[i], walls[i].data());
             particle_step(ctx, ctx->inst[i], ctx->step, false);
         }
@@ -152,8 +155,32 @@ void capture_step(pic_ctx *ctx) {
     GB_CUDA(e);
     ctx->graph_mesh_epoch = ctx->mesh_epoch;
     ctx->graph_lists_epoch = ctx->lists_epoch;
+    ctx->graph_tune_epoch = ctx->tune.epoch;
+}
+
+bool graph_current(const pic_ctx *ctx) {
+    return ctx->step_graph && ctx->graph_mesh_epoch == ctx->mesh_epoch && ctx->graph_lists_epoch == ctx->lists_epoch &&
+           ctx->graph_tune_epoch == ctx->tune.epoch;
 }
 }  // namespace
+
+// Capture (if the captured step is out of date) and upload the step graph now, so that the
+// next replay does no host work beyond the launch.
+void graph_prepare(pic_ctx *ctx) {
+    if (!graph_current(ctx)) capture_step(ctx);
+    GB_CUDA(cudaGraphUpload(ctx->step_graph, ctx->stream));
+}
+
+void one_step(pic_ctx *ctx) {
+    for (Instance &in : ctx->inst) ensure_capacity(ctx, in);
+    if (graph_step_possible(ctx)) {
+        graph_step(ctx);  // an ensemble in steady state: the whole step as one graph replay
+    } else {
+        fields_all(ctx, ctx->step);
+        for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
+    }
+    ++ctx->step;
+}
 
 // Steady state of every instance of an ensemble: batched one-block Poisson solves and valid
 // deposit sums for every species (so the step has no host decision left).
@@ -168,8 +195,7 @@ bool graph_step_possible(pic_ctx *ctx) {
 }
 
 void graph_step(pic_ctx *ctx) {
-    if (!ctx->step_graph || ctx->graph_mesh_epoch != ctx->mesh_epoch || ctx->graph_lists_epoch != ctx->lists_epoch)
-        capture_step(ctx);
+    if (!graph_current(ctx)) capture_step(ctx);
     // this step's number and wall potentials, as an uncaptured step computes them (pageable
     // source: the copies are staged before they return, so the buffer may be reused)
     const int n = (int)ctx->inst.size();

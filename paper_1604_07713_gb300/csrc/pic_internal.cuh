@@ -8,6 +8,7 @@
 #include <string>
 #include <map>
 #include <unordered_map>
+#include <functional>
 #include <vector>
 
 #include "../../include/gbpic.h"
@@ -129,6 +130,10 @@ struct Species {
     void *stay_hi = nullptr, *stay_lo = nullptr;               // R [nleaf]
     double *wsum = nullptr;                                     // [nleaf]
     bool sums_valid = false;
+    // the per-step list repairs as a graph of two IF nodes (pic_lists.cu), valid for the
+    // mesh and list epochs it was built in
+    cudaGraphExec_t repair = nullptr;
+    int64_t repair_mesh_epoch = -1, repair_lists_epoch = -1;
 };
 
 template <typename R> struct SoA {
@@ -199,6 +204,18 @@ struct TimingRec {
 
 }  // namespace gbpic
 
+namespace gbpic {
+// Launch shapes that no result depends on, chosen by pic_autotune (defaults until then).
+struct Tuning {
+    int push_threads = 256;  // block size of the push kernel (128 or 256)
+    int push_bps = 0;        // resident push blocks per SM (0: as many as fit)
+    int graph_div = 4;       // captured ensemble steps: each push takes 1/graph_div of the GPU
+    int branches = 16;       // captured ensemble steps: parallel branches
+    double best_ms = 0.0;    // best step time the tuner measured
+    int64_t epoch = 0;       // bumped on every change (a captured step is captured again)
+};
+}  // namespace gbpic
+
 struct pic_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -230,6 +247,8 @@ struct pic_ctx {
     void *report_dev = nullptr, *report_host = nullptr;  // end-of-call report, one entry per instance
     void *report_tab = nullptr;      // device table the report kernel reads
     int64_t report_epoch = -1;
+    gbpic::Tuning tune;
+    int64_t graph_tune_epoch = -1;
 };
 
 namespace gbpic {
@@ -349,9 +368,16 @@ void lists_installed(pic_ctx *ctx, Species &sp, int64_t nl);  // lim, tail after
 void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl);       // rank0 from start / end
 void count_totals(pic_ctx *ctx, Instance &in);  // flags[1] of every species, device side
 void place_overflow(pic_ctx *ctx, Instance &in, int s);  // tail moves, else re-layout
+void repairs_release(Instance &in);                       // the cached repair graphs
+// Capture into the graph that stream `st` is capturing: a one-thread kernel that reads *value,
+// then an IF node whose body (the launches `body` issues on ctx->stream) runs when it was
+// nonzero.  The body's launches are not counted (they run only when needed).
+void capture_if(pic_ctx *ctx, cudaStream_t st, const int32_t *value, const std::function<void()> &body);
 // pic_graph.cu
 bool graph_step_possible(pic_ctx *ctx);
+void one_step(pic_ctx *ctx);  // one step of every instance (graph replay or launches), step += 1
 void graph_step(pic_ctx *ctx);            // one step of every instance as one graph replay
+void graph_prepare(pic_ctx *ctx);         // capture (if out of date) and upload the step graph
 void graph_release(pic_ctx *ctx);
 void report_all(pic_ctx *ctx);            // exact totals, error flags, solver stats of every instance (syncs)
 void fields_all(pic_ctx *ctx, int64_t step);

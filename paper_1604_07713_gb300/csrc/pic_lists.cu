@@ -259,20 +259,70 @@ template <typename R> void relayout_lists(pic_ctx *ctx, Instance &in, int s) {
     check_launch("relayout_lists");
 }
 
+__global__ void k_set_if(cudaGraphConditionalHandle h, const int32_t *__restrict__ value) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, *value != 0 ? 1u : 0u);
+}
+
+// The repairs after a push, as two IF nodes so that a step without overflow runs two
+// one-thread kernels instead of a dozen launches that return at once: records in the
+// overflow store (flags[0]) -> move their leaves to the tail and place them; tail used up
+// (flags[5]) -> lay every list out again.
+template <typename R> void capture_repairs(pic_ctx *ctx, Instance &in, int s, cudaStream_t st) {
+    Species &sp = in.sp[s];
+    const int64_t nl = in.nleaf;
+    capture_if(ctx, st, sp.flags + 0, [&]() {
+        const SoA<R> d = soa<R>(sp, sp.cur);
+        const SoA<R> o = soa_ovf<R>(sp);
+        k_move_to_tail<R><<<152 * 4, kT, 0, ctx->stream>>>(sp.moved, nl, sp.cap, sp.start, sp.end, sp.lim, sp.stay,
+                                                           sp.fill, d, sp.key, sp.aux, sp.flags);
+        k_place_ovf<R><<<152 * 2, kT, 0, ctx->stream>>>(sp.end, sp.cap, o, sp.ovf_key, sp.ovf_aux, sp.ovf_dest,
+                                                        sp.ovf_slot, d, sp.key, sp.aux, sp.moved, nl, sp.flags);
+    });
+    capture_if(ctx, st, sp.flags + 5, [&]() { relayout_lists<R>(ctx, in, s); });
+}
+
 template <typename R> void place_impl(pic_ctx *ctx, Instance &in, int s) {
     Species &sp = in.sp[s];
-    cudaStream_t st = ctx->stream;
-    const int64_t nl = in.nleaf;
-    const SoA<R> d = soa<R>(sp, sp.cur);
-    const SoA<R> o = soa_ovf<R>(sp);
-    // leaves out of free slots move to the tail
-    k_move_to_tail<R><<<152 * 4, kT, 0, st>>>(sp.moved, nl, sp.cap, sp.start, sp.end, sp.lim, sp.stay, sp.fill, d,
-                                              sp.key, sp.aux, sp.flags);
-    k_place_ovf<R><<<152 * 2, kT, 0, st>>>(sp.end, sp.cap, o, sp.ovf_key, sp.ovf_aux, sp.ovf_dest, sp.ovf_slot, d,
-                                           sp.key, sp.aux, sp.moved, nl, sp.flags);
-    count_launch(ctx, 2);
-    // tail used up: every list again, in leaf order (gated on flags[5])
-    relayout_lists<R>(ctx, in, s);
+    if (ctx->capturing) {  // inside a captured step: the IF nodes go into that graph
+        capture_repairs<R>(ctx, in, s, ctx->stream);
+        count_launch(ctx, 2);
+        return;
+    }
+    if (!sp.repair || sp.repair_mesh_epoch != ctx->mesh_epoch || sp.repair_lists_epoch != ctx->lists_epoch) {
+        if (sp.repair) {
+            cudaGraphExecDestroy(sp.repair);
+            sp.repair = nullptr;
+        }
+        cudaStream_t cs;
+        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaStream_t saved = ctx->stream;
+        const int64_t l0 = ctx->launches;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        try {
+            if (e != cudaSuccess) GB_CUDA(e);
+            ctx->stream = cs;
+            capture_repairs<R>(ctx, in, s, cs);
+            ctx->stream = saved;
+            e = cudaStreamEndCapture(cs, &g);
+        } catch (...) {
+            ctx->stream = saved;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            ctx->launches = l0;
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        ctx->launches = l0;
+        cudaStreamDestroy(cs);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&sp.repair, g, 0);
+        if (g) cudaGraphDestroy(g);
+        GB_CUDA(e);
+        sp.repair_mesh_epoch = ctx->mesh_epoch;
+        sp.repair_lists_epoch = ctx->lists_epoch;
+    }
+    GB_CUDA(cudaGraphLaunch(sp.repair, ctx->stream));
+    count_launch(ctx, 2);  // the two condition kernels (the bodies run only when needed)
 }
 
 // Host-driven compaction: every record counts as staying, nothing enters.
@@ -399,6 +449,59 @@ void count_totals(pic_ctx *ctx, Instance &in) {
         count_launch(ctx);
     }
     check_launch("count_totals");
+}
+
+void capture_if(pic_ctx *ctx, cudaStream_t st, const int32_t *value, const std::function<void()> &body) {
+    cudaStreamCaptureStatus status = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    GB_CUDA(cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &nd));
+    if (status != cudaStreamCaptureStatusActive) fail(PIC_ECUDA, "capture_if outside a stream capture");
+    cudaGraphConditionalHandle h = 0;
+    GB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    k_set_if<<<1, 32, 0, st>>>(h, value);
+    GB_CUDA(cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    GB_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    GB_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // the body, captured on a private stream into the node's body graph
+    cudaStream_t bs;
+    GB_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    const int64_t l0 = ctx->launches;
+    cudaGraph_t bg = nullptr;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    try {
+        if (e != cudaSuccess) GB_CUDA(e);
+        ctx->stream = bs;
+        body();
+        ctx->stream = saved;
+        e = cudaStreamEndCapture(bs, &bg);
+    } catch (...) {
+        ctx->stream = saved;
+        cudaStreamEndCapture(bs, &bg);
+        ctx->launches = l0;
+        cudaStreamDestroy(bs);
+        throw;
+    }
+    ctx->launches = l0;
+    cudaStreamDestroy(bs);
+    GB_CUDA(e);
+}
+
+void repairs_release(Instance &in) {
+    for (Species &sp : in.sp)
+        if (sp.repair) {
+            cudaGraphExecDestroy(sp.repair);
+            sp.repair = nullptr;
+        }
 }
 
 void place_overflow(pic_ctx *ctx, Instance &in, int s) {

@@ -379,8 +379,9 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
 // so the leaf's own records are compacted in place; everything the warp reads of the next
 // chunk lies beyond every slot it writes in this one.  Entering and spawned records only go
 // to free slots past end[], which no warp reads during the pass.
-template <typename R>
-__global__ void __launch_bounds__(kT, 3) k_push(PushArgs<R> a) {
+// NT threads per block (a tuned launch shape); 768 threads per SM either way: 80 registers.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
     extern __shared__ unsigned char push_smem[];
     Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -1033,22 +1034,30 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     cudaStream_t st = ctx->stream;
     const int nsp = in.cfg.n_species;
     const int64_t nl = in.nleaf;
-    const unsigned wb = warp_blocks(nl);
-    // the push kernel runs persistent warps: as many blocks as are resident at once
-    const size_t push_smem = (size_t)(kT / 32) * sizeof(Queue<R>);
-    static int resident = 0, sms = 0;  // per process: one device model, one kernel per R
-    if (!resident) {
-        GB_CUDA(cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_smem));
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_push<R>, kT, push_smem));
+    // the push kernel runs persistent warps: as many blocks as are resident at once (or as the
+    // tuned share allows), in blocks of 128 or 256 threads (a tuned launch shape)
+    const int nt = ctx->tune.push_threads == 128 ? 128 : 256;
+    const size_t push_smem = (size_t)(nt / 32) * sizeof(Queue<R>);
+    static int resident[2] = {0, 0}, sms = 0;  // per process: one device model; [128, 256]
+    if (!sms) {
+        const size_t sm128 = 4 * sizeof(Queue<R>), sm256 = 8 * sizeof(Queue<R>);
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_push<R, 128>, 128, sm128));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_push<R, 256>, 256, sm256));
+        if (resident[0] < 1 || resident[1] < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
         int dev = 0;
         GB_CUDA(cudaGetDevice(&dev));
         GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (resident < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
     }
+    const int wpb = nt / 32;
+    const unsigned wb = (unsigned)std::max<int64_t>(1, (nl + wpb - 1) / wpb);
+    int bps = resident[nt == 128 ? 0 : 1];
+    if (ctx->tune.push_bps > 0) bps = std::min(bps, ctx->tune.push_bps * (256 / nt));  // 256-thread units
     // a captured ensemble step runs instances on parallel branches: a push that takes a
-    // quarter of the GPU lets four instances' pushes run side by side
-    const unsigned full = (unsigned)(resident * sms);
-    const unsigned pb = std::min<unsigned>(wb, ctx->capturing ? std::max(1u, full / 4) : full);
+    // share of the GPU lets several instances' pushes run side by side
+    const unsigned full = (unsigned)(bps * sms);
+    const unsigned pb = std::min<unsigned>(wb, ctx->capturing ? std::max(1u, full / (unsigned)std::max(1, ctx->tune.graph_div)) : full);
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
     Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
@@ -1074,7 +1083,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                     a.ion_total = ion->rank0 + nl;
                 }
             }
-            k_push<R><<<pb, kT, push_smem, st>>>(a);
+            if (nt == 128) k_push<R, 128><<<pb, 128, push_smem, st>>>(a);
+            else k_push<R, 256><<<pb, 256, push_smem, st>>>(a);
             count_launch(ctx);
         }
     }

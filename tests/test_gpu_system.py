@@ -122,3 +122,33 @@ def test_ensemble_steps_replay_one_graph_and_match_uncaptured_steps():
         for s in (0, 1):
             for k in ("id", "x", "vx", "w"):
                 assert np.array_equal(batched[i][s][k], alone[s][k]), (i, s, k)
+
+
+@pytest.mark.parametrize("n_inst", [1, 3])
+def test_autotuned_steps_equal_default_steps(n_inst):
+    # the tuner's steps are ordinary steps under other launch shapes (push block size, blocks
+    # per SM, the GPU share and branches of a captured ensemble step): the state after them
+    # equals stepping with the default shapes, bit for bit
+    cases = [_ccp(32 + 8 * i, 10, 4 + i, 150.0 + 50 * i, 1e21) for i in range(n_inst)]
+    for i, (cfg, _, _) in enumerate(cases):
+        cfg["instance"] = i
+
+    def run(tune):
+        with G.Context([c[0] for c in cases]) as ctx:
+            for i, (cfg, mesh, parts) in enumerate(cases):
+                ctx.set_mesh_dict(mesh, inst=i)
+                for s in sorted(parts):
+                    ctx.load(s, **parts[s], inst=i)
+            used = ctx.autotune(11) if tune else 0
+            ctx.step(12 - used)
+            out = [[ctx.particles(s, inst=i) for s in (0, 1)] for i in range(n_inst)]
+            return out, used, ctx.tuning()
+
+    a, used, t = run(True)
+    b, _, t0 = run(False)
+    assert 5 <= used <= 11 and t["best_step_ms"] > 0.0 and t0["best_step_ms"] == 0.0
+    assert t["push_threads"] in (128, 256) and t["graph_branches"] in (8, 16, 32)
+    for i in range(n_inst):
+        for s in (0, 1):
+            for k in ("id", "x", "y", "vx", "vy", "vz", "w"):
+                assert np.array_equal(a[i][s][k], b[i][s][k]), (i, s, k)
