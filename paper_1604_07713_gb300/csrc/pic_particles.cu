@@ -730,45 +730,7 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
     }
 }
 
-constexpr int kSortLane = 8;  // entering regions up to this long are sorted by one lane
-
-// One lane sorts a short entering region [b0, b0 + k), k <= kSortLane: ranks of the keys
-// (unrolled, in registers), then every record to q0 + its rank (through the scratch buffer
-// when source and destination overlap).
-template <typename R>
-__device__ __forceinline__ void sort_short(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0,
-                                           SoA<R> d, SoA<R> t) {
-    uint32_t key[kSortLane];
-#pragma unroll
-    for (int i = 0; i < kSortLane; ++i) key[i] = i < k ? a.key[b0 + i] : 0xFFFFFFFFu;
-    int rank[kSortLane];
-#pragma unroll
-    for (int i = 0; i < kSortLane; ++i) {
-        int r = 0;
-#pragma unroll
-        for (int j = 0; j < kSortLane; ++j) r += (key[j] < key[i]) ? 1 : 0;
-        rank[i] = r;
-    }
-    const bool overlap = q0 + k > b0;
-    if (overlap) {
-#pragma unroll
-        for (int i = 0; i < kSortLane; ++i)
-            if (i < k) {
-                const int32_t p = b0 + i;
-                t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p]; t.vz[p] = d.vz[p];
-                t.w[p] = d.w[p]; t.id[p] = d.id[p];
-            }
-    }
-    const SoA<R> src = overlap ? t : d;
-#pragma unroll
-    for (int i = 0; i < kSortLane; ++i)
-        if (i < k) {
-            const int32_t p = b0 + i, q = q0 + rank[i];
-            const R u = src.u[p], v = src.v[p], vx = src.vx[p], vy = src.vy[p], vz = src.vz[p], w = src.w[p];
-            const uint32_t id = spawn_id(a, span, key[i], key[i] >= span ? a.aux[p] : 0u, src.id[p]);
-            d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
-        }
-}
+constexpr int kSortLane = 8;  // entering regions up to this long are sorted by a leaf's 8-lane group
 
 // The leaf's weight for the next deposit: staying sum + entering particles in order (a few
 // entering particles: one lane, in order; many: lanes, then an exact combine).
@@ -780,25 +742,67 @@ template <typename R> __device__ __forceinline__ double leaf_weight_seq(const So
     return st + ((double)sum - (double)c);
 }
 
-// Entering regions of every leaf, 32 leaves per warp pass: short regions are sorted by the
-// leaf's own lane; medium ones (up to kSortSmem) are queued for k_sort_medium, long ones for
-// k_sort_big.  Sets end[L] and, with stay sums, the leaf's deposit weight.
+// Entering regions of every leaf, 8 lanes per leaf (4 leaves per warp pass): a short region
+// (k <= kSortLane records) is sorted by its leaf's lane group, lane i holding record b0 + i,
+// so that each of the record's arrays is read and written in one contiguous access per leaf;
+// every record is in registers before any is written (the region and its destination may
+// overlap).  Medium regions (up to kSortSmem) are queued for k_sort_medium, long ones for
+// k_sort_big.  Sets end[L] and, with stay sums, the leaf's deposit weight: the staying sum
+// plus the entering weights in key order.
 template <typename R>
 __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<R> t) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
-    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < a.nleaf;
-         L += (int64_t)gridDim.x * blockDim.x) {
-        int32_t b0, k, q0;
-        entering_region(a, L, b0, k, q0);
-        if (k < 0) continue;
-        if (k <= kSortLane) {
-            if (k > 0) sort_short<R>(a, span, b0, k, q0, d, t);
-            if (a.wsum) a.wsum[L] = leaf_weight_seq<R>(a, L, d, q0, k);
-            a.end[L] = q0 + k;
-        } else if (k <= kSortSmem) {
-            a.med[atomicAdd(a.med + a.nleaf, 1)] = (int32_t)L;
-        } else {
-            a.big[atomicAdd(a.big + a.nleaf, 1)] = (int32_t)L;
+    const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t W = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; W * 4 < a.nleaf; W += nwarp) {
+        const int64_t L = W * 4 + g;
+        const bool has = L < a.nleaf;
+        int32_t b0 = 0, k = 0, q0 = 0;
+        if (has && gl == 0) entering_region(a, L, b0, k, q0);
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0, 8);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0, 8);
+        q0 = __shfl_sync(0xFFFFFFFFu, q0, 0, 8);
+        const bool shortr = has && k >= 0 && k <= kSortLane;
+        const bool mine = shortr && gl < k;
+        const int32_t p = b0 + gl;
+        R u = 0, v = 0, vx = 0, vy = 0, vz = 0, w = 0;
+        uint32_t id = 0, key = 0xFFFFFFFFu;
+        if (mine) {
+            u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p];
+            id = d.id[p];
+            key = a.key[p];
+            id = spawn_id(a, span, key, key >= span ? a.aux[p] : 0u, id);
+        }
+        // rank among the group's keys (keys are distinct)
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < kSortLane; ++j) {
+            const uint32_t kj = __shfl_sync(0xFFFFFFFFu, key, j, 8);
+            r += (kj < key) ? 1 : 0;
+        }
+        __syncwarp();  // every load of the warp is done before any store
+        if (mine) {
+            const int32_t q = q0 + r;
+            d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
+        }
+        if (a.wsum) {
+            // the entering weights in key order, summed by the group's first lane
+            R sum = 0, c = 0;
+#pragma unroll
+            for (int rr = 0; rr < kSortLane; ++rr) {
+                const uint32_t who = (__ballot_sync(0xFFFFFFFFu, mine && r == rr) >> (8 * g)) & 0xFFu;
+                const R wr = __shfl_sync(0xFFFFFFFFu, w, who ? __ffs(who) - 1 : 0, 8);
+                if (who) kahan_add(sum, c, wr);
+            }
+            if (shortr && gl == 0) {
+                const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
+                a.wsum[L] = st + ((double)sum - (double)c);
+            }
+        }
+        if (gl == 0 && has && k >= 0) {
+            if (k <= kSortLane) a.end[L] = q0 + k;
+            else if (k <= kSortSmem) a.med[atomicAdd(a.med + a.nleaf, 1)] = (int32_t)L;
+            else a.big[atomicAdd(a.big + a.nleaf, 1)] = (int32_t)L;
         }
     }
 }
@@ -910,7 +914,8 @@ __global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, const i
 template <typename R> void sort_lists(pic_ctx *ctx, SortArgs a, SoA<R> d, SoA<R> t) {
     GB_CUDA(cudaMemsetAsync(a.big + a.nleaf, 0, 4, ctx->stream));
     GB_CUDA(cudaMemsetAsync(a.med + a.nleaf, 0, 4, ctx->stream));
-    k_sort_entering<R><<<blocks_for(a.nleaf), kT, 0, ctx->stream>>>(a, d, t);
+    k_sort_entering<R><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((a.nleaf + 31) / 32, 152 * 16)), kT, 0,
+                         ctx->stream>>>(a, d, t);
     k_sort_medium<R><<<std::min<unsigned>(warp_blocks(a.nleaf), 152u * 8u), kT, 0, ctx->stream>>>(a, d, t);
     const size_t smem = (size_t)kSortBig * sizeof(unsigned long long);
     static bool attr = false;  // per R, set once (not while a step is being captured)
