@@ -287,7 +287,7 @@ struct SmallLevel {
     // A level of root boxes only (no refinement) is a row-major nx x ny grid whose operator
     // is the 5-point stencil; it is applied from the cell index, without the ELL arrays.
     int32_t uniform, nx, ny;
-    uint32_t nx_magic;   // floor(i / nx) == __umulhi(i, nx_magic) for every cell index i < n
+    uint32_t nx_magic;   // floor(i / nx) == mdiv(i, nx_magic) for every cell index i < n
     uint32_t nxh_magic;  // the same for nx / 2 (uniform levels with even nx)
 };
 struct SmallDesc {
@@ -299,11 +299,16 @@ struct SmallDesc {
     const float *cinv;  // coarsest level: dense inverse (n x n, row-major), or null (CG)
 };
 
+// floor(i / d) by a multiply-high reciprocal m = floor((2^32 - 1) / d) + 1; m = 0 stands for
+// d = 1 (whose reciprocal 2^32 has no 32-bit form).
+__host__ __device__ __forceinline__ uint32_t mdiv_magic(uint32_t d) { return d <= 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int mdiv(int i, uint32_t m) { return m ? (int)__umulhi((uint32_t)i, m) : i; }
+
 // Neighbour sum s and diagonal d of row i, so that (A x)_i = d x_i - s.  Uniform levels:
 // face conductance 1 to each neighbour, 2 to a Dirichlet wall, none at a Neumann wall.
 template <typename T>
 __device__ __forceinline__ T uni_row(int nx, int ny, uint32_t magic, int bcx, int bcy, const T *x, int i, T &d) {
-    const int iy = (int)__umulhi((uint32_t)i, magic), ix = i - iy * nx;
+    const int iy = mdiv(i, magic), ix = i - iy * nx;
     T s = 0;
     int dd = 0;  // counted in integers: the diagonal is converted once
     if (ix > 0) { s += x[i - 1]; dd += 1; }
@@ -346,7 +351,7 @@ __device__ __forceinline__ float sm_row(const SmallDesc &D, const SmallLevel &L,
 
 __device__ __forceinline__ int sm_color(const SmallLevel &L, int i) {
     if (!L.uniform) return L.color[i];
-    const int iy = (int)__umulhi((uint32_t)i, L.nx_magic);
+    const int iy = mdiv(i, L.nx_magic);
     return (i - iy * L.nx + iy) & 1;
 }
 
@@ -370,7 +375,7 @@ __device__ void sm_smooth(const SmallDesc &D, const SmallLevel &L, float *x, con
                 const int j = threadIdx.x + 1024 * k;
                 cell[k] = -1;
                 if (j < half) {
-                    const int iy = (int)__umulhi((uint32_t)j, L.nxh_magic), m = j - iy * nxh;
+                    const int iy = mdiv(j, L.nxh_magic), m = j - iy * nxh;
                     const int i = iy * L.nx + 2 * m + ((c + iy) & 1);
                     float d, dinv;
                     const float sn = sm_row(D, L, x, i, d, dinv);
@@ -562,7 +567,7 @@ __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *r
         for (int p = threadIdx.x; p < Cc.n; p += blockDim.x) {
             float s = 0.0f;
             if (L.uniform && Cc.uniform) {
-                const int py = (int)__umulhi((uint32_t)p, Cc.nx_magic), px = p - py * Cc.nx;
+                const int py = mdiv(p, Cc.nx_magic), px = p - py * Cc.nx;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int i = (2 * py + (k >> 1)) * L.nx + 2 * px + (k & 1);
@@ -597,7 +602,7 @@ __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *r
         const float *xc = sm + Cc.off;
         if (L.uniform && Cc.uniform) {
             for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-                const int iy = (int)__umulhi((uint32_t)i, L.nx_magic), ix = i - iy * L.nx;
+                const int iy = mdiv(i, L.nx_magic), ix = i - iy * L.nx;
                 x[i] += xc[(iy >> 1) * Cc.nx + (ix >> 1)];
             }
         } else {
@@ -759,12 +764,12 @@ SmallDesc small_desc(const Instance &in, int g0) {
         S.nx = L.nx0;
         S.ny = L.ny0;
         // multiply-high reciprocal: floor(i * m / 2^32) == floor(i / nx) for the i < n used here
-        S.nx_magic = 0xFFFFFFFFu / (uint32_t)L.nx0 + 1u;
+        S.nx_magic = mdiv_magic((uint32_t)L.nx0);
         const uint32_t nxh = std::max(1, L.nx0 / 2);
-        S.nxh_magic = 0xFFFFFFFFu / nxh + 1u;
+        S.nxh_magic = mdiv_magic(nxh);
+        auto q = [](int64_t i, uint32_t m) { return m ? (int64_t)(((uint64_t)i * m) >> 32) : i; };
         for (int64_t i = 0; i < L.n; ++i)
-            if ((int64_t)(((uint64_t)i * S.nx_magic) >> 32) != i / L.nx0 ||
-                (int64_t)(((uint64_t)i * S.nxh_magic) >> 32) != i / (int64_t)nxh)
+            if (q(i, S.nx_magic) != i / L.nx0 || q(i, S.nxh_magic) != i / (int64_t)nxh)
                 fail(PIC_EINVAL, "index division check failed");
         off += 2 * (int32_t)L.n;
     }

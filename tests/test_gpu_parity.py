@@ -113,6 +113,40 @@ def test_fields_parity(precision, amr):
     assert c["mg_rel_res"] <= cfg["mg_rel_tol"]
 
 
+@pytest.mark.parametrize("precision", [W.FP32, W.FP64])
+def test_fields_parity_multiblock_levels(precision):
+    # more than 8192 leaves: the finest levels are solved by the multi-block (cooperative)
+    # multigrid, the coarse ones by the one-block tail
+    cfg, mesh, parts = _ccp_small(precision, nx=96, ny=64, ppc=2)
+    mesh = _amr_mesh(96, 64, mesh["h0"], 1, 11, py=True)
+    assert mesh["root"].size > 8192
+    cfg["max_level"] = 1
+    sim = _oracle(cfg, mesh, parts)
+    rho_o, phi_o, E_o = sim.fields()
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.compute_fields()
+        phi = ctx.fields(G.PIC_FIELD_PHI)
+        E = ctx.fields(G.PIC_FIELD_NODE_E)
+        c = ctx.counts()
+    tol = 1e-5 if precision == W.FP32 else 1e-12
+    assert _rel(phi, phi_o) < tol
+    assert _rel(E.reshape(-1), E_o.reshape(-1)) < tol
+    assert c["mg_rel_res"] <= cfg["mg_rel_tol"] and c["mg_cycles"] >= 1
+
+
+def test_fields_periodic_cold_plasma_multiblock_fp64():
+    # 128 x 128 periodic cells: the singular (zero-mean) branch of the multi-block solve
+    cfg, mesh, parts = W.cold_plasma(n_side=128, ppc=1)
+    sim = _oracle(cfg, mesh, parts)
+    rho_o, phi_o, E_o = sim.fields()
+    with _gpu(cfg, mesh, parts) as ctx:
+        ctx.compute_fields()
+        phi = ctx.fields(G.PIC_FIELD_PHI)
+        E = ctx.fields(G.PIC_FIELD_NODE_E)
+    assert _rel(phi, phi_o) < 1e-12
+    assert _rel(E.reshape(-1), E_o.reshape(-1)) < 1e-12
+
+
 def test_fields_periodic_cold_plasma_fp64():
     cfg, mesh, parts = W.cold_plasma(n_side=32, ppc=4)
     sim = _oracle(cfg, mesh, parts)
