@@ -188,6 +188,7 @@ struct Instance {
     float *coarse_inv = nullptr;         // coarsest multigrid level: dense inverse (small levels)
     void *small_item = nullptr;          // meshes that fit one block: the solve's work item
     size_t small_smem = 0;               // and its dynamic shared memory
+    int small_cluster = 1;               // CTAs of its cluster when solved alone
     cudaGraphExec_t mg_cycle = nullptr;  // multi-block meshes: one captured cycle (V-cycle,
     int64_t mg_cycle_nodes = 0;          // correction, residual, norm read-back) and its launches
     int64_t mg_pre_nodes = 0;            // launches before the device-side cycle loop

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "pic_internal.cuh"
 
 namespace gbpic {
@@ -625,9 +627,57 @@ __global__ void __launch_bounds__(1024, 1) k_tail_vcycle(SmallDesc D, const floa
     for (int i = threadIdx.x; i < L.n; i += blockDim.x) gx[i] = sm[L.off + i];
 }
 
+
+// FP64 sums over the cells of a small solve that come out the same whatever the number C of
+// CTAs in the instance's cluster: chunk c (cells 1024 c .. 1024 c + 1023) is summed by CTA
+// c mod C as a fixed tree (warp shuffles, then the 32 warp sums in order), and the chunk
+// sums by the leader CTA in chunk order.  f(i, a, b) adds cell i's terms to a and b; every
+// thread of the cluster receives both totals.  Collective over the cluster.
+constexpr int kSmallChunks = kSmallN / 1024;
+template <typename F>
+__device__ void cl_sums(cooperative_groups::cluster_group &cl, int C, int rank, int n, double *wsum, double *lpart,
+                        double *louts, F f, double &s0, double &s1) {
+    const int nch = (n + 1023) >> 10;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = rank; c < nch; c += C) {
+        const int i = (c << 10) + (int)threadIdx.x;
+        double a = 0.0, b = 0.0;
+        if (i < n) f(i, a, b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+            b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+        }
+        if (lane == 0) { wsum[wid] = a; wsum[32 + wid] = b; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double x = 0.0, y = 0.0;
+            for (int w = 0; w < 32; ++w) { x += wsum[w]; y += wsum[32 + w]; }
+            lpart[2 * c] = x;
+            lpart[2 * c + 1] = y;
+        }
+        __syncthreads();
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int c = 0; c < nch; ++c) { x += lpart[2 * c]; y += lpart[2 * c + 1]; }
+        louts[0] = x;
+        louts[1] = y;
+    }
+    cl.sync();
+    s0 = louts[0];
+    s1 = louts[1];
+}
+
 // Whole solve for a mesh whose every level fits: FP64 residual and correction, FP32 V-cycles
-// in shared memory, convergence test on the device.  One block per item, so a batch of
-// instances solves in one launch.  stats: [cycles, rel. residual, max rel. since reset].
+// in shared memory, convergence test on the device.  One cluster of C CTAs per item (C = 1
+// for a batch of instances, one launch for all; up to 8 for an instance alone): the leader
+// CTA holds the levels and runs the V-cycles, and the FP64 work (warm start, residual,
+// correction, norms) is split by chunks of 1024 cells over the cluster, each CTA writing its
+// chunks' FP32 residual straight into the leader's shared memory.  GB300's FP64 rate per SM
+// is low, so spreading it over the cluster's SMs is what bounds the solve.  The result does
+// not depend on C.  stats: [cycles, rel. residual, max rel. since reset].
 struct SmallSolve {
     SmallDesc D;
     const double *diag64, *val64;
@@ -639,58 +689,63 @@ struct SmallSolve {
 };
 
 __global__ void __launch_bounds__(1024, 1) k_small_solve(const SmallSolve *__restrict__ items) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     extern __shared__ float sm[];
-    __shared__ double red[33];
     __shared__ float redf[33];
     __shared__ SmallDesc D;
-    const SmallSolve &it = items[blockIdx.x];
+    __shared__ double wsum[64], part[2 * kSmallChunks], outs[2];
+    const SmallSolve &it = items[blockIdx.x / C];
     if (threadIdx.x == 0) D = it.D;
     __syncthreads();
+    float *lsm = cl.map_shared_rank(sm, 0);  // the leader's levels
+    double *lpart = cl.map_shared_rank(part, 0), *louts = cl.map_shared_rank(outs, 0);
     const double *__restrict__ diag64 = it.diag64;
     const double *__restrict__ val64 = it.val64;
-    double *__restrict__ phi = it.phi;
-    double *__restrict__ bvec = it.bvec;
+    double *phi = it.phi;
+    double *bvec = it.bvec;
     const uint8_t *__restrict__ lev = it.lev;
     const int lmax = it.lmax, singular = it.singular, maxc = it.maxc;
     const double tol = it.tol;
-    double *stats = it.stats;
+    const SmallLevel &L = D.lv[0];
+    const int n = L.n, nch = (n + 1023) >> 10;
+#define CL_FOR(i)                                                                    \
+    for (int c_ = rank; c_ < nch; c_ += C)                                           \
+        for (int i = (c_ << 10) + (int)threadIdx.x; i < n && i < ((c_ + 1) << 10); i += 1 << 30)
     {
         const int ns = *it.n_solves;
         if (ns >= 1)
-            for (int i = threadIdx.x; i < D.lv[0].n; i += blockDim.x) {
+            CL_FOR(i) {
                 const double p = phi[i];
                 if (ns >= 2) phi[i] = 2.0 * p - it.phi_prev[i];
                 it.phi_prev[i] = p;
             }
-        __syncthreads();
-        if (threadIdx.x == 0) *it.n_solves = ns + 1;
+        cl.sync();  // every CTA has read the counter and its chunks of phi
+        if (rank == 0 && threadIdx.x == 0) *it.n_solves = ns + 1;
     }
-    const SmallLevel &L = D.lv[0];
-    const int n = L.n;
     if (singular) {  // right-hand side compatibility: remove an area-proportional share
-        double sb = 0.0, sa = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double sb, sa;
+        cl_sums(cl, C, rank, n, wsum, lpart, louts, [&](int i, double &a, double &b) {
             const double s = (double)(1 << (lmax - lev[i]));
-            sb += bvec[i];
-            sa += s * s;
-        }
-        sb = sm_block_sum(sb, red);
-        sa = sm_block_sum(sa, red);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            a += bvec[i];
+            b += s * s;
+        }, sb, sa);
+        CL_FOR(i) {
             const double s = (double)(1 << (lmax - lev[i]));
             bvec[i] -= sb / sa * s * s;
         }
-        __syncthreads();
+        cl.sync();
     }
-    double bb = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) bb += bvec[i] * bvec[i];
-    bb = sm_block_sum(bb, red);
-    float *b0 = sm + L.off + n, *x0 = sm + L.off;
+    double bb, unused;
+    cl_sums(cl, C, rank, n, wsum, lpart, louts, [&](int i, double &a, double &) { a += bvec[i] * bvec[i]; }, bb,
+            unused);
+    float *b0 = lsm + L.off + n, *x0 = lsm + L.off;
     int cyc = 0;
     double rel = 0.0;
     for (;;) {
-        double rr = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double rr;
+        cl_sums(cl, C, rank, n, wsum, lpart, louts, [&](int i, double &a, double &) {
             double ax;
             if (L.uniform) {
                 double d;
@@ -706,33 +761,72 @@ __global__ void __launch_bounds__(1024, 1) k_small_solve(const SmallSolve *__res
             }
             const double ri = bvec[i] - ax;
             b0[i] = (float)ri;
-            rr += ri * ri;
-        }
-        rr = sm_block_sum(rr, red);
+            a += ri * ri;
+        }, rr, unused);
         rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         if (rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= maxc) break;
-        sm_vcycle(D, sm, singular != 0, redf);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) phi[i] += (double)x0[i];
-        __syncthreads();
+        if (rank == 0) sm_vcycle(D, sm, singular != 0, redf);
+        cl.sync();  // the correction is in the leader's x0
+        CL_FOR(i) phi[i] += (double)x0[i];
+        cl.sync();  // phi complete before the next residual (and x0 read before the next V-cycle)
         if (singular) {
-            double sv = 0.0, sa = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double sv, sa;
+            cl_sums(cl, C, rank, n, wsum, lpart, louts, [&](int i, double &a, double &b) {
                 const double s = (double)(1 << (lmax - lev[i]));
-                sv += s * s * phi[i];
-                sa += s * s;
-            }
-            sv = sm_block_sum(sv, red);
-            sa = sm_block_sum(sa, red);
-            for (int i = threadIdx.x; i < n; i += blockDim.x) phi[i] -= sv / sa;
-            __syncthreads();
+                a += s * s * phi[i];
+                b += s * s;
+            }, sv, sa);
+            CL_FOR(i) phi[i] -= sv / sa;
+            cl.sync();
         }
         ++cyc;
     }
-    if (threadIdx.x == 0) {
-        stats[0] = (double)cyc;
-        stats[1] = rel;
-        stats[2] = fmax(stats[2], rel);
+#undef CL_FOR
+    if (rank == 0 && threadIdx.x == 0) {
+        it.stats[0] = (double)cyc;
+        it.stats[1] = rel;
+        it.stats[2] = fmax(it.stats[2], rel);
     }
+}
+
+// One launch of the small solve: n_items clusters of C CTAs.
+void launch_small_solve(const void *items, int n_items, int C, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_items * C));
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GB_CUDA(cudaLaunchKernelEx(&cfg, k_small_solve, (const SmallSolve *)items));
+}
+
+// The cluster size for an instance solved alone: one CTA per 1024-cell chunk, at most 8,
+// reduced until the GPU can hold such a cluster.
+int small_cluster(int n, size_t smem) {
+    int C = std::min(8, std::max(1, (n + 1023) / 1024));
+    for (; C > 1; C >>= 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_small_solve, &cfg) == cudaSuccess && nc >= 1) break;
+        cudaGetLastError();
+    }
+    return C;
 }
 
 // Which suffix of the level list fits one block's shared memory.
@@ -945,6 +1039,7 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
         GB_CUDA(cudaStreamSynchronize(ctx->stream));
         in.small_item = d;
         in.small_smem = (size_t)it.D.smem_floats * 4;
+        in.small_cluster = small_cluster((int)L.n, in.small_smem);
     }
     ++ctx->mesh_epoch;
 }
@@ -968,7 +1063,7 @@ void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list, cons
         for (int w = 0; w < 4; ++w) list[k]->last_walls[w] = walls[k][w];
         list[k]->mg_on_device = true;
     }
-    k_small_solve<<<(unsigned)list.size(), 1024, ctx->batch_smem, ctx->stream>>>((const SmallSolve *)ctx->batch_items);
+    launch_small_solve(ctx->batch_items, (int)list.size(), 1, ctx->batch_smem, ctx->stream);
     count_launch(ctx);
     check_launch("poisson_solve_batch");
 }
@@ -981,7 +1076,7 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     const int64_t n = L.n;
     const bool singular = in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC;
     if (in.small_item) {
-        k_small_solve<<<1, 1024, (size_t)in.small_smem, s>>>((const SmallSolve *)in.small_item);
+        launch_small_solve(in.small_item, 1, in.small_cluster, (size_t)in.small_smem, s);
         count_launch(ctx);
         check_launch("poisson_solve");
         in.mg_on_device = true;
