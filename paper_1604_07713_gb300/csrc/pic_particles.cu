@@ -251,11 +251,11 @@ template <typename R> __device__ __forceinline__ void normals3(const U4 &r, R n[
 constexpr int kQueue = 64;
 
 template <typename R> struct Queue {
-    R a[kQueue], b[kQueue];  // leaver: X, Y (old leaf's finest-lattice units); stayer: new u, v
+    R a[kQueue], b[kQueue];  // new offsets in the old leaf (a leaver's lie outside [0, 1))
     R vx[kQueue], vy[kQueue], vz[kQueue], w[kQueue];
     uint32_t r[4][kQueue];  // collision candidates: the four purpose-0 Philox words
     uint32_t id[kQueue], key[kQueue], cand[kQueue];
-    int32_t L[kQueue], dst[kQueue], I[kQueue], J[kQueue];  // dst: a stayer's slot, -1 for a leaver
+    int32_t L[kQueue], dst[kQueue];  // dst: a stayer's slot, -1 for a leaver
 };
 
 // Deferred work of queue entry e; all 32 lanes call it (`valid`: the lane has an entry).
@@ -272,6 +272,25 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
         vx = q.vx[e]; vy = q.vy[e]; vz = q.vz[e]; w = q.w[e];
         id = q.id[e]; cand = q.cand[e];
         L = q.L[e]; dst = q.dst[e];
+    }
+    // a leaver: the finest-lattice cell of its new position, wrapped or absorbed at the walls
+    // (an absorbed particle neither collides nor enters a list)
+    R X = 0, Y = 0;
+    int32_t I = 0, J = 0;
+    bool alive = true;
+    if (valid && dst < 0) {
+        const int32_t s = 1 << (a.lmax - a.lev[L]);
+        X = q.a[e] * (R)s; Y = q.b[e] * (R)s;  // exact: s is a power of two
+        I = a.ix[L] + (int32_t)m_floor(X); J = a.iy[L] + (int32_t)m_floor(Y);
+        if (I < 0 || I >= a.NX) {
+            if (!a.px) alive = false;
+            else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) alive = false; }
+        }
+        if (J < 0 || J >= a.NY) {
+            if (!a.py) alive = false;
+            else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) alive = false; }
+        }
+        if (!alive) cand = 0;
     }
     R sv[3] = {0, 0, 0}, si[3] = {0, 0, 0};
     bool spawns = false;
@@ -344,7 +363,7 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
     }
     run_count = (Llast == run_leaf ? run_count : 0) + __popc(smask & same_last);
     run_leaf = Llast;
-    if (!valid) return;
+    if (!valid || !alive) return;
     int32_t nl;
     R u, v;
     if (dst >= 0) {  // staying: the record is in place except its velocity
@@ -352,8 +371,6 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
         nl = L;
         u = q.a[e]; v = q.b[e];
     } else {         // entering: locate, re-express the offsets in the new leaf, take a slot
-        const R X = q.a[e], Y = q.b[e];
-        const int32_t I = q.I[e], J = q.J[e];
         nl = __ldg(a.map + (int64_t)J * a.NX + I);
         const int32_t s2 = 1 << (a.lmax - a.lev[nl]);
         const R inv_s2 = (R)1 / (R)s2;
@@ -431,54 +448,59 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
         R E[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) E[k] = a.stencil[8 * (int64_t)L + k];
+        // the bilinear form in the leaf's corner field, E(u, v) = e0 + u e_u + v (e_v + u e_uv)
+        // per component (corners 00, 10, 01, 11 at E[0..1], E[2..3], E[4..5], E[6..7])
+        R Bx[4], By[4];
+        Bx[0] = E[0]; Bx[1] = E[2] - E[0]; Bx[2] = E[4] - E[0]; Bx[3] = (E[0] - E[2]) - (E[4] - E[6]);
+        By[0] = E[1]; By[1] = E[3] - E[1]; By[2] = E[5] - E[1]; By[3] = (E[1] - E[3]) - (E[5] - E[7]);
         int32_t stay_run = 0;
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
             const bool live = p < p1;
-            bool alive = false, stays = false, cand = false;
+            bool stays = false, cand = false;
             R u = nu, v = nv, vx = nvx, vy = nvy, vz = nvz, w = nwt;
             uint32_t id = nid;
             if (p + 32 < p1) fetch(p + 32);
             else if (c0 + 32 >= p1 && np0 + lane < np1) fetch(np0 + lane);
-            R X = 0, Y = 0;
             U4 r0{0u, 0u, 0u, 0u};
-            int32_t I = 0, J = 0;
             if (live) {
                 // gather: bilinear in the leaf's corner field
-                const R w00 = ((R)1 - u) * ((R)1 - v), w10 = u * ((R)1 - v), w01 = ((R)1 - u) * v, w11 = u * v;
-                const R ex = w00 * E[0] + w10 * E[2] + w01 * E[4] + w11 * E[6];
-                const R ey = w00 * E[1] + w10 * E[3] + w01 * E[5] + w11 * E[7];
+                const R ex = Bx[0] + u * Bx[1] + v * (Bx[2] + u * Bx[3]);
+                const R ey = By[0] + u * By[1] + v * (By[2] + u * By[3]);
                 // leapfrog kick and drift in leaf units
                 vx += a.qm_dt * ex;
                 vy += a.qm_dt * ey;
                 const R un = u + vx * dth, vn = v + vy * dth;
-                alive = true;
                 if (un >= (R)0 && un < (R)1 && vn >= (R)0 && vn < (R)1) {
                     stays = true;
                     u = un; v = vn;
                 } else {
-                    // the finest-lattice cell, wrapped or absorbed at the walls
-                    X = un * (R)s; Y = vn * (R)s;  // exact: s is a power of two
-                    I = lx + (int32_t)m_floor(X); J = ly + (int32_t)m_floor(Y);
-                    if (I < 0 || I >= a.NX) {
-                        if (!a.px) alive = false;
-                        else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) alive = false; }
-                    }
-                    if (J < 0 || J >= a.NY) {
-                        if (!a.py) alive = false;
-                        else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) alive = false; }
-                    }
-                    // a leaf as wide as a periodic domain can take its own particle back
-                    if (a.self_wrap && alive && I >= lx && I < lx + s && J >= ly && J < ly + s) {
-                        const R inv = (R)1 / (R)s;
-                        R un2 = ((R)(I - (int32_t)m_floor(X) - lx) + X) * inv;
-                        R vn2 = ((R)(J - (int32_t)m_floor(Y) - ly) + Y) * inv;
-                        u = un2 < (R)0 ? (R)0 : (un2 >= (R)1 ? below_one<R>() : un2);
-                        v = vn2 < (R)0 ? (R)0 : (vn2 >= (R)1 ? below_one<R>() : vn2);
-                        stays = true;
+                    // a leaver: its new cell, the walls and its list slot are deferred work
+                    u = un; v = vn;
+                    if (a.self_wrap) {
+                        // a leaf as wide as a periodic domain can take its own particle back
+                        const R X = un * (R)s, Y = vn * (R)s;  // exact: s is a power of two
+                        int32_t I = lx + (int32_t)m_floor(X), J = ly + (int32_t)m_floor(Y);
+                        bool in = true;
+                        if (I < 0 || I >= a.NX) {
+                            if (!a.px) in = false;
+                            else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) in = false; }
+                        }
+                        if (J < 0 || J >= a.NY) {
+                            if (!a.py) in = false;
+                            else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) in = false; }
+                        }
+                        if (in && I >= lx && I < lx + s && J >= ly && J < ly + s) {
+                            const R inv = (R)1 / (R)s;
+                            R un2 = ((R)(I - (int32_t)m_floor(X) - lx) + X) * inv;
+                            R vn2 = ((R)(J - (int32_t)m_floor(Y) - ly) + Y) * inv;
+                            u = un2 < (R)0 ? (R)0 : (un2 >= (R)1 ? below_one<R>() : un2);
+                            v = vn2 < (R)0 ? (R)0 : (vn2 >= (R)1 ? below_one<R>() : vn2);
+                            stays = true;
+                        }
                     }
                 }
-                if (alive && a.mcc) {
+                if (a.mcc) {
                     const R v2 = vx * vx + vy * vy + vz * vz;
                     r0 = philox4x32_10(id, a.inst_word, step, 0u, a.keys);
                     const R U0 = u24<R>(r0.x);
@@ -500,11 +522,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
                     }
                 }
             }
-            const uint32_t stay_mask = __ballot_sync(0xFFFFFFFFu, live && alive && stays);
-            const bool defer = live && alive && (!stays || cand);
+            const uint32_t stay_mask = __ballot_sync(0xFFFFFFFFu, live && stays);
+            const bool defer = live && (!stays || cand);
             const uint32_t defer_mask = __ballot_sync(0xFFFFFFFFu, defer);
             int32_t dst = -1;
-            if (live && alive && stays) {
+            if (live && stays) {
                 dst = p0 + stay_run + __popc(stay_mask & lanemask_lt());
                 kahan_add(ws_sum, ws_c, w);
                 a.d.u[dst] = u; a.d.v[dst] = v;
@@ -514,7 +536,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
             if (defer_mask) {
                 if (defer) {
                     const int e = (qhead + qn + __popc(defer_mask & lanemask_lt())) & (kQueue - 1);
-                    q.a[e] = stays ? u : X; q.b[e] = stays ? v : Y;
+                    q.a[e] = u; q.b[e] = v;
                     q.vx[e] = vx; q.vy[e] = vy; q.vz[e] = vz; q.w[e] = w;
                     q.cand[e] = cand ? 1u : 0u;
                     if (cand) {
@@ -522,7 +544,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
                         if (a.species == 0) q.r[1][e] = r0.y;
                     }
                     q.id[e] = id; q.key[e] = key0 + (uint32_t)p;
-                    q.L[e] = L; q.dst[e] = dst; q.I[e] = I; q.J[e] = J;
+                    q.L[e] = L; q.dst[e] = dst;
                 }
                 qn += __popc(defer_mask);
                 if (qn >= 32) {
