@@ -163,6 +163,50 @@ __global__ void k_rbgs_half(int64_t n, const int32_t *__restrict__ col, const fl
     xout[i] = dinv[i] * (b[i] - off);
 }
 
+// The first two half sweeps of a pre-smoothing from x = 0 in one kernel: the first (colour 0
+// from zero) leaves t = D^-1 (b - 0) on colour 0 and 0 elsewhere, which the second (colour 1)
+// forms on the fly; the same arithmetic as the two half sweeps, so the same values.
+__global__ void k_rbgs_first(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
+                             const float *__restrict__ dinv, const uint8_t *__restrict__ color,
+                             const float *__restrict__ b, float *__restrict__ xout) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (color[i] != 1) {
+        xout[i] = dinv[i] * (b[i] - 0.0f);
+        return;
+    }
+    float off = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kEll; ++j) {
+        const int32_t cc = col[(int64_t)j * n + i];
+        if (cc >= 0) off = fmaf(val[(int64_t)j * n + i], color[cc] == 0 ? dinv[cc] * (b[cc] - 0.0f) : 0.0f, off);
+    }
+    xout[i] = dinv[i] * (b[i] - off);
+}
+
+// Injection of the coarse correction (x += xc[parent]) fused into the first half sweep after
+// it: every value the sweep reads gets its correction added on the way, with the same
+// additions as a separate injection pass.
+__global__ void k_rbgs_half_prolong(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
+                                    const float *__restrict__ dinv, const uint8_t *__restrict__ color, int c,
+                                    const float *__restrict__ b, const float *__restrict__ xin,
+                                    const int32_t *__restrict__ parent, const float *__restrict__ xc,
+                                    float *__restrict__ xout) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (color[i] != c) {
+        xout[i] = xin[i] + xc[parent[i]];
+        return;
+    }
+    float off = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kEll; ++j) {
+        const int32_t cc = col[(int64_t)j * n + i];
+        if (cc >= 0) off = fmaf(val[(int64_t)j * n + i], xin[cc] + xc[parent[cc]], off);
+    }
+    xout[i] = dinv[i] * (b[i] - off);
+}
+
 // Coarse right-hand side: summed residuals of the children; zero coarse iterate.
 __global__ void k_restrict_residual(int64_t nc, const int32_t *__restrict__ child4, int64_t nf,
                                     const int32_t *__restrict__ col, const float *__restrict__ val,
@@ -187,11 +231,6 @@ __global__ void k_restrict_residual(int64_t nc, const int32_t *__restrict__ chil
     xc[p] = 0.0f;
 }
 
-__global__ void k_prolong(int64_t nf, const int32_t *__restrict__ parent, const float *__restrict__ xc,
-                          float *__restrict__ xf) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nf) xf[i] += xc[parent[i]];
-}
 
 // One-block Jacobi-preconditioned CG on the coarsest level (symmetric: one uniform level).
 __global__ void __launch_bounds__(1024) k_coarse_cg(int64_t n, const int32_t *__restrict__ col,
@@ -415,22 +454,6 @@ __device__ void sm_smooth(const SmallDesc &D, const SmallLevel &L, float *x, con
     }
 }
 
-__device__ double sm_block_sum(double v, double *red) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        red[32] = s;
-    }
-    __syncthreads();
-    const double out = red[32];
-    __syncthreads();
-    return out;
-}
 
 
 __device__ __forceinline__ float warp_sumf(float v) {
@@ -895,22 +918,27 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     }
     Level &C = in.lv[g + 1];
     const unsigned nb = blocks_for(L.n);
-    // pre-smoothing (x starts at zero)
-    for (int k = 0; k < kNu; ++k)
-        for (int c = 0; c < 2; ++c) {
-            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, k == 0 && c == 0);
-            std::swap(L.x, L.t);
-        }
-    k_restrict_residual<<<blocks_for(C.n), kT, 0, s>>>(C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
-    count_launch(ctx, 2 * kNu + 1);
-    vcycle(ctx, in, g + 1, singular);
-    k_prolong<<<nb, kT, 0, s>>>(L.n, L.parent, C.x, L.x);
-    for (int k = 0; k < kNu; ++k)
+    // pre-smoothing (x starts at zero): the first sweep's two half sweeps in one kernel
+    k_rbgs_first<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, L.b, L.x);
+    for (int k = 1; k < kNu; ++k)
         for (int c = 0; c < 2; ++c) {
             k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
             std::swap(L.x, L.t);
         }
-    count_launch(ctx, 2 * kNu + 1);
+    k_restrict_residual<<<blocks_for(C.n), kT, 0, s>>>(C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
+    count_launch(ctx, 2 * kNu);
+    vcycle(ctx, in, g + 1, singular);
+    // post-smoothing, the injection of the correction fused into its first half sweep
+    k_rbgs_half_prolong<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, 0, L.b, L.x, L.parent, C.x, L.t);
+    std::swap(L.x, L.t);
+    k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, 1, L.b, L.x, L.t, 0);
+    std::swap(L.x, L.t);
+    for (int k = 1; k < kNu; ++k)
+        for (int c = 0; c < 2; ++c) {
+            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
+            std::swap(L.x, L.t);
+        }
+    count_launch(ctx, 2 * kNu);
 }
 }  // namespace
 
