@@ -244,17 +244,22 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
+# The push kernel's translation unit: the sources that decide its code and so its DRAM
+# traffic (the kernel file, the internal header it includes and the ABI header).
+PUSH_SOURCES = ("paper_1604_07713_gb300/csrc/pic_particles.cu", "paper_1604_07713_gb300/csrc/pic_internal.cuh",
+                "include/gbpic.h")
+
+
 def _csrc_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1604_07713_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in PUSH_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()
 
 
 def _traffic_record(name):
     """DRAM bytes per launch of the move kernel from the committed ncu summary, if that was
-    taken on the current kernel sources and this workload (else None)."""
+    taken on the push kernel's current sources (PUSH_SOURCES) and this workload (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None

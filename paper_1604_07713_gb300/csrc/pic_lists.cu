@@ -7,9 +7,10 @@
 // Entering records that find no free slot left go to the overflow store, and their leaf
 // moves to a fresh segment at the tail of the buffer (past every segment in use) with room
 // for them.  Only when the tail is used up are all lists of the species laid out again, in
-// leaf order with fresh free slots.  Both repairs run as kernels queued every step that do
-// nothing unless the device saw an overflow; the order of records inside a list never
-// depends on where its segment lies (order keys are list ranks, not slot numbers).
+// leaf order with fresh free slots.  Both repairs sit behind IF nodes of a CUDA graph whose
+// conditions a one-thread kernel sets from the device's overflow flags, so a step without
+// overflow costs two tiny kernels and the host never waits; the order of records inside a
+// list never depends on where its segment lies (order keys are list ranks, not slot numbers).
 //
 // This file holds the allocation of a species' buffers, the construction of segments from
 // per-leaf counts, list ranks and record totals, and the two repairs.

@@ -3,9 +3,12 @@
 // phi += e are FP64 (iterative refinement); each correction e comes from one FP32
 // geometric-multigrid V-cycle over the tree-clamped and root-coarsened levels, with two
 // red-black Gauss-Seidel sweeps before and after the coarse correction, summed restriction
-// and piecewise-constant prolongation; the coarsest level is solved by conjugate gradients.
-// Levels of at most 8192 cells live in one block's shared memory; when every level does, the
-// whole solve (FP64 residual, V-cycles, convergence test) is a single launch.
+// and piecewise-constant prolongation; the coarsest level (at most 64 cells) is solved by its
+// dense inverse, built on the host in FP64, or else by conjugate gradients.  Levels of at
+// most 8192 cells live in one block's shared memory; when every level does, the whole solve
+// (FP64 residual, V-cycles, convergence test) is a single launch of a thread-block cluster
+// that spreads the FP64 work over its SMs (one CTA per instance in a batch).  Larger meshes
+// run one CUDA graph per solve whose WHILE node repeats the cycle until the device decides.
 #include <algorithm>
 #include <cmath>
 
