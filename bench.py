@@ -269,6 +269,20 @@ def _traffic_record(name):
     return rec
 
 
+def _aggregate(t_local, particle_steps_local, ws, device):
+    """The whole job over ranks: the slowest rank's timed seconds and the particle-steps of
+    all ranks (FP64 all-reduces on `device`; one rank: the local values)."""
+    if ws <= 1:
+        return float(t_local), float(particle_steps_local)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ps = torch.tensor([float(particle_steps_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(ps)
+    return float(tt.item()), float(ps.item())
+
+
 def run_gpu(args):
     import torch
     import paper_1604_07713_gb300 as G
@@ -369,16 +383,7 @@ def run_gpu(args):
     G.pic_set_timing(ctx.ctx, False)
     launches = G.pic_get_launch_count(ctx.ctx) - launches0
     clocks = sampler.stop()
-    t_max = t_total
-    if ws > 1:
-        tt = torch.tensor([t_total], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ps = torch.tensor([float(particle_steps)], device="cuda")
-        torch.distributed.all_reduce(ps)
-        particle_steps_all = float(ps.item())
-    else:
-        particle_steps_all = float(particle_steps)
+    t_max, particle_steps_all = _aggregate(t_total, particle_steps, ws, "cuda")
     value = particle_steps_all / t_max
     final = counts_all()
 
