@@ -169,3 +169,57 @@ def test_balance_closure_refines_neighbours_of_deep_refinement():
     sim.adapt(particles=False)
     assert sim.mesh.level.max() == M.level.max() + 1
     assert _corner_balanced(sim.mesh)
+
+
+def test_field_criterion_alone_refines_and_blocks_coarsening_hand_case():
+    """No particles, so the count criterion never fires; the potential depends on x only and
+    its face gradients are written out by hand.  8 x 4 roots of side 1, Dirichlet in x
+    (phi = 0 and 14 on the walls), Neumann in y; cell-centred phi per column
+    0.5, 1.5, 2.5, 3.5, 7.5, 11.5, 12.5, 13.5: face gradients 1 (wall), 1, 1, 1, 4, 4, 1, 1,
+    1 (wall), so the centre |E| of the columns is 1, 1, 1, 2.5, 4, 2.5, 1, 1.  With
+    e_ref = 2 and refine_field = 0.75 (threshold 1.5) exactly the 12 leaves of columns 3-5
+    refine.  Second case: every root refined once, fine-column gradients 1 except 1.3 on the
+    two faces of fine column 8, so only that column's |E| (1.3) reaches coarsen_field
+    e_ref = 1.2: its four quartets stay fine and the other 28 coarsen.  Fails for: the
+    threshold taken without e_ref, the coarsening test against refine_field, or the field
+    criterion read from the corner field instead of the centre."""
+    cfg = W.base_config(precision=W.FP64, n_species=1, q=[-1.0], m=[1.0], bc_x=W.BC_DIRICHLET,
+                        bc_y=W.BC_NEUMANN, max_level=1, refine_count=128, coarsen_count=32,
+                        e_ref=2.0, refine_field=0.75, coarsen_field=0.6)
+    M = O.Mesh(8, 4, 1.0, 1, O.BC_DIRICHLET, O.BC_NEUMANN)
+    sim = O.Sim(cfg, M)
+    col = M.ix >> 1
+    phi_col = np.array([0.5, 1.5, 2.5, 3.5, 7.5, 11.5, 12.5, 13.5])
+    sim.phi = phi_col[col]
+    sim.last_walls = np.array([0.0, 14.0, 0.0, 0.0])
+    emag = M.cell_emag(sim.phi, sim.last_walls)
+    assert np.abs(emag - np.array([1, 1, 1, 2.5, 4, 2.5, 1, 1])[col]).max() < 1e-14
+    st = sim.adapt(particles=False)["mesh"]
+    M2 = sim.mesh
+    assert st["refined"] == 12 and st["coarsened"] == 0 and M2.nleaf == 32 - 12 + 48
+    fine_roots = np.unique(M2.root[M2.level == 1])
+    assert sorted((fine_roots % 8).tolist()) == [3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 5]
+
+    # every root refined once: 16 x 8 fine leaves of side 1/2
+    r, l, m = W.region_tree(8, 4, 1, lambda lv, xc, yc, h: True)
+    M = O.Mesh(8, 4, 1.0, 1, O.BC_DIRICHLET, O.BC_NEUMANN, r, l, m)
+    cfg["e_ref"] = 1.0
+    cfg["coarsen_field"] = 1.2
+    sim = O.Sim(cfg, M)
+    fcol = M.ix                                   # fine column 0..15
+    g = np.ones(17)                               # gradients of faces 0..16 (0, 16: walls)
+    g[8] = g[9] = 1.3                             # the two faces of fine column 8
+    # phi at fine-column centres from the face gradients (h = 1/2; the wall face is h/4 away)
+    phi_f = np.empty(16)
+    phi_f[0] = g[0] * 0.25
+    for j in range(1, 16):
+        phi_f[j] = phi_f[j - 1] + g[j] * 0.5
+    sim.phi = phi_f[fcol]
+    sim.last_walls = np.array([0.0, phi_f[15] + g[16] * 0.25, 0.0, 0.0])
+    emag = M.cell_emag(sim.phi, sim.last_walls)
+    expect = np.where(fcol == 8, 1.3, np.where((fcol == 7) | (fcol == 9), 1.15, 1.0))
+    assert np.abs(emag - expect).max() < 1e-12
+    st = sim.adapt(particles=False)["mesh"]
+    M2 = sim.mesh
+    assert st["refined"] == 0 and st["coarsened"] == 28 and M2.nleaf == 28 + 16
+    assert np.all((M2.root[M2.level == 1] % 8) == 4)

@@ -277,7 +277,7 @@ def test_mcc_collision_count_is_binomial_and_branching_matches_cross_sections():
     assert abs(collided - mean) < 5 * sd, (collided, mean, sd)
     frac = siz / (sig_el + siz)
     assert abs(n_iz - collided * frac) < 5 * np.sqrt(collided * frac * (1 - frac))
-    # ionization conserves energy: e1 + e2 = eps - eps_th for every pair
+    # every ionization adds one electron (its energy split is pinned below)
     assert sim.species[0].n == n + n_iz
 
 
@@ -336,3 +336,284 @@ def test_cold_plasma_oscillates_at_plasma_frequency():
     per = int(round(np.pi / 0.05))
     assert abs(tot[-per:].mean() - tot[:per].mean()) < 0.01 * We.max()
     assert (tot.max() - tot.min()) < 0.1 * We.max()
+
+
+# --------------------------------------------------------------------------------------
+# Ion collisions (§3 MCC of ions with neutrals): a Maxwellian neutral partner, isotropic
+# scattering in the centre-of-mass frame
+# --------------------------------------------------------------------------------------
+def _ion_sim(n, speed, ng, dt, t_gas, m_ion, m_neutral, sig=6e-20, seed=0):
+    mesh = O.Mesh(4, 4, 0.25, 0, O.BC_PERIODIC, O.BC_PERIODIC)
+    cfg = W.base_config(precision=W.FP64, n_species=2, dt=dt, eps0=1.0, q=[-W.QE, W.QE],
+                        m=[W.ME, m_ion], qe=W.QE, mcc=1, gas_density=ng, gas_temperature_ev=t_gas,
+                        neutral_mass=m_neutral, sigma_el=sig, sigma_iz0=0.0, eps_th_ev=24.6)
+    sim = O.Sim(cfg, mesh)
+    rng = np.random.default_rng(seed)
+    x = rng.random(n); y = rng.random(n)
+    d = rng.standard_normal((3, n)); d /= np.linalg.norm(d, axis=0)
+    sim.load(0, x[:0], y[:0], x[:0], x[:0], x[:0], x[:0])
+    sim.load(1, x, y, speed * d[0], speed * d[1], speed * d[2], np.zeros(n))
+    return sim
+
+
+def _mean_collision_probability(k, a, vt):
+    """E[1 - exp(-k g)] with g = |v - v_n|, |v| = a vt and v_n ~ Maxwellian of thermal speed
+    vt (vt^2 per component): by symmetry g = vt sqrt(t + (a + z)^2), z ~ N(0, 1) along v and
+    t ~ chi^2 with 2 degrees of freedom across it; Gauss-Hermite x Gauss-Laguerre quadrature."""
+    zh, wh = np.polynomial.hermite_e.hermegauss(80)
+    tl, wl = np.polynomial.laguerre.laggauss(80)      # int_0^inf f(s) e^{-s} ds, t = 2 s
+    wh = wh / np.sqrt(2 * np.pi)
+    g = vt * np.sqrt(2 * tl[None, :] + (a + zh[:, None]) ** 2)
+    return float(np.sum(wh[:, None] * wl[None, :] * (1 - np.exp(-k * g))))
+
+
+def test_ion_collision_count_matches_the_mean_over_the_maxwellian_partner():
+    """The ion's collision probability is taken with the relative speed to a partner drawn from
+    the neutral Maxwellian (thermal speed sqrt(T/M)).  The count of ions whose velocity changed
+    must be binomial around N E[1 - exp(-n sigma g dt)], the expectation worked out here by
+    quadrature over the Maxwellian.  Fails for: P from the ion speed alone (no partner), the
+    partner drawn with the ion mass instead of the neutral mass, or a partner at rest."""
+    n = 200_000
+    m_ion, m_n = 4 * W.AMU, 40 * W.AMU
+    t_gas = 0.5
+    vt = np.sqrt(t_gas * W.QE / m_n)
+    a = 1.5
+    ng, sig = 1e22, 6e-20
+    dt = 0.1 / (ng * sig * vt)                 # k vt = 0.1
+    sim = _ion_sim(n, a * vt, ng, dt, t_gas, m_ion, m_n, sig)
+    v0 = {int(i): (vx, vy, vz) for i, vx, vy, vz in zip(sim.species[1].id, sim.species[1].vx,
+                                                        sim.species[1].vy, sim.species[1].vz)}
+    sim.step()
+    sp = sim.species[1]
+    before = np.array([v0[int(i)] for i in sp.id])
+    collided = np.count_nonzero(np.any(np.stack([sp.vx, sp.vy, sp.vz], 1) != before, axis=1))
+    p = _mean_collision_probability(ng * sig * dt, a, vt)
+    mean, sd = n * p, np.sqrt(n * p * (1 - p))
+    assert abs(collided - mean) < 5 * sd, (collided, mean, sd)
+    # the same count with the ion speed alone would be n (1 - exp(-k a vt)): far outside
+    p_wrong = 1 - np.exp(-ng * sig * dt * a * vt)
+    assert abs(n * p_wrong - mean) > 20 * sd
+
+
+@pytest.mark.parametrize("m_ratio", [1.0, 10.0])
+def test_ion_scatter_conserves_momentum_and_energy_of_the_pair(m_ratio):
+    """Cold gas (partner at rest): after an elastic centre-of-mass scatter the neutral carries
+    momentum m (v - v') and energy |m (v - v')|^2 / 2M, so every collided ion must satisfy
+    m |v|^2 = m |v'|^2 + (m^2 / M) |v - v'|^2 to rounding.  Its mean retained energy fraction
+    is (m^2 + M^2) / (m + M)^2 for isotropic centre-of-mass scattering.  Fails for: an
+    isotropic scatter in the lab frame, the reduced-mass factor M/(m+M) swapped for m/(m+M),
+    or the centre-of-mass velocity weighted by the wrong masses."""
+    n = 100_000
+    m_ion = 4 * W.AMU
+    m_n = m_ratio * m_ion
+    speed = 2.0e4
+    ng, sig = 1e22, 6e-20
+    dt = 0.5 / (ng * sig * speed)
+    sim = _ion_sim(n, speed, ng, dt, 0.0, m_ion, m_n, sig)
+    v0 = {int(i): (vx, vy, vz) for i, vx, vy, vz in zip(sim.species[1].id, sim.species[1].vx,
+                                                        sim.species[1].vy, sim.species[1].vz)}
+    sim.step()
+    sp = sim.species[1]
+    v = np.array([v0[int(i)] for i in sp.id])
+    vp = np.stack([sp.vx, sp.vy, sp.vz], 1)
+    hit = np.any(vp != v, axis=1)
+    assert abs(hit.mean() - (1 - np.exp(-0.5))) < 5 * np.sqrt(0.4 * 0.6 / n)
+    e_in = np.sum(v[hit] ** 2, 1)
+    e_out = np.sum(vp[hit] ** 2, 1)
+    recoil = (m_ion / m_n) * np.sum((v[hit] - vp[hit]) ** 2, 1)
+    assert np.abs(e_in - e_out - recoil).max() <= 1e-12 * speed ** 2
+    frac = e_out / e_in
+    expect = (m_ion ** 2 + m_n ** 2) / (m_ion + m_n) ** 2
+    assert abs(frac.mean() - expect) < 5 * frac.std() / np.sqrt(frac.size)
+
+
+def _old_energy(sp, m):
+    return 0.5 * m * (sp.vx ** 2 + sp.vy ** 2 + sp.vz ** 2) / W.QE
+
+
+def test_ionization_pays_the_threshold_and_spawns_a_neutral_temperature_ion():
+    """Every ionizing electron pays eps_th; the rest is shared between the parent and the new
+    electron, so e_parent + e_new = eps - eps_th for every pair, with the parent's share
+    uniform on [0, 1).  The pair is spawned at the parent's position with ids next_id + 2k
+    (electron) and + 1 (ion), k the parent's rank in list order; the ion takes a velocity from
+    the neutral Maxwellian: zero mean, variance T_gas qe / M_neutral per component.  Fails
+    for: the energy split taken before paying the threshold, both shares drawn independently,
+    pairs ranked in another order, or the ion's thermal speed from the ion or electron mass."""
+    from scipy import stats
+    n = 400_000
+    eps = 60.0
+    speed = np.sqrt(2 * eps * W.QE / W.ME)
+    sig_el, sig0, th = 6e-20, 1e-20, 24.6
+    ng, dt = 2e23, 2e-12
+    t_gas, m_n = 0.3, 40 * W.AMU
+    mesh = O.Mesh(4, 4, 0.25, 0, O.BC_PERIODIC, O.BC_PERIODIC)
+    cfg = W.base_config(precision=W.FP64, n_species=2, dt=dt, eps0=1.0, q=[-W.QE, W.QE],
+                        m=[W.ME, 4 * W.AMU], qe=W.QE, mcc=1, gas_density=ng, gas_temperature_ev=t_gas,
+                        neutral_mass=m_n, sigma_el=sig_el, sigma_iz0=sig0, eps_th_ev=th)
+    sim = O.Sim(cfg, mesh)
+    rng = np.random.default_rng(2)
+    x = rng.random(n); y = rng.random(n)
+    d = rng.standard_normal((3, n)); d /= np.linalg.norm(d, axis=0)
+    sim.load(0, x, y, speed * d[0], speed * d[1], speed * d[2], np.zeros(n))
+    sim.load(1, x[:0], y[:0], x[:0], x[:0], x[:0], x[:0])
+    old_ids = sim.species[0].id.copy()
+    sim.step()
+    e, ion = sim.species[0], sim.species[1]
+    by_id = {int(i): k for k, i in enumerate(e.id)}
+    ion_by_id = {int(i): k for k, i in enumerate(ion.id)}
+    en = _old_energy(e, W.ME)
+    rest = eps - th
+    # parents: original electrons left with at most eps - eps_th (elastic ones keep ~eps)
+    parents = [int(i) for i in old_ids if en[by_id[int(i)]] <= rest * (1 + 1e-12)]
+    k = len(parents)
+    assert k == ion.n and e.n == n + k and k > 2000
+    e1 = np.array([en[by_id[p]] for p in parents])
+    e2 = np.array([en[by_id[n + 2 * r]] for r in range(k)])
+    assert np.abs(e1 + e2 - rest).max() <= 1e-12 * rest
+    assert stats.kstest(e1 / rest, "uniform").pvalue > 1e-4
+    for r, p in enumerate(parents):
+        a, b, c = by_id[p], by_id[n + 2 * r], ion_by_id[n + 2 * r + 1]
+        assert e.x[a] == e.x[b] == ion.x[c] and e.y[a] == e.y[b] == ion.y[c]
+    vi = np.stack([ion.vx, ion.vy, ion.vz])
+    var = t_gas * W.QE / m_n
+    assert np.abs(vi.mean(axis=1)).max() < 5 * np.sqrt(var / k)
+    s2 = (vi ** 2).mean()
+    assert abs(s2 / var - 1) < 5 * np.sqrt(2.0 / (3 * k))
+    # the new electrons' directions are isotropic
+    be = np.array([by_id[n + 2 * r] for r in range(k)])
+    dz = e.vz[be] / np.sqrt(2 * e2 * W.QE / W.ME)
+    assert abs((dz ** 2).mean() - 1 / 3) < 5 * np.sqrt(4 / 45 / k)
+
+
+# --------------------------------------------------------------------------------------
+# Corner and centre fields (§3: E on cell nodes/corners; the adaptation's |E| criterion)
+# --------------------------------------------------------------------------------------
+def _disk_mesh(n, lmax, bcx, bcy):
+    r, l, m = _disk_tree(n, lmax)
+    return O.Mesh(n, n, 1.0 / n, lmax, bcx, bcy, r, l, m)
+
+
+def test_cell_emag_exact_for_linear_potentials_on_amr():
+    """|E| at leaf centres from the face gradients is exact for a linear potential on a
+    four-level tree, at coarse-fine faces and at the walls (Dirichlet along the gradient,
+    Neumann across it).  Fails for: a coarse-fine gradient taken over h instead of 3h/4, a
+    wall gradient over h instead of h/2, or a dropped factor of one half in the averages."""
+    n = 8
+    a, b = 2.5, -1.75
+    M = _disk_mesh(n, 3, O.BC_DIRICHLET, O.BC_NEUMANN)
+    assert len(np.unique(M.s)) == 4
+    xc, yc = M.centres()
+    em = M.cell_emag(a * xc, [0.0, a * M.lx, 0.0, 0.0])
+    assert np.abs(em - abs(a)).max() < 1e-12
+    M = _disk_mesh(n, 3, O.BC_NEUMANN, O.BC_DIRICHLET)
+    xc, yc = M.centres()
+    em = M.cell_emag(b * yc, [0.0, 0.0, 0.0, b * M.ly])
+    assert np.abs(em - abs(b)).max() < 1e-12
+    # both components: leaves away from the walls
+    M = _disk_mesh(n, 3, O.BC_DIRICHLET, O.BC_DIRICHLET)
+    xc, yc = M.centres()
+    em = M.cell_emag(a * xc + b * yc, [0.0, 0.0, 0.0, 0.0])
+    inner = (M.ix > 0) & (M.iy > 0) & (M.ix + M.s < (n << 3)) & (M.iy + M.s < (n << 3))
+    assert inner.sum() > 100
+    assert np.abs(em[inner] - np.hypot(a, b)).max() < 1e-12
+
+
+def test_node_e_on_a_uniform_mesh_is_the_compact_four_cell_formula():
+    """On a uniform periodic mesh the corner field of any potential is the compact formula
+    E_x = -[(phi_{i+1,j} - phi_{i,j}) + (phi_{i+1,j+1} - phi_{i,j+1})] / 2h (E_y likewise) of
+    the four cells around the node, and it is exact at every node for a quadratic potential.
+    Fails for: a face gradient taken on the wrong side of the node, one of the two incident
+    faces dropped, or a corner index transposed."""
+    n = 16
+    h = 1.0 / n
+    M = O.Mesh(n, n, h, 0, O.BC_PERIODIC, O.BC_PERIODIC)
+    rng = np.random.default_rng(8)
+    phi = rng.standard_normal(M.nleaf)
+    E = M.node_e(phi, [0, 0, 0, 0])
+    g = np.zeros((n, n)); g[M.iy, M.ix] = phi        # g[j, i]
+    # node (I, J) at the lower-left corner of cell (I, J): cells I-1, I and J-1, J around it
+    gl, gd, gld = np.roll(g, 1, axis=1), np.roll(g, 1, axis=0), np.roll(np.roll(g, 1, axis=0), 1, axis=1)
+    ex = -((g - gl) + (gd - gld)) / (2 * h)
+    ey = -((g - gd) + (gl - gld)) / (2 * h)
+    for c, (di, dj) in enumerate(((0, 0), (1, 0), (0, 1), (1, 1))):
+        I = (M.ix + di) % n; J = (M.iy + dj) % n
+        assert np.abs(E[:, c, 0] - ex[J, I]).max() < 1e-12 * n
+        assert np.abs(E[:, c, 1] - ey[J, I]).max() < 1e-12 * n
+    # quadratic potential on a Dirichlet box: exact at interior nodes
+    M = O.Mesh(n, n, h, 0, O.BC_DIRICHLET, O.BC_DIRICHLET)
+    xc, yc = M.centres()
+    phi = 0.7 * xc ** 2 - 1.3 * xc * yc + 0.4 * yc ** 2 + 0.2 * xc
+    E = M.node_e(phi, [0, 0, 0, 0])
+    for c, (di, dj) in enumerate(((0, 0), (1, 0), (0, 1), (1, 1))):
+        X = (M.ix + di) * h; Y = (M.iy + dj) * h
+        inner = (X > 0) & (X < 1) & (Y > 0) & (Y < 1)
+        ex = -(1.4 * X - 1.3 * Y + 0.2); ey = -(-1.3 * X + 0.8 * Y)
+        assert np.abs(E[inner, c, 0] - ex[inner]).max() < 1e-12
+        assert np.abs(E[inner, c, 1] - ey[inner]).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed,px,py", [(4, True, True), (5, False, True)])
+def test_node_e_is_continuous_across_hanging_nodes(seed, px, py):
+    """On a 2:1 tree, a corner of a fine leaf that lies inside the edge of a coarser leaf must
+    carry the value of the coarse leaf's bilinear field there (the mean of that edge's two
+    corner values), for any potential, so that the gathered field is continuous.  Fails for:
+    a hanging node treated as a regular node, or the mean taken over the ends of another edge."""
+    nx0, ny0, lmax = 4, 3, 3
+    r, l, m = W.random_tree(nx0, ny0, lmax, 0.35, seed, px, py)
+    M = O.Mesh(nx0, ny0, 0.25, lmax, O.BC_PERIODIC if px else O.BC_DIRICHLET,
+               O.BC_PERIODIC if py else O.BC_NEUMANN, r, l, m)
+    rng = np.random.default_rng(seed)
+    phi = rng.standard_normal(M.nleaf)
+    E = M.node_e(phi, [0.3, -0.2, 0.0, 0.0])
+    NX, NY = nx0 << lmax, ny0 << lmax
+    checked = 0
+    for A in range(M.nleaf):
+        for c, (di, dj) in enumerate(((0, 0), (1, 0), (0, 1), (1, 1))):
+            I, J = M.ix[A] + di * M.s[A], M.iy[A] + dj * M.s[A]
+            # leaves on the four lattice cells around the node
+            around = [M.leaf_at(I - 1, J - 1), M.leaf_at(I, J - 1), M.leaf_at(I - 1, J), M.leaf_at(I, J)]
+            for B in set(around) - {-1, A}:
+                if M.s[B] != 2 * M.s[A]:
+                    continue
+                # node strictly inside an edge of B (periodic distances on the lattice)
+                oi = (I - M.ix[B]) % NX if px else I - M.ix[B]
+                oj = (J - M.iy[B]) % NY if py else J - M.iy[B]
+                sB = M.s[B]
+                if oi in (0, sB) and 0 < oj < sB:      # vertical edge of B: corners below/above
+                    k0, k1 = (0, 2) if oi == 0 else (1, 3)
+                elif oj in (0, sB) and 0 < oi < sB:    # horizontal edge
+                    k0, k1 = (0, 1) if oj == 0 else (2, 3)
+                else:
+                    continue
+                ref = 0.5 * (E[B, k0] + E[B, k1])
+                assert np.abs(E[A, c] - ref).max() <= 1e-12 * np.abs(E).max(), (A, c, B)
+                checked += 1
+    assert checked > 20
+
+
+def test_node_e_and_cell_emag_converge_for_a_smooth_potential_on_amr():
+    """For phi = sin(pi x) sin(pi y) sampled at the leaf centres of a three-level tree (walls at
+    phi = 0), the corner field converges to -grad phi at the corners and |E| to |grad phi| at
+    the centres as the mesh is refined: observed order >= 0.95 in the max norm (first order at
+    hanging nodes and walls) and >= 1.3 in the mean square.  Fails for: a dropped term of
+    the corner average or of the wall gradient, a sign error, or E taken at the leaf centre."""
+    errs = []
+    for n in (16, 32, 64):
+        M = _disk_mesh(n, 2, O.BC_DIRICHLET, O.BC_DIRICHLET)
+        xc, yc = M.centres()
+        phi = np.sin(np.pi * xc) * np.sin(np.pi * yc)
+        E = M.node_e(phi, [0, 0, 0, 0])
+        h = M.h()
+        X = (M.ix * M.hf)[:, None] + np.array([0, 1, 0, 1])[None, :] * h[:, None]
+        Y = (M.iy * M.hf)[:, None] + np.array([0, 0, 1, 1])[None, :] * h[:, None]
+        ex = -np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        ey = -np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        en = np.maximum(np.abs(E[:, :, 0] - ex), np.abs(E[:, :, 1] - ey))
+        em = M.cell_emag(phi, [0, 0, 0, 0])
+        ec = np.abs(em - np.pi * np.hypot(np.cos(np.pi * xc) * np.sin(np.pi * yc),
+                                          np.sin(np.pi * xc) * np.cos(np.pi * yc)))
+        errs.append((en.max(), np.sqrt((en ** 2).mean()), ec.max(), np.sqrt((ec ** 2).mean())))
+    e = np.array(errs)
+    order = np.log2(e[:-1] / e[1:])
+    assert order[:, 0].min() >= 0.95 and order[:, 2].min() >= 0.95, order
+    assert order[:, 1].min() >= 1.3 and order[:, 3].min() >= 1.3, order
