@@ -72,7 +72,13 @@ enum {
     PIC_FIELD_COUNT_I = 3, /* particles of species 1 in the leaf (1 per leaf)                 */
     PIC_FIELD_NODE_E = 4,  /* E at the leaf's 4 corners (x0,y0),(x1,y0),(x0,y1),(x1,y1),
                               (Ex,Ey) each: 8 per leaf [V/m]                                */
-    PIC_FIELD_EMAG = 5     /* |E| at the leaf centre from the face gradients (1 per leaf)     */
+    PIC_FIELD_EMAG = 5,    /* |E| at the leaf centre from the face gradients (1 per leaf)     */
+    /* time averages over the steps since the diagnostics were last reset (pic_diag_enable;
+       0 when none were taken): */
+    PIC_FIELD_AVG_NE = 6,  /* electron density [m^-3]                                         */
+    PIC_FIELD_AVG_NI = 7,  /* ion density [m^-3]                                              */
+    PIC_FIELD_AVG_TE = 8,  /* electron temperature (2/3) <eps> [eV], 0 where no electrons     */
+    PIC_FIELD_AVG_PHI = 9  /* potential [V]                                                   */
 };
 
 /* Phases timed by pic_get_timing (CUDA events on the context's stream). */
@@ -121,7 +127,10 @@ typedef struct pic_config {
 } pic_config;
 
 /* Create a context of n_instances independent PIC instances, one config each (cfg points
- * to n_instances structs).  The device is the current CUDA device.  *out receives the
+ * to n_instances structs): the ES-PIC with MCC of electrons and ions with neutrals of §3 (its
+ * physical parameters: charges, masses, time step, neutral gas, the analytic cross sections,
+ * wall potentials), the refinement and particle-management parameters of §3.1 and §4.3, and
+ * the multigrid tolerance of §3.  The device is the current CUDA device.  *out receives the
  * context.  Errors: PIC_EINVAL (bad config), PIC_ENOMEM, PIC_ECUDA. */
 GBPIC_API pic_status pic_create(const pic_config *cfg, int32_t n_instances, pic_ctx **out);
 
@@ -147,8 +156,12 @@ GBPIC_API pic_status pic_set_mesh(pic_ctx *ctx, int32_t inst, int32_t nx0, int32
  * host arrays of absolute positions x, y, velocities vx, vy, vz and weights w (real
  * particles per macro-particle per unit depth).  id == NULL assigns ids next_id ..
  * next_id + n - 1.  Particles are located in their leaf (half-open cells, floor rule) and
- * put into cell-list order: by leaf, load order inside a leaf.  Errors: PIC_EINVAL
- * (position outside the domain, id >= 2^32, mesh not set), PIC_ENOMEM, PIC_ECUDA. */
+ * put into the leaf's cell-based list (§3.1): by leaf, load order inside a leaf.  After
+ * loading species 0 (the electrons) the explicit-PIC limits of §3 are checked as by
+ * pic_check_stability: when a leaf is wider than 3 Debye lengths or omega_pe dt > 1 the
+ * call returns PIC_WARN_STABILITY (the particles are loaded; pic_last_error() gives the
+ * numbers).  Errors: PIC_EINVAL (position outside the domain, id >= 2^32, mesh not set),
+ * PIC_ENOMEM, PIC_ECUDA. */
 GBPIC_API pic_status pic_load_particles(pic_ctx *ctx, int32_t inst, int32_t species, int64_t n,
                               const double *x, const double *y, const double *vx,
                               const double *vy, const double *vz, const double *w,
@@ -158,7 +171,8 @@ GBPIC_API pic_status pic_load_particles(pic_ctx *ctx, int32_t inst, int32_t spec
  * multigrid Poisson -> corner E -> fused gather, leapfrog push, wall handling, leaf
  * location and MCC with electron-ion pair spawning -> cell-list update.  Asynchronous
  * except for capacity checks.  Errors: PIC_ECAPACITY, PIC_ENOTCONV (the step still
- * completed with the last iterate), PIC_ECUDA. */
+ * completed with the last iterate; also when the residual is not finite -- NaN or Inf in the
+ * charge density or the potential -- which pic_last_error() names), PIC_ECUDA. */
 GBPIC_API pic_status pic_step(pic_ctx *ctx, int32_t n_steps);
 
 /* Compute deposit -> Poisson -> corner E for the current state without moving particles
@@ -174,7 +188,13 @@ GBPIC_API pic_status pic_compute_fields(pic_ctx *ctx);
  * below ppc_min; merge pairs down to ppc_target when it is above ppc_max. */
 GBPIC_API pic_status pic_adapt(pic_ctx *ctx, int32_t flags);
 
-/* Copy a per-leaf field (PIC_FIELD_*) of instance `inst` to host memory `out`. */
+/* Copy a per-leaf field (PIC_FIELD_*) of instance `inst` to host memory `out`, in leaf (Morton
+ * key) order: the potential at cell centres and the NGP charge density of §3, the per-leaf
+ * counts of the cell-based lists of §3.1, the corner field that §3's bilinear gather reads,
+ * and the centre |E| of the refinement criterion.  out must hold 8 values per leaf for
+ * PIC_FIELD_NODE_E, 1 otherwise; `cap` and `n_out` as in the conventions above.  Fields are
+ * those of the last step or pic_compute_fields.  Errors: PIC_EINVAL (unknown field, cap too
+ * small, mesh not set), PIC_ECUDA. */
 GBPIC_API pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *out,
                            int64_t cap, int64_t *n_out);
 
@@ -221,17 +241,19 @@ GBPIC_API pic_status pic_get_list_stats(pic_ctx *ctx, int32_t inst, int32_t spec
                                         int64_t *tail_moves, int64_t *overflowed);
 
 /* |E| at the leaf centres of instance `inst`, exactly as pic_read_fields(PIC_FIELD_EMAG), for
- * callers that cannot allocate device memory: code that runs while another thread captures a
- * CUDA graph in global capture mode (where cudaMalloc is refused), callers whose device memory
- * is fully owned by an outside allocator or a fixed budget, and real-time loops that allocate
- * nothing after start-up.  The paper has no counterpart; this is an interface convenience.
- * It uses a fixed 1 MiB file-scope device array (held by every GPU that loads the library
- * until the process exits) instead of a temporary buffer, so it accepts meshes of at most
- * 131,072 leaves and returns PIC_EINVAL with a message for larger ones.  The first call on a
- * device looks up that array's device address (once per device, with the device current);
- * make that first call before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (other streams, threads or contexts at the same time) race on it.  `out`,
- * `cap`, `n_out` and the errors are as in pic_read_fields; the call synchronises the stream. */
+ * callers that cannot allocate device memory: code whose device memory is fully owned by an
+ * outside allocator or a fixed budget (where a cudaMalloc behind its back could fail or break
+ * its accounting), and real-time loops that allocate nothing after start-up (cudaMalloc and
+ * cudaFree can stall or synchronize the device).  The paper has no counterpart; this is an
+ * interface convenience.  It uses a fixed 1 MiB file-scope device array (held by every GPU
+ * that loads the library until the process exits) instead of a temporary buffer, so it
+ * accepts meshes of at most 131,072 leaves and returns PIC_EINVAL with a message for larger
+ * ones.  The first call on a device looks up that array's device address (once per device,
+ * with the device current); make that first call before any stream capture.  The current
+ * device must be the context's device (else PIC_EINVAL, the context stays usable).  All
+ * calls share the one array and it keeps the last call's values: calls that overlap on the
+ * GPU (other streams, threads or contexts at the same time) race on it.  `out`, `cap`,
+ * `n_out` and the errors are as in pic_read_fields; the call synchronises the stream. */
 GBPIC_API pic_status pic_read_emag_noalloc(pic_ctx *ctx, int32_t inst, double *out, int64_t cap,
                                            int64_t *n_out);
 
@@ -254,6 +276,80 @@ GBPIC_API pic_status pic_autotune(pic_ctx *ctx, int32_t max_steps, int32_t *step
  * Any pointer may be NULL. */
 GBPIC_API pic_status pic_get_tuning(const pic_ctx *ctx, int32_t *push_threads, int32_t *push_blocks_per_sm,
                                     int32_t *graph_push_div, int32_t *graph_branches, double *best_ms);
+
+/* Time-averaged diagnostics of instance `inst` (§3.3: the discharge results are RF-cycle
+ * averages of n_e, n_i, T_e, phi and the electron energy distribution; §3.1: statistics
+ * counters are reset when the grid changes).  With n_bins > 0, every later step adds, after its
+ * field solve, the stored state (x^n, v^{n-1/2}) and the step's potential to per-leaf sums of
+ * the electron and ion weights, the electrons' weighted kinetic energy eps = m |v|^2 / (2 qe)
+ * [eV] and phi, and the weight of every electron inside region = {x0, x1, y0, y1} (absolute,
+ * [x0, x1) x [y0, y1); NULL = the whole domain) to an energy histogram of n_bins (<= 512)
+ * bins of width eps_max_ev / n_bins (energies >= eps_max_ev are not binned).  The sums are
+ * reset by this call, by pic_diag_reset and by every mesh change (pic_adapt with
+ * PIC_ADAPT_MESH, pic_set_mesh).  n_bins = 0 turns the diagnostics off.  Read them with
+ * pic_read_fields (PIC_FIELD_AVG_*) and pic_read_eedf.  Every sum is taken in a fixed order:
+ * two runs give the same bits.  Instances with diagnostics on are stepped without the
+ * ensemble's captured graph.  Errors: PIC_EINVAL (n_bins > 512, eps_max_ev <= 0). */
+GBPIC_API pic_status pic_diag_enable(pic_ctx *ctx, int32_t inst, int32_t n_bins, double eps_max_ev,
+                                     const double *region);
+GBPIC_API pic_status pic_diag_reset(pic_ctx *ctx, int32_t inst);
+
+/* The electron energy distribution of the diagnostics' region accumulated since the reset,
+ * normalised as a density in energy: f[b] = S_b / (sum_b S_b * d_eps) [1/eV] for the bin
+ * [b d_eps, (b + 1) d_eps), S_b the summed weights (all 0 when nothing was binned).
+ * *samples (may be NULL) receives the steps accumulated.  cap / n_out as for read-outs
+ * (n_bins values).  Errors: PIC_EINVAL (diagnostics off, cap too small). */
+GBPIC_API pic_status pic_read_eedf(pic_ctx *ctx, int32_t inst, double *f, int64_t cap, int64_t *n_out,
+                                   int64_t *samples);
+
+/* The explicit-PIC limits of §3 (cells smaller than about 3 Debye lengths, omega_pe dt < 1)
+ * for given plasma parameters: n_e_max the largest electron density over leaves [m^-3],
+ * w_leaf_max the largest electron weight sum of a leaf (n_e h^2 per unit depth [m^-1]),
+ * t_e_ev the electron temperature [eV], with q[0], m[0], eps0, qe and dt of *cfg.  Writes
+ * max h / lambda_D = sqrt(w_leaf_max q^2 / (eps0 kT)) (infinite when kT = 0 and electrons
+ * are present) and max omega_pe dt = sqrt(n_e_max q^2 / (eps0 m)) dt (either pointer may be
+ * NULL).  Returns PIC_WARN_STABILITY when the first exceeds 3 or the second 1, else PIC_OK.
+ * A host computation: needs no context and no GPU.  Errors: PIC_EINVAL (negative inputs,
+ * non-positive eps0, m[0] or qe). */
+GBPIC_API pic_status pic_stability_limits(const pic_config *cfg, double n_e_max, double w_leaf_max, double t_e_ev,
+                                          double *dx_over_debye, double *wpe_dt);
+
+/* The same limits for the current electron population (species 0) of instance `inst`: per
+ * leaf the weight sum and density from the cell lists, the temperature from the weighted
+ * velocity variance of the whole population (kT = m <|v - <v>|^2> / 3).  Writes the two
+ * ratios and T_e [eV] (any pointer may be NULL); returns PIC_WARN_STABILITY or PIC_OK as
+ * pic_stability_limits.  Synchronises the stream.  Errors: PIC_EINVAL (mesh not set),
+ * PIC_ECUDA. */
+GBPIC_API pic_status pic_check_stability(pic_ctx *ctx, int32_t inst, double *dx_over_debye, double *wpe_dt,
+                                         double *t_e_ev);
+
+/* Checkpoint of instance `inst` (no counterpart in the paper): a self-contained byte image of
+ * every piece of state the following steps read -- the leaf mesh, the potential with the
+ * previous solution and the solve count of the multigrid warm start, the wall potentials of
+ * the last solve, the context's step counter and the instance's next particle id, and per
+ * species the cell lists (records in list order, in the state's precision) with the per-leaf
+ * weight sums left for the next deposit.  Writes the image to `buf` (host memory of `cap`
+ * bytes) and its size to *bytes; with buf == NULL or cap too small it only reports the size
+ * and returns PIC_EINVAL.  Synchronises the stream.  Errors: PIC_EINVAL, PIC_ECUDA. */
+GBPIC_API pic_status pic_checkpoint_write(pic_ctx *ctx, int32_t inst, void *buf, int64_t cap, int64_t *bytes);
+
+/* Restore instance `inst` from an image of pic_checkpoint_write taken from an instance of the
+ * same configuration (precision, species, max_level must match; the image is checked).  The
+ * mesh and both populations are replaced and the context's step counter is set to the
+ * image's.  Later steps and adaptations then give bit for bit the results the checkpointed
+ * run gives.  Errors: PIC_EINVAL (not an image of this version, configuration mismatch,
+ * truncated), PIC_ECAPACITY, PIC_ENOMEM, PIC_ECUDA. */
+GBPIC_API pic_status pic_checkpoint_read(pic_ctx *ctx, int32_t inst, const void *buf, int64_t bytes);
+
+/* Host-side fault injection for tests of the failure paths (no counterpart in the paper; no
+ * GPU fault is made).  PIC_FAULT_ALLOC: after `count` more device allocations from the
+ * context's block cache (every mesh, particle and temporary buffer), the next one fails as a
+ * failed cudaMalloc would, and the call that made it returns PIC_ENOMEM (the context stays
+ * usable).  PIC_FAULT_BALANCE: pic_adapt's 2:1 balance closure gives up after `count`
+ * sweeps (1..64; normally 64) with PIC_ETIMEOUT, before the mesh is changed.
+ * PIC_FAULT_NONE clears both.  Errors: PIC_EINVAL. */
+enum { PIC_FAULT_NONE = 0, PIC_FAULT_ALLOC = 1, PIC_FAULT_BALANCE = 2 };
+GBPIC_API pic_status pic_inject_fault(pic_ctx *ctx, int32_t kind, int64_t count);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 GBPIC_API const char *pic_last_error(void);

@@ -101,7 +101,7 @@ def _declare(L):
     L.or_cell_emag.argtypes = [C.POINTER(_Mesh), _p, _p, _p]
     L.or_deposit.argtypes = [_i64, _i64, _p, _p, C.c_double, _p]
     L.or_push_mcc.argtypes = [C.POINTER(_Mesh), C.POINTER(_PushParams), _p, _i64, _p, _p, _p,
-                              _p, _p, _p, _p, _p, _p, _p, _p]
+                              _p, _p, _p, _p, _p, _p, _p, _p, _p]
     L.or_push_mcc.restype = _i64
 
 
@@ -302,6 +302,8 @@ class Sim:
         self.last_walls = None
         self.last_rho = None
         self.last_node_e = None
+        self.last_decisions = {}
+        self.diag = None
 
     # -- loading: the population is located and put into list order by a stable sort on
     #    the leaf index (load order inside a leaf) ---------------------------------------
@@ -358,9 +360,69 @@ class Sim:
         out = {}
         if mesh:
             out["mesh"] = adapt_mesh(self)
+            if out["mesh"]["refined"] or out["mesh"]["coarsened"]:
+                self.diag_reset()  # §3.1: statistics counters restart when the grid changes
         if particles:
             out["particles"] = split_merge(self)
         return out
+
+    # -- §3.3 time averages: the discharge's RF-cycle averages of n_e, n_i, T_e, phi and the
+    #    electron energy distribution, accumulated over the steps since the last reset ----
+    def diag_enable(self, n_bins, eps_max_ev, region=None):
+        """Every later step samples, after its field solve, the stored state (x^n,
+        v^{n-1/2}) and the step's potential: per leaf the electron and ion weights, the
+        electrons' weighted kinetic energy eps = m |v|^2 / (2 qe) [eV] and phi; and the weight
+        of every electron inside region (x0, x1, y0, y1; [x0, x1) x [y0, y1)) goes to the
+        energy bin floor(eps * (n_bins / eps_max)) when that is below n_bins."""
+        if n_bins <= 0:
+            self.diag = None
+            return
+        r = (-np.inf, np.inf, -np.inf, np.inf) if region is None else tuple(float(v) for v in region)
+        self.diag = dict(n_bins=int(n_bins), eps_max=float(eps_max_ev), region=r)
+        self.diag_reset()
+
+    def diag_reset(self):
+        d = self.diag
+        if d is None:
+            return
+        n = self.mesh.nleaf
+        d.update(we=np.zeros(n), wi=np.zeros(n), wee=np.zeros(n), phi=np.zeros(n),
+                 hist=np.zeros(d["n_bins"]), samples=0)
+
+    def _diag_sample(self):
+        d = self.diag
+        e = self.species[0]
+        if e is not None and e.n:
+            hmq = 0.5 * e.m / self.cfg.get("qe", QE)
+            eps = hmq * (e.vx * e.vx + e.vy * e.vy + e.vz * e.vz)
+            np.add.at(d["we"], e.leaf, e.w)
+            np.add.at(d["wee"], e.leaf, e.w * eps)
+            x0, x1, y0, y1 = d["region"]
+            inside = (e.x >= x0) & (e.x < x1) & (e.y >= y0) & (e.y < y1) & (eps < d["eps_max"])
+            b = np.floor(eps[inside] * (d["n_bins"] / d["eps_max"])).astype(np.int64)
+            keep = b < d["n_bins"]
+            np.add.at(d["hist"], b[keep], e.w[inside][keep])
+        if len(self.species) > 1 and self.species[1] is not None and self.species[1].n:
+            np.add.at(d["wi"], self.species[1].leaf, self.species[1].w)
+        d["phi"] += self.phi
+        d["samples"] += 1
+
+    def diag_fields(self):
+        """Averages since the reset: n_e, n_i [per volume], T_e = (2/3) <eps> [eV], phi."""
+        d = self.diag
+        k = max(1, d["samples"])
+        area = self.mesh.area()
+        z = d["samples"] > 0
+        te = np.where(d["we"] > 0, (2.0 / 3.0) * d["wee"] / np.where(d["we"] > 0, d["we"], 1.0), 0.0)
+        return dict(ne=d["we"] / (k * area) * z, ni=d["wi"] / (k * area) * z, te=te * z, phi=d["phi"] / k * z)
+
+    def diag_eedf(self):
+        """f[b] = S_b / (sum S * d_eps) [1/eV] and the number of samples."""
+        d = self.diag
+        tot = d["hist"].sum()
+        deps = d["eps_max"] / d["n_bins"]
+        f = d["hist"] / (tot * deps) if tot > 0 else np.zeros(d["n_bins"])
+        return f, d["samples"]
 
     def push_params(self, s):
         c = self.cfg
@@ -378,6 +440,8 @@ class Sim:
 
     def _step_once(self):
         _, _, E = self.fields()
+        if self.diag is not None:
+            self._diag_sample()
         Eflat = np.ascontiguousarray(E.reshape(-1))
         results = []
         for s, sp in enumerate(self.species):
@@ -389,9 +453,13 @@ class Sim:
             spawn = np.zeros(n, np.uint8)
             sv = np.zeros(3 * n); svi = np.zeros(3 * n)
             p = self.push_params(s)
+            dec = np.empty(4 * n)
             lib().or_push_mcc(C.byref(self.mesh._c), C.byref(p), _ptr(Eflat), n, _ptr(sp.x),
                               _ptr(sp.y), _ptr(sp.vx), _ptr(sp.vy), _ptr(sp.vz), _ptr(sp.id),
-                              _ptr(sp.leaf), _ptr(new_leaf), _ptr(spawn), _ptr(sv), _ptr(svi))
+                              _ptr(sp.leaf), _ptr(new_leaf), _ptr(spawn), _ptr(sv), _ptr(svi),
+                              _ptr(dec))
+            # the collision decisions of this step by particle id: (U0, P, U1 sigma_T, sigma_iz)
+            self.last_decisions[s] = (sp.id.copy(), dec.reshape(n, 4))
             results.append((new_leaf, spawn, sv.reshape(n, 3), svi.reshape(n, 3)))
         # spawned pairs (electrons only): ids next_id + 2*rank (electron), +1 (ion), rank =
         # position among the ionizing electrons in list order

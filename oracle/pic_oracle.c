@@ -496,17 +496,21 @@ static void iso_dir(double uc, double up, double d[3])
  * leaf of x^n, node E per leaf corner (or_node_e layout).  Outputs in place: v^{n+1/2}
  * (after collisions), x^{n+1}; new_leaf (-1 = absorbed).  Electrons that ionize set
  * spawn[i] = 1 and write the new electron velocity (spawn_v[3i..]) and new ion velocity
- * (spawn_vi[3i..]).  Returns the number of ionizations.
+ * (spawn_vi[3i..]).  When dec is not NULL it receives the quantities of each particle's
+ * collision decisions, dec[4i..4i+3] = (U0, P, U1 sigma_T, sigma_iz): collide iff U0 < P,
+ * ionize iff U1 sigma_T < sigma_iz (electrons; ions 0, 0); U0 = -1 where no collision test
+ * was made (absorbed particle, collisions off).  Returns the number of ionizations.
  */
 int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *node_e_arr,
                     int64_t n, double *x, double *y, double *vx, double *vy, double *vz,
                     const uint64_t *id, const int64_t *leaf, int64_t *new_leaf, uint8_t *spawn,
-                    double *spawn_v, double *spawn_vi)
+                    double *spawn_v, double *spawn_vi, double *dec)
 {
     double hf = m->h0 / (double)(1 << m->lmax);
     int64_t nspawn = 0;
     for (int64_t i = 0; i < n; ++i) {
         spawn[i] = 0;
+        if (dec) { dec[4 * i] = -1.0; dec[4 * i + 1] = 0.0; dec[4 * i + 2] = 0.0; dec[4 * i + 3] = 0.0; }
         int64_t l = leaf[i];
         double h = m->s[l] * hf;
         double u = (x[i] - m->ix[l] * hf) / h, v = (y[i] - m->iy[l] * hf) / h;
@@ -546,6 +550,7 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
             double s_iz = eps > p->eps_th_ev ? p->sigma_iz0 * (1.0 - p->eps_th_ev / eps) : 0.0;
             double s_t = p->sigma_el + s_iz;
             double P = 1.0 - exp(-p->ng * s_t * speed * p->dt);
+            if (dec) { dec[4 * i] = U[0]; dec[4 * i + 1] = P; dec[4 * i + 2] = U[1] * s_t; dec[4 * i + 3] = s_iz; }
             if (!(U[0] < P)) continue;
             if (U[1] * s_t < s_iz) {
                 /* ionization: pay the threshold, share the rest, spawn an e-ion pair */
@@ -582,6 +587,7 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
             double g[3] = {vx[i] - vn[0], vy[i] - vn[1], vz[i] - vn[2]};
             double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             double P = 1.0 - exp(-p->ng * p->sigma_el * gm * p->dt);
+            if (dec) { dec[4 * i] = U[0]; dec[4 * i + 1] = P; }
             if (!(U[0] < P)) continue;
             double d[3];
             iso_dir(U[2], U[3], d);

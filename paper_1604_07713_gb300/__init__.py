@@ -23,7 +23,7 @@ PIC_FP32, PIC_FP64 = 0, 1
 PIC_BC_PERIODIC, PIC_BC_DIRICHLET, PIC_BC_NEUMANN = 0, 1, 2
 PIC_ADAPT_MESH, PIC_ADAPT_PARTICLES = 1, 2
 PIC_FIELD_PHI, PIC_FIELD_RHO, PIC_FIELD_COUNT_E, PIC_FIELD_COUNT_I, PIC_FIELD_NODE_E, \
-    PIC_FIELD_EMAG = range(6)
+    PIC_FIELD_EMAG, PIC_FIELD_AVG_NE, PIC_FIELD_AVG_NI, PIC_FIELD_AVG_TE, PIC_FIELD_AVG_PHI = range(10)
 PHASES = ["deposit", "poisson", "node_e", "lists", "scan", "move", "sort", "adapt", "split_merge", "graph"]
 PIC_N_PHASES = len(PHASES)
 
@@ -31,7 +31,10 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_
             "pic_step", "pic_compute_fields", "pic_adapt", "pic_read_fields", "pic_read_mesh",
             "pic_read_particles", "pic_get_counts", "pic_get_step", "pic_set_step",
             "pic_set_timing", "pic_get_timing", "pic_get_launch_count", "pic_get_list_stats", "pic_read_emag_noalloc",
-            "pic_autotune", "pic_get_tuning", "pic_last_error"]
+            "pic_autotune", "pic_get_tuning", "pic_stability_limits", "pic_check_stability",
+            "pic_checkpoint_write", "pic_checkpoint_read", "pic_inject_fault", "pic_diag_enable",
+            "pic_diag_reset", "pic_read_eedf", "pic_last_error"]
+PIC_FAULT_NONE, PIC_FAULT_ALLOC, PIC_FAULT_BALANCE = 0, 1, 2
 
 
 class PicConfig(C.Structure):
@@ -112,6 +115,12 @@ def _declare(L):
         "pic_get_list_stats": [_p, _i32, _i32, _p, _p, _p],
         "pic_read_emag_noalloc": [_p, _i32, _p, _i64, _p],
         "pic_autotune": [_p, _i32, _p], "pic_get_tuning": [_p, _p, _p, _p, _p, _p],
+        "pic_stability_limits": [_p, C.c_double, C.c_double, C.c_double, _p, _p],
+        "pic_check_stability": [_p, _i32, _p, _p, _p],
+        "pic_checkpoint_write": [_p, _i32, _p, _i64, _p], "pic_checkpoint_read": [_p, _i32, _p, _i64],
+        "pic_inject_fault": [_p, _i32, _i64],
+        "pic_diag_enable": [_p, _i32, _i32, C.c_double, _p], "pic_diag_reset": [_p, _i32],
+        "pic_read_eedf": [_p, _i32, _p, _i64, _p, _p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -168,10 +177,13 @@ def pic_set_mesh(ctx, inst, nx0, ny0, h0, root=None, morton=None, level=None):
 
 
 def pic_load_particles(ctx, inst, species, x, y, vx, vy, vz, w, ids=None):
+    """Returns PIC_OK, or PIC_WARN_STABILITY when the loaded electrons break the explicit-PIC
+    limits (the particles are loaded either way)."""
     arrs = [_f64(a) for a in (x, y, vx, vy, vz, w)]
     n = arrs[0].size
     i = None if ids is None else np.ascontiguousarray(ids, np.uint64)
-    _call("pic_load_particles", ctx, inst, species, n, *[_ptr(a) for a in arrs], _ptr(i))
+    return _call("pic_load_particles", ctx, inst, species, n, *[_ptr(a) for a in arrs], _ptr(i),
+                 ok=(PIC_OK, PIC_WARN_STABILITY))
 
 
 def pic_step(ctx, n_steps=1, allow_notconv=False):
@@ -284,6 +296,60 @@ def pic_read_emag_noalloc(ctx, inst, out: np.ndarray) -> int:
     return n.value
 
 
+def pic_stability_limits(cfg: dict, n_e_max, w_leaf_max, t_e_ev):
+    """(status, max h / lambda_D, max omega_pe dt) for the given plasma parameters (host only)."""
+    c = config_struct(cfg)
+    a, b = C.c_double(), C.c_double()
+    st = _call("pic_stability_limits", C.byref(c), n_e_max, w_leaf_max, t_e_ev, C.byref(a), C.byref(b),
+               ok=(PIC_OK, PIC_WARN_STABILITY))
+    return st, a.value, b.value
+
+
+def pic_check_stability(ctx, inst=0):
+    """(status, max h / lambda_D, max omega_pe dt, T_e [eV]) of the instance's electrons."""
+    a, b, t = C.c_double(), C.c_double(), C.c_double()
+    st = _call("pic_check_stability", ctx, inst, C.byref(a), C.byref(b), C.byref(t),
+               ok=(PIC_OK, PIC_WARN_STABILITY))
+    return st, a.value, b.value, t.value
+
+
+def pic_checkpoint_write(ctx, inst=0) -> bytes:
+    n = C.c_int64()
+    lib().pic_checkpoint_write(ctx, inst, None, 0, C.byref(n))
+    if n.value <= 0:
+        raise PicError("pic_checkpoint_write", PIC_EINVAL, lib().pic_last_error().decode())
+    buf = C.create_string_buffer(n.value)
+    _call("pic_checkpoint_write", ctx, inst, C.cast(buf, C.c_void_p), n.value, C.byref(n))
+    return buf.raw[:n.value]
+
+
+def pic_checkpoint_read(ctx, inst, image: bytes):
+    buf = C.create_string_buffer(image, len(image))
+    _call("pic_checkpoint_read", ctx, inst, C.cast(buf, C.c_void_p), len(image))
+
+
+def pic_diag_enable(ctx, inst, n_bins, eps_max_ev, region=None):
+    r = None if region is None else np.ascontiguousarray(region, np.float64)
+    _call("pic_diag_enable", ctx, inst, n_bins, eps_max_ev, _ptr(r))
+
+
+def pic_diag_reset(ctx, inst=0):
+    _call("pic_diag_reset", ctx, inst)
+
+
+def pic_read_eedf(ctx, inst=0):
+    """(f [1/eV] per energy bin, steps accumulated)."""
+    n, k = C.c_int64(), C.c_int64()
+    lib().pic_read_eedf(ctx, inst, None, 0, C.byref(n), None)
+    out = np.empty(max(0, n.value), np.float64)
+    _call("pic_read_eedf", ctx, inst, _ptr(out), out.size, C.byref(n), C.byref(k))
+    return out, k.value
+
+
+def pic_inject_fault(ctx, kind, count=0):
+    _call("pic_inject_fault", ctx, kind, count)
+
+
 def pic_last_error() -> str:
     return lib().pic_last_error().decode()
 
@@ -325,7 +391,22 @@ class Context:
                      mesh.get("morton"), mesh.get("level"))
 
     def load(self, species, x, y, vx, vy, vz, w, ids=None, inst=0):
-        pic_load_particles(self.ctx, inst, species, x, y, vx, vy, vz, w, ids)
+        return pic_load_particles(self.ctx, inst, species, x, y, vx, vy, vz, w, ids)
+
+    def checkpoint(self, inst=0) -> bytes:
+        return pic_checkpoint_write(self.ctx, inst)
+
+    def restore(self, image: bytes, inst=0):
+        pic_checkpoint_read(self.ctx, inst, image)
+
+    def stability(self, inst=0):
+        return pic_check_stability(self.ctx, inst)
+
+    def diag_enable(self, n_bins, eps_max_ev, region=None, inst=0):
+        pic_diag_enable(self.ctx, inst, n_bins, eps_max_ev, region)
+
+    def eedf(self, inst=0):
+        return pic_read_eedf(self.ctx, inst)
 
     def step(self, n=1, allow_notconv=False):
         return pic_step(self.ctx, n, allow_notconv)

@@ -62,6 +62,11 @@ void *raw_alloc(size_t bytes) {
 }  // namespace
 
 void *BlockCache::get(size_t bytes) {
+    if (fail_after == 0) {
+        fail_after = -1;
+        throw Failure(PIC_ENOMEM, "injected allocation failure (" + std::to_string(bytes) + " bytes)");
+    }
+    if (fail_after > 0) --fail_after;
     const size_t c = size_class(bytes);
     auto it = idle.lower_bound(c);
     if (it != idle.end() && it->first <= c + c / 4) {
@@ -209,7 +214,7 @@ double collect_solver_stats(pic_ctx *ctx, Instance &in) {
         ctx->launches += (int64_t)in.mg_cycles * in.mg_cycle_nodes;
         in.mg_count_cycles = false;
     }
-    return std::max(in.mg_res_max, in.red_host[6]);
+    return worst_residual_host(in.mg_res_max, in.red_host[6]);
 }
 
 void ensure_species(pic_ctx *ctx, Instance &in) {
@@ -219,6 +224,22 @@ void ensure_species(pic_ctx *ctx, Instance &in) {
 }
 
 }  // namespace
+
+// A new mesh for instance `in` (arguments checked by the caller): particles discarded, leaf
+// arrays, multigrid levels and the corner-field array built.
+void gbpic::set_mesh_impl(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t n_leaves,
+                          const uint32_t *root, const uint32_t *morton, const uint8_t *level) {
+    in.part_mem[0].release_all();
+    in.part_mem[1].release_all();
+    for (auto &sp : in.sp) sp = Species();
+    mesh_build(ctx, in, nx0, ny0, h0, n_leaves, root, morton, level);
+    poisson_setup(ctx, in);
+    diag_reset(ctx, in);
+    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
+    in.stencil = in.mesh_mem.alloc(8 * rs * in.nleaf + 64);
+    GB_CUDA(cudaMemsetAsync(in.stencil, 0, 8 * rs * in.nleaf, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+}
 
 // Field half of a step for every instance: deposits, then one batched launch for all
 // instances whose meshes fit one block (one block each), other instances one by one.
@@ -262,14 +283,21 @@ namespace {
 pic_status end_of_steps(pic_ctx *ctx) {
     report_all(ctx);
     pic_status st = PIC_OK;
+    bool finite = true;
     for (Instance &in : ctx->inst) {
-        if (in.mg_worst > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
+        if (!(in.mg_worst <= in.cfg.mg_rel_tol)) st = PIC_ENOTCONV;
+        if (!std::isfinite(in.mg_worst)) {
+            finite = false;
+            poisson_reset_warm_start(ctx, in);
+        }
         if (in.report_err != 0) {
             ctx->poisoned = true;
             fail(PIC_ESTATE, "particle bookkeeping violated a slot bound (overflow store or re-layout)");
         }
     }
-    if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
+    if (st != PIC_OK)
+        set_error(finite ? "Poisson solve did not reach mg_rel_tol"
+                         : "non-finite Poisson residual: NaN or Inf in the charge density or the potential");
     return st;
 }
 
@@ -373,15 +401,7 @@ pic_status pic_set_mesh(pic_ctx *ctx, int32_t inst, int32_t nx0, int32_t ny0, do
         if (level)
             for (int64_t i = 0; i < n_leaves; ++i)
                 if (level[i] > in.cfg.max_level) fail(PIC_EINVAL, "leaf level above max_level");
-        in.part_mem[0].release_all();
-        in.part_mem[1].release_all();
-        for (auto &sp : in.sp) sp = Species();
-        mesh_build(ctx, in, nx0, ny0, h0, n_leaves, root, morton, level);
-        poisson_setup(ctx, in);
-        const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
-        in.stencil = in.mesh_mem.alloc(8 * rs * in.nleaf + 64);
-        GB_CUDA(cudaMemsetAsync(in.stencil, 0, 8 * rs * in.nleaf, ctx->stream));
-        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        set_mesh_impl(ctx, in, nx0, ny0, h0, n_leaves, root, morton, level);
         return PIC_OK;
     });
 }
@@ -396,7 +416,14 @@ pic_status pic_load_particles(pic_ctx *ctx, int32_t inst, int32_t species, int64
         if (n < 0 || n >= (1ll << 31)) fail(PIC_EINVAL, "bad particle count");
         if (n > 0 && (!x || !y || !vx || !vy || !vz || !w)) fail(PIC_EINVAL, "null particle array");
         particles_load(ctx, in, species, n, x, y, vx, vy, vz, w, id);
-        return PIC_OK;
+        if (species != 0) return PIC_OK;
+        double a = 0.0, b = 0.0, te = 0.0;
+        const pic_status st = stability_check(ctx, in, &a, &b, &te);
+        if (st == PIC_WARN_STABILITY)
+            set_error("explicit-PIC limits exceeded: max dx / lambda_D = " + std::to_string(a) +
+                      " (limit 3), max omega_pe dt = " + std::to_string(b) + " (limit 1), T_e = " +
+                      std::to_string(te) + " eV; the particles were loaded");
+        return st;
     });
 }
 
@@ -410,9 +437,18 @@ pic_status pic_compute_fields(pic_ctx *ctx) {
             reset_solver_stats(ctx, in);
         }
         fields_all(ctx, ctx->step);
-        for (Instance &in : ctx->inst)
-            if (collect_solver_stats(ctx, in) > in.cfg.mg_rel_tol) st = PIC_ENOTCONV;
-        if (st != PIC_OK) set_error("Poisson solve did not reach mg_rel_tol");
+        bool finite = true;
+        for (Instance &in : ctx->inst) {
+            const double worst = collect_solver_stats(ctx, in);
+            if (!(worst <= in.cfg.mg_rel_tol)) st = PIC_ENOTCONV;
+            if (!std::isfinite(worst)) {
+                finite = false;
+                poisson_reset_warm_start(ctx, in);
+            }
+        }
+        if (st != PIC_OK)
+            set_error(finite ? "Poisson solve did not reach mg_rel_tol"
+                             : "non-finite Poisson residual: NaN or Inf in the charge density or the potential");
         return st;
     });
 }
@@ -549,7 +585,7 @@ pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *ou
         if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
         const int64_t nl = in.nleaf;
         int64_t need = field == PIC_FIELD_NODE_E ? 8 * nl : nl;
-        if (field < PIC_FIELD_PHI || field > PIC_FIELD_EMAG) fail(PIC_EINVAL, "unknown field");
+        if (field < PIC_FIELD_PHI || field > PIC_FIELD_AVG_PHI) fail(PIC_EINVAL, "unknown field");
         if (n_out) *n_out = need;
         if (!out || cap < need) fail(PIC_EINVAL, "output capacity too small");
         cudaStream_t st = ctx->stream;
@@ -601,6 +637,15 @@ pic_status pic_read_fields(pic_ctx *ctx, int32_t inst, int32_t field, double *ou
             double walls[4];
             walls_at(in, ctx->step, walls);
             cell_emag(ctx, in, walls, d);
+            GB_CUDA(cudaMemcpyAsync(out, d, nl * 8, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            tmp.release_all();
+            break;
+        }
+        default: {  // time averages
+            DeviceArena tmp(&ctx->cache);
+            double *d = dalloc<double>(tmp, nl);
+            diag_read_field(ctx, in, field, d);
             GB_CUDA(cudaMemcpyAsync(out, d, nl * 8, cudaMemcpyDeviceToHost, st));
             GB_CUDA(cudaStreamSynchronize(st));
             tmp.release_all();
@@ -730,6 +775,89 @@ pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches, int32_t n
             if (ms) ms[r.phase] += t;
             if (launches) launches[r.phase] += r.launches;
         }
+        return PIC_OK;
+    });
+}
+
+pic_status pic_diag_enable(pic_ctx *ctx, int32_t inst, int32_t n_bins, double eps_max_ev, const double *region) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        if (n_bins < 0) fail(PIC_EINVAL, "n_bins < 0");
+        if (region && !(region[0] < region[1] && region[2] < region[3])) fail(PIC_EINVAL, "empty region");
+        diag_enable(ctx, in, n_bins, eps_max_ev, region);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_diag_reset(pic_ctx *ctx, int32_t inst) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        diag_reset(ctx, in);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_read_eedf(pic_ctx *ctx, int32_t inst, double *f, int64_t cap, int64_t *n_out, int64_t *samples) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.diag.on) fail(PIC_EINVAL, "diagnostics are off (pic_diag_enable)");
+        if (n_out) *n_out = in.diag.nbins;
+        if (!f || cap < in.diag.nbins) fail(PIC_EINVAL, "output capacity too small");
+        diag_read_eedf(ctx, in, f, samples);
+        return PIC_OK;
+    });
+}
+
+pic_status pic_check_stability(pic_ctx *ctx, int32_t inst, double *dx_over_debye, double *wpe_dt, double *t_e_ev) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        const pic_status st = stability_check(ctx, in, dx_over_debye, wpe_dt, t_e_ev);
+        if (st == PIC_WARN_STABILITY) set_error("explicit-PIC limits exceeded (dx > 3 lambda_D or omega_pe dt > 1)");
+        return st;
+    });
+}
+
+pic_status pic_inject_fault(pic_ctx *ctx, int32_t kind, int64_t count) {
+    return guarded(ctx, [&]() -> pic_status {
+        if (!ctx) fail(PIC_EINVAL, "null context");
+        switch (kind) {
+        case PIC_FAULT_NONE:
+            ctx->cache.fail_after = -1;
+            ctx->fault_balance_sweeps = 0;
+            break;
+        case PIC_FAULT_ALLOC:
+            if (count < 0) fail(PIC_EINVAL, "count < 0");
+            ctx->cache.fail_after = count;
+            break;
+        case PIC_FAULT_BALANCE:
+            if (count < 1 || count > 64) fail(PIC_EINVAL, "balance sweeps must be in [1, 64]");
+            ctx->fault_balance_sweeps = (int32_t)count;
+            break;
+        default:
+            fail(PIC_EINVAL, "unknown fault kind");
+        }
+        return PIC_OK;
+    });
+}
+
+pic_status pic_checkpoint_write(pic_ctx *ctx, int32_t inst, void *buf, int64_t cap, int64_t *bytes) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        if (!in.has_mesh) fail(PIC_EINVAL, "mesh not set");
+        const int64_t need = checkpoint_write(ctx, in, buf, cap);
+        if (bytes) *bytes = need;
+        if (!buf || cap < need) fail(PIC_EINVAL, "checkpoint buffer too small");
+        return PIC_OK;
+    });
+}
+
+pic_status pic_checkpoint_read(pic_ctx *ctx, int32_t inst, const void *buf, int64_t bytes) {
+    return guarded(ctx, [&]() -> pic_status {
+        Instance &in = get_inst(ctx, inst);
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        checkpoint_read(ctx, in, buf, bytes);
         return PIC_OK;
     });
 }

@@ -727,6 +727,13 @@ template <typename R> void split_merge_impl(pic_ctx *ctx, Instance &in) {
 
 }  // namespace
 
+// Any leaf refined or coarsened (its emitted count is not 1: 4 for a refined leaf, 0 or 1
+// for the members of a coarsened quartet).
+__global__ void k_adapt_changed(int64_t n, const int32_t *__restrict__ cnt, int32_t *__restrict__ changed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cnt[i] != 1) atomicOr(changed, 1);
+}
+
 void adapt_mesh(pic_ctx *ctx, Instance &in) {
     cudaStream_t st = ctx->stream;
     const int64_t n = in.nleaf;
@@ -741,20 +748,29 @@ void adapt_mesh(pic_ctx *ctx, Instance &in) {
     k_adapt_flags<<<blocks_for(n), kT, 0, st>>>(a, refine, group, gactive);
     count_launch(ctx);
     int32_t *changed = dalloc<int32_t>(T, 1);
-    for (int it = 0; it < 64; ++it) {
+    // the closure settles in at most max_level sweeps; the bound is lower only under an
+    // injected fault (pic_inject_fault), which tests the PIC_ETIMEOUT path
+    const int max_sweeps = ctx->fault_balance_sweeps > 0 ? std::min(64, (int)ctx->fault_balance_sweeps) : 64;
+    for (int it = 0; it < max_sweeps; ++it) {
         GB_CUDA(cudaMemsetAsync(changed, 0, 4, st));
         k_adapt_balance<<<blocks_for(n), kT, 0, st>>>(n, in.lmax, g.map, in.nx0 << in.lmax, in.ny0 << in.lmax,
                                                       in.cfg.bc_x == PIC_BC_PERIODIC, in.cfg.bc_y == PIC_BC_PERIODIC,
                                                       g.ix, g.iy, g.lev, refine, group, gactive, changed);
         count_launch(ctx);
         if (!read_i32(ctx, changed)) break;
-        if (it == 63) fail(PIC_ETIMEOUT, "2:1 balance closure did not settle");
+        if (it == max_sweeps - 1)
+            fail(PIC_ETIMEOUT, "2:1 balance closure did not settle in " + std::to_string(max_sweeps) + " sweeps");
     }
     int32_t *cnt = dalloc<int32_t>(T, n + 1), *pos = dalloc<int32_t>(T, n + 1);
     int32_t *scr = dalloc<int32_t>(T, scan_scratch_elems(n));
     k_adapt_emit_count<<<blocks_for(n), kT, 0, st>>>(n, refine, group, gactive, cnt);
     count_launch(ctx);
     exclusive_scan_i32(ctx, cnt, pos, n, scr);
+    int32_t *grid_changed = dalloc<int32_t>(T, 1);
+    GB_CUDA(cudaMemsetAsync(grid_changed, 0, 4, st));
+    k_adapt_changed<<<blocks_for(n), kT, 0, st>>>(n, cnt, grid_changed);
+    count_launch(ctx);
+    const bool grid_did_change = read_i32(ctx, grid_changed) != 0;
     const int64_t n_new = read_i32(ctx, pos + n);
     uint32_t *nroot = dalloc<uint32_t>(T, n_new), *nmort = dalloc<uint32_t>(T, n_new);
     uint8_t *nlev = dalloc<uint8_t>(T, n_new);
@@ -796,6 +812,7 @@ void adapt_mesh(pic_ctx *ctx, Instance &in) {
     GB_CUDA(cudaStreamSynchronize(st));
     old_mesh.release_all();
     T.release_all();
+    if (grid_did_change) diag_reset(ctx, in);  // §3.1: statistics counters restart when the grid changes
 }
 
 void split_merge(pic_ctx *ctx, Instance &in) {

@@ -177,7 +177,10 @@ void one_step(pic_ctx *ctx) {
         graph_step(ctx);  // an ensemble in steady state: the whole step as one graph replay
     } else {
         fields_all(ctx, ctx->step);
-        for (Instance &in : ctx->inst) particle_step(ctx, in, ctx->step);
+        for (Instance &in : ctx->inst) {
+            diag_accumulate(ctx, in);  // time averages of the step's state (when enabled)
+            particle_step(ctx, in, ctx->step);
+        }
     }
     ++ctx->step;
 }
@@ -187,7 +190,7 @@ void one_step(pic_ctx *ctx) {
 bool graph_step_possible(pic_ctx *ctx) {
     if (ctx->inst.size() < 2) return false;
     for (Instance &in : ctx->inst) {
-        if (!in.has_mesh || !in.small_item) return false;
+        if (!in.has_mesh || !in.small_item || in.diag.on) return false;
         for (int s = 0; s < in.cfg.n_species; ++s)
             if (!in.sp[s].start || !in.sp[s].sums_valid) return false;
     }
@@ -267,7 +270,7 @@ void report_all(pic_ctx *ctx) {
         if (in.mg_on_device && in.mg_stats) {
             in.mg_cycles = (int)r[i].mg[0];
             in.mg_res = r[i].mg[1];
-            in.mg_worst = std::max(in.mg_res_max, r[i].mg[2]);
+            in.mg_worst = worst_residual_host(in.mg_res_max, r[i].mg[2]);
             if (in.mg_count_cycles) {  // kernels of the device-side cycle loop of the last solve
                 ctx->launches += (int64_t)in.mg_cycles * in.mg_cycle_nodes;
                 in.mg_count_cycles = false;

@@ -42,6 +42,7 @@ struct BlockCache {
     std::multimap<size_t, void *> idle;      // size class -> cached block
     std::unordered_map<void *, size_t> cls;  // every block from this cache -> its size class
     size_t idle_bytes = 0;
+    int64_t fail_after = -1;  // injected fault: this many more blocks succeed, then one fails
     void *get(size_t bytes);
     void put(void *p);
     void trim();  // cudaFree every cached block
@@ -155,6 +156,21 @@ template <typename R> inline SoA<R> soa_ovf(Species &sp) {
     return a;
 }
 
+// Time-averaged diagnostics of one instance (pic_diag_enable): per-leaf sums over the steps
+// since the last reset, and the electron energy histogram of a region.
+struct Diag {
+    bool on = false;
+    int nbins = 0;
+    double eps_max = 0.0;                   // [eV]
+    double region[4] = {0, 0, 0, 0};        // x0, x1, y0, y1 (absolute)
+    int64_t samples = 0;                    // steps accumulated since the reset
+    int64_t nleaf = 0;
+    double *leaf = nullptr;                 // [4 nleaf]: sum w_e, sum w_i, sum w_e eps [eV], sum phi
+    double *eedf = nullptr;                 // [nbins] sum of electron weights per energy bin
+    double *part = nullptr;                 // per-warp partial histograms of one step
+    DeviceArena mem;
+};
+
 struct Instance {
     pic_config cfg{};
     bool has_mesh = false;
@@ -168,6 +184,7 @@ struct Instance {
     double *phi = nullptr, *bvec = nullptr, *res = nullptr, *charge = nullptr;
     double *phi_prev = nullptr;  // previous solution: the next solve starts from 2 phi - phi_prev
     int n_solves = 0;            // solves since the mesh was set (extrapolation needs two)
+    int32_t *d_n_solves = nullptr;  // the same count on the device, for meshes solved in one launch
     double last_walls[4] = {0, 0, 0, 0};  // wall potentials of the last solve
     double *red = nullptr;       // reduction scratch
     double *red_host = nullptr;  // pinned
@@ -185,7 +202,7 @@ struct Instance {
     double mg_res_max = 0;         // host-driven solves: worst relative residual since reset
     bool mg_on_device = false;     // last solve ran its loop on the device (stats below)
     double *mg_stats = nullptr;    // device: [cycles, rel. residual, max rel. since reset]
-    float *coarse_inv = nullptr;         // coarsest multigrid level: dense inverse (small levels)
+    double *coarse_inv = nullptr;        // coarsest multigrid level: dense FP64 inverse (small levels)
     void *small_item = nullptr;          // meshes that fit one block: the solve's work item
     size_t small_smem = 0;               // and its dynamic shared memory
     int small_cluster = 1;               // CTAs of its cluster when solved alone
@@ -193,6 +210,7 @@ struct Instance {
     int64_t mg_cycle_nodes = 0;          // correction, residual, norm read-back) and its launches
     int64_t mg_pre_nodes = 0;            // launches before the device-side cycle loop
     bool mg_count_cycles = false;        // add the device loop's cycles to the launch count
+    Diag diag;                   // time-averaged diagnostics (off unless enabled)
     DeviceArena mesh_mem;        // freed on pic_set_mesh
     DeviceArena part_mem[2];     // freed on reload / regrow
 };
@@ -250,6 +268,7 @@ struct pic_ctx {
     int64_t report_epoch = -1;
     gbpic::Tuning tune;
     int64_t graph_tune_epoch = -1;
+    int32_t fault_balance_sweeps = 0;  // injected fault: bound of the adaptation's balance closure (0: none)
 };
 
 namespace gbpic {
@@ -342,9 +361,13 @@ void mesh_build(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t
 void mesh_build_device(pic_ctx *ctx, Instance &in, int64_t n);  // from in.root/morton/lev
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]);
 void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev);
+// pic_abi.cu
+void set_mesh_impl(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t n_leaves,
+                   const uint32_t *root, const uint32_t *morton, const uint8_t *level);
 // pic_poisson.cu
 void poisson_setup(pic_ctx *ctx, Instance &in);
 void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]);
+void poisson_reset_warm_start(pic_ctx *ctx, Instance &in);
 void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list,
                          const std::vector<const double *> &walls);
 // pic_particles.cu
@@ -383,9 +406,22 @@ void graph_release(pic_ctx *ctx);
 void report_all(pic_ctx *ctx);            // exact totals, error flags, solver stats of every instance (syncs)
 void fields_all(pic_ctx *ctx, int64_t step);
 void species_compact(pic_ctx *ctx, Instance &in, int s);  // leaf-order re-layout, tail freed
+// pic_checkpoint.cu
+int64_t checkpoint_write(pic_ctx *ctx, Instance &in, void *buf, int64_t cap);  // bytes needed
+void checkpoint_read(pic_ctx *ctx, Instance &in, const void *buf, int64_t bytes);
+// pic_diag.cu
+pic_status stability_check(pic_ctx *ctx, Instance &in, double *dx_ld, double *wdt, double *t_e_ev);
+void diag_reset(pic_ctx *ctx, Instance &in);       // zero the sums (and fit them to the mesh)
+void diag_accumulate(pic_ctx *ctx, Instance &in);  // add this step's sample
+void diag_read_field(pic_ctx *ctx, Instance &in, int field, double *out);  // PIC_FIELD_AVG_*
+void diag_enable(pic_ctx *ctx, Instance &in, int nbins, double eps_max, const double *region);
+void diag_read_eedf(pic_ctx *ctx, Instance &in, double *f, int64_t *samples);
 // pic_adapt.cu
 void adapt_mesh(pic_ctx *ctx, Instance &in);
 void split_merge(pic_ctx *ctx, Instance &in);
+
+// The larger of two relative residuals, NaN if either is NaN (so a non-finite field is reported).
+inline double worst_residual_host(double a, double b) { return (a != a || b != b) ? a + b : (a > b ? a : b); }
 
 // Runs fn(arg) with the ABI's error mapping (exceptions -> pic_status, last error, context
 // poisoning on CUDA failures).  Allocates nothing on the device.

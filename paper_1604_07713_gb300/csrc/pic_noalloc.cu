@@ -51,6 +51,13 @@ pic_status run(void *v) {
         gbpic::fail(PIC_EINVAL, "pic_read_emag_noalloc: " + std::to_string(nl) + " leaves exceed the fixed scratch of " +
                                     std::to_string(kNoAllocMaxLeaves) + " leaves; use pic_read_fields");
     if (!a.out || a.cap < nl) gbpic::fail(PIC_EINVAL, "output capacity too small");
+    // the scratch is picked by the current device: it must be the context's, or the launch on
+    // the context's stream would fail and poison the context
+    int dev = -1;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev != a.ctx->device)
+        gbpic::fail(PIC_EINVAL, "pic_read_emag_noalloc: the current CUDA device (" + std::to_string(dev) +
+                                    ") is not the context's device (" + std::to_string(a.ctx->device) + ")");
     double *scratch = scratch_for_current_device();
     double walls[4];
     gbpic::walls_at(in, a.ctx->step, walls);

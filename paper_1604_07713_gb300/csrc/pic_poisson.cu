@@ -78,6 +78,12 @@ __global__ void k_finish_sums(int nparts, const double *__restrict__ part, doubl
     if (lane == 0) { out[0] = a; out[1] = b; }
 }
 
+// The larger of two relative residuals, NaN if either is NaN: a non-finite residual (NaN or
+// Inf in the charge density or the potential) stays visible to the host.
+__device__ __forceinline__ double worst_residual(double a, double b) {
+    return (a != a || b != b) ? __longlong_as_double(0x7FF8000000000000ll) : fmax(a, b);
+}
+
 // After a residual norm: the solve's statistics and whether another cycle runs (the
 // condition of the graph's WHILE node).  first = 1 before the first cycle.
 __global__ void k_mg_decide(cudaGraphConditionalHandle h, const double *__restrict__ sums, double tol, int maxc,
@@ -89,7 +95,7 @@ __global__ void k_mg_decide(cudaGraphConditionalHandle h, const double *__restri
     const bool done = rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= (double)maxc;
     stats[0] = cyc;
     stats[1] = rel;
-    if (done) stats[2] = fmax(stats[2], rel);
+    if (done) stats[2] = worst_residual(stats[2], rel);
     cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
@@ -340,7 +346,7 @@ struct SmallDesc {
     SmallLevel lv[kMaxSmallLevels];
     int32_t off_cg;  // smem offset of the coarsest CG vectors r, p, q (3 n)
     int32_t smem_floats;
-    const float *cinv;  // coarsest level: dense inverse (n x n, row-major), or null (CG)
+    const double *cinv;  // coarsest level: dense FP64 inverse (n x n, row-major), or null (CG)
 };
 
 // floor(i / d) by a multiply-high reciprocal m = floor((2^32 - 1) / d) + 1; m = 0 stands for
@@ -561,24 +567,31 @@ __device__ void sm_coarse_cg(const SmallDesc &D, const SmallLevel &L, float *x, 
     __syncthreads();
 }
 
-// Coarsest level by its dense inverse C (at most kDirectN cells): x = C (b - mean(b)) with
-// the mean taken out when the mesh is periodic in both directions (C then inverts
-// A + 1 1^T / n, which maps a zero-mean right-hand side to the zero-mean solution).  Warp w
-// forms rows w, w + 32, ...; all threads of the block call it.
+// Coarsest level by its dense inverse C (at most kDirectN cells), applied in FP64:
+// x = C (b - mean(b)) with the mean taken out when the mesh is periodic in both directions (C
+// then inverts A + 1 1^T / n, which maps a zero-mean right-hand side to the zero-mean
+// solution).  Warp w forms rows w, w + 32, ...; all threads of the block call it.
 __device__ void sm_coarse_direct(const SmallDesc &D, const SmallLevel &L, float *x, const float *b, bool singular,
                                  float *red) {
     const int n = L.n, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    float mb = 0.0f;
+    double mb = 0.0;
     if (singular) {
-        float sb = 0.0f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sb += b[i];
-        mb = sm_block_sumf(sb, red) / (float)n;
+        // every lane of warp 0 sums the (at most 64) values in the same order
+        __shared__ double mean_sh;
+        if (threadIdx.x < 32) {
+            double sb = 0.0;
+            for (int i = 0; i < n; ++i) sb += (double)b[i];
+            if (threadIdx.x == 0) mean_sh = sb / (double)n;
+        }
+        __syncthreads();
+        mb = mean_sh;
     }
     for (int r = threadIdx.x >> 5; r < n; r += nwarp) {
-        float acc = 0.0f;
-        for (int c = lane; c < n; c += 32) acc = fmaf(__ldg(D.cinv + r * n + c), b[c] - mb, acc);
-        acc = warp_sumf(acc);
-        if (lane == 0) x[r] = acc;
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc = fma(__ldg(D.cinv + r * n + c), (double)b[c] - mb, acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) x[r] = (float)acc;
     }
     __syncthreads();
 }
@@ -811,7 +824,7 @@ __global__ void __launch_bounds__(1024, 1) k_small_solve(const SmallSolve *__res
     if (rank == 0 && threadIdx.x == 0) {
         it.stats[0] = (double)cyc;
         it.stats[1] = rel;
-        it.stats[2] = fmax(it.stats[2], rel);
+        it.stats[2] = worst_residual(it.stats[2], rel);
     }
 }
 
@@ -953,7 +966,7 @@ constexpr int kDirectN = 64;  // coarsest levels up to this size are solved by a
 // diagonal 1 / dinv rounded to FP32), plus 1 1^T / n when the mesh is periodic in both
 // directions.  Gauss-Jordan with partial pivoting in FP64; null (the CG is used) for a
 // level larger than kDirectN cells or a singular matrix.
-float *coarse_inverse(pic_ctx *ctx, Instance &in, bool singular) {
+double *coarse_inverse(pic_ctx *ctx, Instance &in, bool singular) {
     const Level &L = in.lv.back();
     const int n = (int)L.n;
     if (n > kDirectN || n < 1) return nullptr;
@@ -1016,10 +1029,8 @@ float *coarse_inverse(pic_ctx *ctx, Instance &in, bool singular) {
             }
         }
     }
-    std::vector<float> C((size_t)n * n);
-    for (size_t t = 0; t < C.size(); ++t) C[t] = (float)Inv[t];
-    float *d = dalloc<float>(in.mesh_mem, C.size());
-    GB_CUDA(cudaMemcpyAsync(d, C.data(), C.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    double *d = dalloc<double>(in.mesh_mem, Inv.size());
+    GB_CUDA(cudaMemcpyAsync(d, Inv.data(), Inv.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     return d;
 }
@@ -1037,6 +1048,7 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     in.phi = dalloc<double>(A, n);
     in.phi_prev = dalloc<double>(A, n);
     in.n_solves = 0;
+    in.d_n_solves = nullptr;
     in.bvec = dalloc<double>(A, n);
     in.res = dalloc<double>(A, n);
     in.charge = dalloc<double>(A, n);
@@ -1065,6 +1077,7 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
         int32_t *ns = dalloc<int32_t>(A, 1);
         GB_CUDA(cudaMemsetAsync(ns, 0, 4, ctx->stream));
         it.n_solves = ns;
+        in.d_n_solves = ns;
         SmallSolve *d = (SmallSolve *)A.alloc(sizeof(SmallSolve));
         GB_CUDA(cudaMemcpyAsync(d, &it, sizeof(SmallSolve), cudaMemcpyHostToDevice, ctx->stream));
         GB_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1073,6 +1086,16 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
         in.small_cluster = small_cluster((int)L.n, in.small_smem);
     }
     ++ctx->mesh_epoch;
+}
+
+// After a solve that ended with a non-finite residual: the next solve starts from zero instead
+// of extrapolating from a potential that holds NaN or Inf.
+void poisson_reset_warm_start(pic_ctx *ctx, Instance &in) {
+    const int64_t n = in.lv[0].n;
+    GB_CUDA(cudaMemsetAsync(in.phi, 0, n * 8, ctx->stream));
+    GB_CUDA(cudaMemsetAsync(in.phi_prev, 0, n * 8, ctx->stream));
+    in.n_solves = 0;
+    if (in.d_n_solves) GB_CUDA(cudaMemsetAsync(in.d_n_solves, 0, 4, ctx->stream));
 }
 
 // One launch for every instance whose mesh fits one block: block b solves instance b.

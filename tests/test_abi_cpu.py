@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1604_07713_gb300 as G
@@ -64,3 +65,34 @@ def test_bad_configuration_is_refused_before_any_device_call():
         with pytest.raises(G.PicError) as e:
             G.pic_create(cfg)
         assert e.value.status == G.PIC_EINVAL
+
+
+def test_stability_limits_match_the_formulary_debye_length_and_plasma_frequency():
+    """The explicit-PIC limits of §3 (h < ~3 lambda_D, omega_pe dt < 1) evaluated by the
+    library's host function against the NRL plasma formulary's numerical forms
+    lambda_D = 743 sqrt(T_e[eV] / n_e[cm^-3]) cm and omega_pe = 5.64e4 sqrt(n_e[cm^-3]) rad/s
+    (three-digit constants: 1e-3 relative), for the capacitively coupled discharge's cells
+    (h = 6.7 cm / 512, n = 1e15 m^-3, T_e = 2.5 eV, dt = 1 / (400 x 13.56 MHz)), and the
+    warning thresholds on either side of the limits."""
+    from paper_1604_07713_gb300 import workloads as W
+    G.build()
+    cfg, mesh, _ = W.ccp(nx=512, ny=16, ppc=1)
+    h, n, te = mesh["h0"], 1e15, 2.5
+    st, dx_ld, wdt = G.pic_stability_limits(cfg, n, n * h * h, te)
+    lam = 743.0 * np.sqrt(te / (n * 1e-6)) * 1e-2
+    wpe = 5.64e4 * np.sqrt(n * 1e-6)
+    assert st == G.PIC_OK
+    assert abs(dx_ld / (h / lam) - 1) < 1e-3 and abs(wdt / (wpe * cfg["dt"]) - 1) < 1e-3
+    # densities 1 % above and below the one where h = 3 lambda_D
+    n3 = n * 9.0 / (dx_ld / 1.0) ** 2
+    assert G.pic_stability_limits(cfg, 0.0, 1.01 * n3 * h * h, te)[0] == G.PIC_WARN_STABILITY
+    assert G.pic_stability_limits(cfg, 0.0, 0.99 * n3 * h * h, te)[0] == G.PIC_OK
+    n1 = n / wdt ** 2                          # omega_pe dt = 1
+    assert G.pic_stability_limits(cfg, 1.01 * n1, 0.0, te)[0] == G.PIC_WARN_STABILITY
+    assert G.pic_stability_limits(cfg, 0.99 * n1, 0.0, te)[0] == G.PIC_OK
+    # a cold population is never resolved; no electrons never warns
+    st, dx_ld, _ = G.pic_stability_limits(cfg, n, n * h * h, 0.0)
+    assert st == G.PIC_WARN_STABILITY and np.isinf(dx_ld)
+    assert G.pic_stability_limits(cfg, 0.0, 0.0, 0.0)[0] == G.PIC_OK
+    with pytest.raises(G.PicError):
+        G.pic_stability_limits(cfg, -1.0, 0.0, te)

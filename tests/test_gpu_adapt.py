@@ -120,3 +120,37 @@ def test_adapt_with_crowded_lists_lays_them_out_first_fp64():
         sim.step(2)
         ctx.step(2)
         _compare(sim, ctx, 1e-11)
+
+
+def test_adapt_fp32_with_the_field_criterion_on():
+    """FP32 state with the |E| criterion active: the threshold is put in a gap of the oracle's
+    centre |E| values (every |E| at least 1e-6 away from the refine and coarsen thresholds;
+    |E| comes from the FP64 potential on both sides), so the refinement decisions, the tree
+    and the list order are bit-exact; more leaves refine than the count criterion alone asks."""
+    cfg, mesh, parts = _dyadic_case(W.FP32)
+    M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], mesh["lmax"], cfg["bc_x"], cfg["bc_y"], mesh["root"],
+               mesh["level"], mesh["morton"])
+    probe = O.Sim(cfg, M)
+    probe.load(0, **parts[0])
+    probe.fields()
+    em = np.sort(M.cell_emag(probe.phi, probe.last_walls))
+    ok = lambda t: np.all(np.abs(em - t) > 1e-6 * t) and np.all(np.abs(em - 0.8 * t) > 1e-6 * t)
+    lo = int(0.7 * em.size)
+    gaps = [(em[i + 1] - em[i], i) for i in range(lo, em.size - 1)]
+    thr = None
+    for _, i in sorted(gaps, reverse=True):
+        t = 0.5 * (em[i] + em[i + 1])
+        if ok(t):
+            thr = t
+            break
+    assert thr is not None
+    cfg["e_ref"] = thr / cfg["refine_field"]            # refine above thr, coarsen below 0.8 thr
+    sim, ctx = _pair(cfg, mesh, parts)
+    with ctx:
+        sim.fields(); ctx.compute_fields()
+        cnt = sim.counts(0)
+        by_count = int(np.count_nonzero((cnt > cfg["refine_count"]) & (sim.mesh.level < mesh["lmax"])))
+        st = sim.adapt()
+        ctx.adapt()
+        assert st["mesh"]["refined"] > by_count + 5
+        _compare(sim, ctx, 1e-6)

@@ -1,9 +1,12 @@
 """The streamer at its full size (5e7 particles, ~3.8e5 leaves after adaptation), in the launch
 configuration the benchmark times: properties that hold at any size (every particle inside
 the leaf that lists it, per-leaf counts, unique ids, charge conservation of the deposit), and
-one step of a random sample of particles recomputed by the oracle's push and collisions from
-the GPU's own corner field (FP32 against FP64: positions, velocities, leaves and absorption
-within rounding; collision decisions may differ only inside the rounding margin)."""
+one step of a random sample of 200,000 particles per species recomputed by the oracle's push
+and collisions from the GPU's own corner field (FP32 against FP64): a particle may differ only
+when its collision decision lies inside the rounding margin (|U0 - P| <= 1e-6 P, or the process
+choice within 1e-6 sigma_T of its threshold) or its new position lies within 1e-6 of its leaf
+size of a face; such differences number at most 1e-5 of the sample.  Every other particle has
+the oracle's absorption, leaf, position (1e-5 of the finest cell) and velocity (1e-5)."""
 import ctypes as C
 
 import numpy as np
@@ -60,7 +63,7 @@ def test_streamer_full_size_properties_and_sampled_step():
             assert np.unique(p["id"]).size == p["id"].size
             charge += cfg["q"][s] * p["w"].sum()
             scale += abs(cfg["q"][s]) * p["w"].sum()
-            idx = rng.choice(p["x"].size, 20_000, replace=False)
+            idx = rng.choice(p["x"].size, 200_000, replace=False)
             sample[s] = {k: np.ascontiguousarray(v[idx]) for k, v in p.items()}
             del p, leaf, x0, y0, side
         # the deposit: sum over leaves of rho * area is the total charge
@@ -75,6 +78,7 @@ def test_streamer_full_size_properties_and_sampled_step():
             del a
     sim = O.Sim(cfg, M)
     sim.step_count = step
+    n_all, disagree = 0, 0
     for s in (0, 1):
         smp = sample[s]
         n = smp["x"].size
@@ -85,21 +89,42 @@ def test_streamer_full_size_properties_and_sampled_step():
         new_leaf = np.empty(n, np.int64)
         spawn = np.zeros(n, np.uint8)
         sv, svi = np.zeros(3 * n), np.zeros(3 * n)
+        dec = np.empty(4 * n)
         pp = sim.push_params(s)
         O.lib().or_push_mcc(C.byref(M._c), C.byref(pp), O._ptr(E), n, O._ptr(x), O._ptr(y), O._ptr(vx), O._ptr(vy),
                             O._ptr(vz), O._ptr(ids), O._ptr(leaf), O._ptr(new_leaf), O._ptr(spawn), O._ptr(sv),
-                            O._ptr(svi))
+                            O._ptr(svi), O._ptr(dec))
+        U0, P, U1st, siz = dec.reshape(n, 4).T
+        # rounding margin of the collision decisions (FP32 against FP64 arithmetic)
+        margin = (U0 >= 0) & (np.abs(U0 - P) <= 1e-6 * np.maximum(P, 1e-30))
+        if s == 0:
+            margin |= (U0 >= 0) & (U0 < P) & (np.abs(U1st - siz) <= 1e-6 * (cfg["sigma_el"] + siz))
         a = after[s]
         pos = np.minimum(np.searchsorted(a["id"], ids), a["id"].size - 1)
         found = a["id"][pos] == ids
         alive = new_leaf >= 0
-        assert (found == alive).mean() >= 0.9995  # absorbed at a wall exactly when the oracle absorbs
+        # ... and of the new position: within 1e-6 of the leaf size of a face (the oracle's
+        # leaf, or the GPU's), which includes the walls
+        def near_face(xx, yy, lf):
+            ok = lf >= 0
+            l2 = np.where(ok, lf, 0)
+            hl = M.s[l2] * hf
+            u = (xx - M.ix[l2] * hf) / hl
+            v = (yy - M.iy[l2] * hf) / hl
+            return ok & (np.minimum(np.minimum(u, 1 - u), np.minimum(v, 1 - v)) <= 1e-6)
+        lg = np.where(found, a["leaf"][pos].astype(np.int64), -1)
+        margin |= near_face(x, y, new_leaf) | near_face(a["x"][pos], a["y"][pos], lg)
         both = found & alive
         g = pos[both]
         assert both.sum() > 0.9 * n
         dx = np.maximum(np.abs(a["x"][g] - x[both]), np.abs(a["y"][g] - y[both]))
-        assert np.quantile(dx, 0.999) <= 1e-5 * hf
         dv = np.sqrt((a["vx"][g] - vx[both]) ** 2 + (a["vy"][g] - vy[both]) ** 2 + (a["vz"][g] - vz[both]) ** 2)
         vmag = np.sqrt(vx[both] ** 2 + vy[both] ** 2 + vz[both] ** 2)
-        assert (dv <= 1e-5 * np.maximum(vmag, 1e-3 * vmag.max())).mean() >= 0.999
-        assert (a["leaf"][g].astype(np.int64) == new_leaf[both]).mean() >= 0.9999
+        bad = np.zeros(n, bool)
+        bad[both] = ((dx > 1e-5 * hf) | (dv > 1e-5 * np.maximum(vmag, 1e-3 * vmag.max())) |
+                     (a["leaf"][g].astype(np.int64) != new_leaf[both]))
+        bad |= found != alive                          # absorbed by one side only
+        assert not np.any(bad & ~margin), (s, np.nonzero(bad & ~margin)[0][:10])
+        disagree += int(np.count_nonzero(bad))
+        n_all += n
+    assert disagree <= 1e-5 * n_all, disagree

@@ -21,16 +21,15 @@ def _built():
     O.build()
 
 
-def _beam_case(precision, ionize, seed=11):
+def _beam_case(precision, ionize, seed=11, nb=300):
     """8 x 2 leaves of 1 mm, absorbing walls at x = 0 and 8 mm (0 V), periodic in y.
-    300 electrons at 100 eV moving +x by 1 mm per step from x in [1.2, 1.8] mm, on top of 5
+    nb electrons at 100 eV moving +x by 1 mm per step from x in [1.2, 1.8] mm, on top of 5
     electrons and 5 ions per leaf at rest-ish; with ionization, most beam electrons spawn a
     pair per step."""
     rng = np.random.default_rng(seed)
     h = 1e-3
     v = math.sqrt(2.0 * 100.0 * W.QE / W.ME)
     dt = h / v
-    nb = 300
     xb = (1.2 + 0.6 * rng.random(nb)) * h
     yb = (0.05 + 1.9 * rng.random(nb)) * h
     nbg = 5 * 16
@@ -115,3 +114,17 @@ def test_beam_overflow_with_ionization_spawn_ids_fp64():
     assert g[1]["id"].size - n0[1] > 150, "the beam must spawn many pairs"
     assert np.unique(np.concatenate([g[0]["id"], g[1]["id"]])).size == g[0]["id"].size + g[1]["id"].size
     assert stats[1][1] >= 2  # the spawned ions overflowed their leaves too
+
+
+@pytest.mark.parametrize("nb", [2_000, 40_000])
+def test_long_entering_regions_and_long_loaded_lists_keep_the_oracle_order(nb):
+    """A beam of nb electrons loads into two leaves and crosses into the next two in one step:
+    about nb / 2 records per leaf.  2,000 takes the per-leaf block sort of entering regions
+    longer than one warp's (512); 40,000 takes, at the load and in the step, the rank pass
+    of regions longer than one block's shared-memory sort (16,384).  Cell-list order, leaves
+    and values against the oracle, FP64."""
+    cfg, mesh, parts = _beam_case(W.FP64, ionize=False, nb=nb)
+    res, stats = _run_pair(cfg, mesh, parts, 2)
+    _check(res, W.FP64)
+    g, _ = res[0]
+    assert np.bincount(g[0]["leaf"].astype(np.int64), minlength=16).max() >= 0.45 * nb

@@ -187,8 +187,50 @@ def test_one_step_fp64_bit_exact_lists_with_ionization():
             assert np.abs(g[s][k] - ref).max() <= 1e-12 * scale, (s, k)
 
 
-def test_one_step_fp32_within_tolerance():
-    cfg, mesh, parts = _ccp_small(W.FP32, nx=32, ny=8, ppc=40, te=30.0, ng=3e21)
+def _dyadic_ccp(nx=64, ny=8, ppc=200, seed=7, te=30.0, ng=3e21):
+    """The capacitively coupled discharge on cells of side 2^-13 m with positions, velocities
+    and weights that the FP32 state holds exactly (float32 offsets in their cell, float32
+    velocities and weights), so that the FP32 path and the FP64 oracle start from identical
+    values."""
+    cfg, mesh, parts = W.ccp(nx=nx, ny=ny, ppc=ppc, seed=seed, precision=W.FP32, te=te, ng=ng)
+    h_old, h = mesh["h0"], 2.0 ** -13
+    mesh = dict(mesh, h0=h)
+    f32 = np.float32
+    for p in parts.values():
+        for key, n in (("x", nx), ("y", ny)):
+            t = p[key] / h_old
+            cell = np.clip(np.floor(t), 0, n - 1)
+            frac = np.minimum((t - cell).astype(f32), np.nextafter(f32(1), f32(0)))
+            p[key] = (cell + frac.astype(np.float64)) * h
+        for key in ("vx", "vy", "vz", "w"):
+            p[key] = p[key].astype(f32).astype(np.float64)
+    cfg["mg_rel_tol"] = 1e-11
+    return cfg, mesh, parts
+
+
+def _decision_margin(sim, s, cfg):
+    """Ids whose collision decision lies inside the rounding margin: |U0 - P| <= 1e-6 P, or
+    (electrons that collide) |U1 sigma_T - sigma_iz| <= 1e-6 sigma_T."""
+    ids, dec = sim.last_decisions[s]
+    U0, P, U1st, siz = dec.T
+    tested = U0 >= 0
+    near = tested & (np.abs(U0 - P) <= 1e-6 * np.maximum(P, 1e-30))
+    if s == 0:
+        st = cfg["sigma_el"] + siz
+        near |= tested & (U0 < P) & (np.abs(U1st - siz) <= 1e-6 * st)
+    return set(ids[near].tolist())
+
+
+def test_one_step_fp32_decisions_and_leaves_bit_exact_outside_the_rounding_margin():
+    """FP32 path against the FP64 oracle for one step with ionization from identical state
+    (the benchmark spec: RNG collision decisions and leaves bit-exact given identical positions).  A
+    particle may differ only when its decision lies inside the rounding margin (|U0 - P| <=
+    1e-6 P, or the process choice within 1e-6 of its threshold) or its new position lies
+    within 1e-6 of its leaf size of a face; such differences number at most 1e-5 N.  Every
+    other particle has the oracle's leaf, its position within 1e-5 h, its direction within
+    2e-5 and its kinetic energy within 2e-5 of the larger of its energy and (electrons) the
+    ionization threshold, and the spawned pairs (ids, leaves) are the oracle's."""
+    cfg, mesh, parts = _dyadic_ccp()
     cfg["dt"] *= 4
     sim = _oracle(cfg, mesh, parts)
     sim.step(1)
@@ -196,25 +238,60 @@ def test_one_step_fp32_within_tolerance():
         ctx.step(1)
         g = [ctx.particles(s) for s in (0, 1)]
     h = mesh["h0"]
+    M = sim.mesh
+    N = sum(p["x"].size for p in parts.values())
+    n_loaded = N  # ids 0 .. N - 1 were loaded; spawned ids follow
+    disagree, margin_hits, compared = 0, 0, 0
+    n_spawn = sim.species[1].n - parts[1]["x"].size
+    assert n_spawn > 100, "the case must exercise ionization"
     for s in (0, 1):
         sp = sim.species[s]
+        dec_margin = _decision_margin(sim, s, cfg)
+        # the oracle's new offsets in its leaf: near a face within 1e-6 of the leaf size
+        hl = M.s[sp.leaf] * M.hf
+        u = (sp.x - M.ix[sp.leaf] * M.hf) / hl
+        v = (sp.y - M.iy[sp.leaf] * M.hf) / hl
+        near_face = (np.minimum(np.minimum(u, 1 - u), np.minimum(v, 1 - v)) <= 1e-6)
+        face_margin = set(sp.id[near_face].tolist())
         a = _by_id(g[s])
+        lg = a["leaf"].astype(np.int64)   # the same near-face test on the GPU's positions
+        hg = M.s[lg] * M.hf
+        ug = (a["x"] - M.ix[lg] * M.hf) / hg
+        vg = (a["y"] - M.iy[lg] * M.hf) / hg
+        face_margin |= set(a["id"][np.minimum(np.minimum(ug, 1 - ug), np.minimum(vg, 1 - vg)) <= 1e-6].tolist())
+        margin = dec_margin | face_margin
         o = np.argsort(sp.id)
-        ids_o = sp.id[o]
-        common = np.intersect1d(a["id"], ids_o)
-        # particles whose collision decision flipped within FP32 rounding are the only
-        # allowed differences in the population
-        assert common.size >= 0.999 * max(a["id"].size, ids_o.size)
-        ia = np.searchsorted(a["id"], common); io = o[np.searchsorted(ids_o, common)]
-        dx = np.abs(a["x"][ia] - sp.x[io])
-        assert np.quantile(dx, 0.999) <= 1e-5 * h
-        v_o = np.sqrt(sp.vx[io] ** 2 + sp.vy[io] ** 2 + sp.vz[io] ** 2)
-        v_g = np.sqrt(a["vx"][ia] ** 2 + a["vy"][ia] ** 2 + a["vz"][ia] ** 2)
-        close = np.abs(v_g - v_o) <= 1e-5 * v_o.max()
-        assert close.mean() >= 0.999
-        # leaf agreement except at faces (FP32 offsets vs FP64 absolute positions)
+        oid = sp.id[o]
+        # populations: ids present in one and not the other are disagreements
+        only = np.setxor1d(a["id"], oid)
+        parents = only[only < n_loaded]
+        assert set(parents.tolist()) <= margin, "a particle was absorbed or spawned outside the margin"
+        disagree += parents.size
+        if s == 0:
+            e_dec_margin = dec_margin
+        if not e_dec_margin:  # no ionization decision inside the margin: the same spawned pairs
+            assert only.size == 0, (s, only[:10])
+        common = np.intersect1d(a["id"], oid)
+        ia = np.searchsorted(a["id"], common); io = o[np.searchsorted(oid, common)]
+        # velocities as kinetic energy and direction: an ionization shares eps - eps_th, whose
+        # FP32 rounding is a fraction of eps_th's, not of the (possibly tiny) share's
+        vo = np.stack([sp.vx[io], sp.vy[io], sp.vz[io]], 1)
+        vg = np.stack([a["vx"][ia], a["vy"][ia], a["vz"][ia]], 1)
+        eo, eg = (vo ** 2).sum(1), (vg ** 2).sum(1)
+        e_scale = np.maximum(eo, 2 * cfg["eps_th_ev"] * W.QE / cfg["m"][s] if s == 0 else 0.0)
+        do = vo / np.sqrt(np.maximum(eo, 1e-300))[:, None]
+        dg = vg / np.sqrt(np.maximum(eg, 1e-300))[:, None]
+        bad_v = (np.abs(eg - eo) > 2e-5 * e_scale) | (np.abs(dg - do).max(1) > 2e-5)
+        dx = np.maximum(np.abs(a["x"][ia] - sp.x[io]), np.abs(a["y"][ia] - sp.y[io]))
         same_leaf = a["leaf"][ia].astype(np.int64) == sp.leaf[io]
-        assert same_leaf.mean() >= 0.9999
+        bad = bad_v | (dx > 1e-5 * h) | ~same_leaf
+        in_margin = np.isin(common, np.array(sorted(margin), dtype=common.dtype))
+        assert not np.any(bad & ~in_margin), (s, common[bad & ~in_margin][:10])
+        disagree += int(np.count_nonzero(bad))
+        margin_hits += len(margin)
+        compared += common.size
+    assert compared > 0.99 * N
+    assert disagree <= 1e-5 * N, (disagree, margin_hits)
 
 
 @pytest.mark.parametrize("amr", [False, True])

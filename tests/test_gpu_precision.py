@@ -1,0 +1,197 @@
+"""Precision study of the streamer at 2e8 particles (FP32 cell-relative push and compensated
+deposit; multigrid with FP32 smoothing, FP64 residual, coarsest solve and iterative refinement
+to a 1e-10 relative residual) against FP64.
+
+The state: the streamer channel of 2e8 macro-particles (1e8 electrons, 1e8 ions) refined onto
+the particles by count (field criterion off, so that both precisions build the same tree) with
+particles held in the band 8-1024 per leaf around 512 -- the paper holds ~500-1000 particles
+per cell while the population grows (§4.3).
+
+1. Full size, FP32 against FP64 on the GPU: the same host arrays load into both contexts,
+   which adapt to the same tree and then step once with collisions and ionization.
+2. A subset of ~1e6 particles (every particle whose hashed id is 0 modulo ceil(N / 1e6), the
+   weights scaled by N / N_sub) on the adapted tree: the FP32 GPU path against the FP64 CPU
+   oracle, at load and after one step.
+
+Asserted: fields (phi, corner E) within 1e-5 relative (L2 over leaves) at load and after the
+step; densities n_e, n_i within 1e-6 at load; after the step, particles may change their leaf
+differently only within FP32 rounding of a face (at most 1e-5 of the population) and the
+densities of every other leaf agree within 1e-6.  The error table is printed (pytest -s).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1604_07713_gb300 as G
+from paper_1604_07713_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N_FULL = 200_000_000
+N_SUB = 1_000_000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    G.build()
+    O.build()
+
+
+def _rel(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a, float) - b)) / (nb if nb > 0 else 1.0)
+
+
+def _fmix64(x):
+    """MurmurHash3's 64-bit finalizer (Appleby): a published bijective mixing of the id."""
+    x = x.astype(np.uint64)
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(0xFF51AFD7ED558CCD)
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(0xC4CEB9FE1A85EC53)
+    x ^= x >> np.uint64(33)
+    return x
+
+
+def _config(precision):
+    cfg, mesh, parts = W.streamer_snapshot(n_particles=N_FULL, precision=precision)
+    cfg.update(ppc_target=512, ppc_min=8, ppc_max=1024, refine_count=1024, coarsen_count=256,
+               e_ref=1e30, mg_rel_tol=1e-10, mg_max_cycles=60)
+    return cfg, mesh, parts
+
+
+def _setup(ctx, mesh):
+    for _ in range(mesh["lmax"] + 1):
+        ctx.compute_fields(allow_notconv=True)
+        ctx.adapt(G.PIC_ADAPT_MESH)
+    ctx.compute_fields(allow_notconv=True)
+    ctx.adapt()
+
+
+def _densities(ctx):
+    """n_e, n_i per leaf of the current state (one diagnostics sample: the step's start)."""
+    ctx.diag_enable(1, 1.0)
+    ctx.step(1)
+    out = ctx.fields(G.PIC_FIELD_AVG_NE), ctx.fields(G.PIC_FIELD_AVG_NI)
+    ctx.diag_enable(0, 1.0)
+    return out
+
+
+def _run_full(cfg, mesh, parts):
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s in (0, 1):
+            ctx.load(s, **parts[s])
+        _setup(ctx, mesh)
+        tree = ctx.mesh()
+        c = ctx.counts()
+        load = dict(phi=None, counts=[ctx.fields(G.PIC_FIELD_COUNT_E), ctx.fields(G.PIC_FIELD_COUNT_I)])
+        ctx.compute_fields()
+        load.update(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1),
+                    rho=ctx.fields(G.PIC_FIELD_RHO))
+        ctx.step(1)                                   # collisions, ionization, list update
+        after = dict(counts=[ctx.fields(G.PIC_FIELD_COUNT_E), ctx.fields(G.PIC_FIELD_COUNT_I)])
+        after["ne"], after["ni"] = _densities(ctx)    # samples the state after the step
+        after.update(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1))
+        return tree, c["n_e"] + c["n_i"], load, after
+
+
+def test_precision_study_2e8_streamer_fp32_against_fp64():
+    cfg32, mesh, parts = _config(W.FP32)
+    cfg64 = dict(cfg32, precision=W.FP64)
+    tree32, n32, load32, after32 = _run_full(cfg32, mesh, parts)
+    tree64, n64, load64, after64 = _run_full(cfg64, mesh, parts)
+    # the same tree and the same lists (counts per leaf) after adaptation and split / merge
+    assert all(np.array_equal(a, b) for a, b in zip(tree32, tree64))
+    assert n32 == n64 and n32 >= 1.9e8, n32
+    for a, b in zip(load32["counts"], load64["counts"]):
+        assert np.array_equal(a, b)
+    table = {"full_fp32_vs_fp64": {"particles": int(n32), "leaves": int(tree32[0].size)}}
+    t = table["full_fp32_vs_fp64"]
+    for k in ("phi", "E", "rho"):
+        t[f"{k}_load"] = _rel(load32[k], load64[k])
+    for k in ("phi", "E", "ne", "ni"):
+        t[f"{k}_step"] = _rel(after32[k], after64[k])
+    diff = [(a != b) for a, b in zip(after32["counts"], after64["counts"])]
+    t["leaves_with_other_counts"] = [int(d.sum()) for d in diff]
+    same = ~(diff[0] | diff[1])
+    t["ne_step_same_count_leaves"] = _rel(after32["ne"][same], after64["ne"][same])
+    t["ni_step_same_count_leaves"] = _rel(after32["ni"][same], after64["ni"][same])
+    assert t["phi_load"] < 1e-5 and t["E_load"] < 1e-5 and t["rho_load"] < 1e-6
+    assert t["phi_step"] < 1e-5 and t["E_step"] < 1e-5
+    assert sum(t["leaves_with_other_counts"]) <= 2e-5 * n32
+    assert t["ne_step_same_count_leaves"] < 1e-6 and t["ni_step_same_count_leaves"] < 1e-6
+
+    # --- the ~1e6 subset against the FP64 oracle, on the adapted tree -----------------------
+    k = int(np.ceil(N_FULL / N_SUB))
+    sub = {}
+    id0 = 0
+    for s in (0, 1):
+        n = parts[s]["x"].size
+        ids = np.arange(id0, id0 + n, dtype=np.uint64)   # the load's ids: 0.. for electrons, then ions
+        id0 += n
+        keep = (_fmix64(ids) % np.uint64(k)) == 0
+        sub[s] = {key: np.ascontiguousarray(v[keep]) for key, v in parts[s].items()}
+        sub[s]["w"] = sub[s]["w"] * (N_FULL / (keep.sum() * 2))
+        sub[s]["ids"] = ids[keep]
+    del parts
+    n_sub = sum(sub[s]["x"].size for s in (0, 1))
+    r, m, lv = tree32
+    smesh = dict(mesh, root=r, morton=m, level=lv)
+    M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], mesh["lmax"], cfg32["bc_x"], cfg32["bc_y"], r, lv, m)
+    sim = O.Sim(cfg32, M)
+    for s in (0, 1):
+        sim.load(s, **sub[s])
+    rho_o, phi_o, E_o = sim.fields()
+    with G.Context(cfg32) as ctx:
+        ctx.set_mesh_dict(smesh)
+        for s in (0, 1):
+            ctx.load(s, **sub[s])
+        ctx.compute_fields()
+        g_load = dict(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1),
+                      rho=ctx.fields(G.PIC_FIELD_RHO))
+        ctx.step(1)
+        gp = [ctx.particles(s) for s in (0, 1)]
+        ctx.compute_fields()
+        g_after = dict(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1))
+    sim.step(1)
+    _, phi_o2, E_o2 = sim.fields()
+    u = {"particles": int(n_sub), "leaves": int(M.nleaf)}
+    u["phi_load"] = _rel(g_load["phi"], phi_o)
+    u["E_load"] = _rel(g_load["E"], E_o.reshape(-1))
+    u["rho_load"] = _rel(g_load["rho"], rho_o)
+    u["phi_step"] = _rel(g_after["phi"], phi_o2)
+    u["E_step"] = _rel(g_after["E"], E_o2.reshape(-1))
+    # densities after the step, leaf by leaf; leaves holding a particle within 1e-6 of a face
+    # (FP32 rounding of the new offset) are left out, and those particles are counted
+    area = M.area()
+    hf = M.hf
+    moved_other, masked = 0, np.zeros(M.nleaf, bool)
+    dens = {}
+    for s in (0, 1):
+        sp = sim.species[s]
+        for side, (lf, x, y) in (("o", (sp.leaf, sp.x, sp.y)),
+                                 ("g", (gp[s]["leaf"].astype(np.int64), gp[s]["x"], gp[s]["y"]))):
+            hl = M.s[lf] * hf
+            uu = (x - M.ix[lf] * hf) / hl
+            vv = (y - M.iy[lf] * hf) / hl
+            near = np.minimum(np.minimum(uu, 1 - uu), np.minimum(vv, 1 - vv)) <= 1e-6
+            masked[lf[near]] = True
+        # the same ids on the same leaves, except near faces
+        ia, io = np.argsort(gp[s]["id"]), np.argsort(sp.id)
+        common, ca, co = np.intersect1d(gp[s]["id"][ia], sp.id[io], return_indices=True)
+        moved_other += int(np.count_nonzero(gp[s]["leaf"][ia][ca].astype(np.int64) != sp.leaf[io][co]))
+        moved_other += int(gp[s]["id"].size + sp.n - 2 * common.size)
+        dens[s] = (np.bincount(gp[s]["leaf"].astype(np.int64), weights=gp[s]["w"], minlength=M.nleaf) / area,
+                   np.bincount(sp.leaf, weights=sp.w, minlength=M.nleaf) / area)
+    keep = ~masked
+    u["leaf_or_population_differences"] = moved_other
+    u["masked_leaves"] = int(masked.sum())
+    u["ne_step"] = _rel(dens[0][0][keep], dens[0][1][keep])
+    u["ni_step"] = _rel(dens[1][0][keep], dens[1][1][keep])
+    table["subset_fp32_gpu_vs_fp64_oracle"] = u
+    print("\nprecision study:", table)
+    assert u["phi_load"] < 1e-5 and u["E_load"] < 1e-5 and u["rho_load"] < 1e-6
+    assert u["phi_step"] < 1e-5 and u["E_step"] < 1e-5
+    assert moved_other <= 1e-5 * n_sub + 2
+    assert u["ne_step"] < 1e-6 and u["ni_step"] < 1e-6

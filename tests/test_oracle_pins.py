@@ -617,3 +617,97 @@ def test_node_e_and_cell_emag_converge_for_a_smooth_potential_on_amr():
     order = np.log2(e[:-1] / e[1:])
     assert order[:, 0].min() >= 0.95 and order[:, 2].min() >= 0.95, order
     assert order[:, 1].min() >= 1.3 and order[:, 3].min() >= 1.3, order
+
+
+# --------------------------------------------------------------------------------------
+# Time averages (§3.3 RF-cycle averages of n_e, n_i, T_e, phi and the EEDF; §3.1 reset)
+# --------------------------------------------------------------------------------------
+def _static_sim(n, te_ev, seed=3, n_bins=64, eps_max=40.0):
+    """Electrons and ions that do not move (zero time step) on a uniform Dirichlet mesh with a
+    fixed wall potential: every step samples the same state."""
+    cfg = W.base_config(precision=W.FP64, n_species=2, dt=1e-30, eps0=W.EPS0, q=[-W.QE, W.QE],
+                        m=[W.ME, 4 * W.AMU], qe=W.QE, bc_x=W.BC_DIRICHLET, bc_y=W.BC_NEUMANN,
+                        phi_right=5.0)
+    M = O.Mesh(8, 4, 0.25, 0, O.BC_DIRICHLET, O.BC_NEUMANN)
+    sim = O.Sim(cfg, M)
+    rng = np.random.default_rng(seed)
+    vt = np.sqrt(te_ev * W.QE / W.ME)
+    for s in (0, 1):
+        x = rng.random(n) * M.lx; y = rng.random(n) * M.ly
+        v = rng.standard_normal((3, n)) * (vt if s == 0 else 0.0)
+        sim.load(s, x, y, v[0], v[1], v[2], rng.random(n) + 0.5)
+    sim.diag_enable(n_bins, eps_max)
+    return sim
+
+
+def test_time_averages_of_a_static_state_equal_the_state():
+    """A state that does not change (zero time step): the averages over 5 steps equal the
+    instantaneous densities per leaf, the potential of the solve, and T_e = (2/3) <eps> of each
+    leaf's electrons; counts in the energy histogram are exact (5 x the weights per bin).
+    Fails for: a missing division by the sample count or by the leaf area, the 2/3, or a
+    sample taken twice per step."""
+    sim = _static_sim(4000, 2.0)
+    sim.step(5)
+    d = sim.diag_fields()
+    e, i = sim.species
+    area = sim.mesh.area()
+    ne = np.bincount(e.leaf, weights=e.w, minlength=sim.mesh.nleaf) / area
+    ni = np.bincount(i.leaf, weights=i.w, minlength=sim.mesh.nleaf) / area
+    eps = 0.5 * W.ME * (e.vx ** 2 + e.vy ** 2 + e.vz ** 2) / W.QE
+    te = (2.0 / 3.0) * np.bincount(e.leaf, weights=e.w * eps, minlength=sim.mesh.nleaf) / (ne * area)
+    assert np.allclose(d["ne"], ne, rtol=1e-13) and np.allclose(d["ni"], ni, rtol=1e-13)
+    assert np.allclose(d["te"], te, rtol=1e-13)
+    assert np.allclose(d["phi"], sim.phi, rtol=1e-13, atol=1e-13)
+    f, k = sim.diag_eedf()
+    assert k == 5
+    counts = np.bincount(np.floor(eps / (40.0 / 64)).astype(int)[eps < 40.0],
+                         weights=e.w[eps < 40.0], minlength=64)
+    assert np.allclose(f * 5 * counts.sum() * (40.0 / 64), 5 * counts, rtol=1e-12)
+
+
+def test_eedf_of_a_maxwellian_is_the_maxwell_distribution_and_te_its_temperature():
+    """Electrons from a Maxwellian at T (isotropic, no drift): the EEDF is
+    f(eps) = 2 sqrt(eps / pi) T^(-3/2) exp(-eps / T) per eV (chi-square over bins with >= 20
+    expected counts) and the averaged T_e = (2/3) <eps> = T within sampling error.  Fails
+    for: a histogram of speeds instead of energies, a missing factor 1/2 in eps, bins off by
+    one."""
+    from scipy import stats
+    T = 3.0
+    sim = _static_sim(40000, T, n_bins=40, eps_max=20.0)
+    e = sim.species[0]
+    e.w[:] = 1.0   # equal weights: the histogram is a plain count
+    sim.step(1)
+    f, k = sim.diag_eedf()
+    edges = np.linspace(0.0, 20.0, 41)
+    cdf = stats.gamma(1.5, scale=T).cdf(edges)       # eps / T ~ Gamma(3/2) for a 3D Maxwellian
+    p = np.diff(cdf) / (cdf[-1] - cdf[0])
+    n_in = int(np.count_nonzero(0.5 * W.ME * (e.vx ** 2 + e.vy ** 2 + e.vz ** 2) / W.QE < 20.0))
+    obs = f * (20.0 / 40) * n_in
+    exp = p * n_in
+    ok = exp >= 20
+    chi2 = np.sum((obs[ok] - exp[ok]) ** 2 / exp[ok])
+    assert stats.chi2(ok.sum() - 1).sf(chi2) > 1e-4
+    d = sim.diag_fields()
+    te_all = (2.0 / 3.0) * np.sum(e.w * 0.5 * W.ME * (e.vx ** 2 + e.vy ** 2 + e.vz ** 2) / W.QE) / e.w.sum()
+    assert abs(te_all / T - 1) < 5 * np.sqrt(2.0 / (3 * e.n))
+    assert np.all(d["te"][d["ne"] > 0] > 0)
+
+
+def test_time_averages_restart_when_the_grid_changes():
+    """§3.1: statistics counters are reset when the grid changes; an adaptation that changes
+    no leaf keeps them."""
+    sim = _static_sim(2000, 2.0)
+    sim.cfg.update(max_level=1, refine_count=10 ** 9, coarsen_count=-1, e_ref=1e30)
+    sim.step(3)
+    sim.adapt(mesh=True, particles=False)
+    assert sim.diag["samples"] == 3
+    sim.cfg.update(refine_count=10)
+    M = O.Mesh(8, 4, 0.25, 1, O.BC_DIRICHLET, O.BC_NEUMANN)
+    sim2 = O.Sim(dict(sim.cfg), M)
+    for s in (0, 1):
+        sp = sim.species[s]
+        sim2.load(s, sp.x, sp.y, sp.vx, sp.vy, sp.vz, sp.w)
+    sim2.diag_enable(64, 40.0)
+    sim2.step(3)
+    st = sim2.adapt(mesh=True, particles=False)["mesh"]
+    assert st["refined"] > 0 and sim2.diag["samples"] == 0 and sim2.diag["we"].size == sim2.mesh.nleaf
