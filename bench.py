@@ -35,7 +35,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "ccp-512x16-ppc100-fp32"
 METRIC = "particle-steps/s"
 WORKLOADS = ("ccp", "streamer", "ensemble")
 
@@ -58,7 +57,7 @@ def _workload(seed, name="ccp", n_particles=50_000_000, precision="fp32"):
     return cfg, mesh, parts
 
 
-def _config_json(ws, name="ccp", extra=None):
+def _config_json(ws, name="ccp", extra=None, precision="fp32"):
     if name == "ensemble":
         d = {"workload": "ccp-ensemble-256-fp32", "instances": 256,
              "cells": "per instance 64-512 x 16 uniform leaves (multiples of 16 in x)",
@@ -67,13 +66,13 @@ def _config_json(ws, name="ccp", extra=None):
              "l2": "inputs larger than L2 (particle state >> 129 MB)", "parallelism": f"replicas x{ws}",
              "poisson_rel_tol": 1e-8}
     elif name == "streamer":
-        d = {"workload": "streamer-amr-128x128-l4-fp32", "cells": "adaptive quadtree, 128x128 roots, up to 4 levels",
+        d = {"workload": f"streamer-amr-128x128-l4-{precision}", "cells": "adaptive quadtree, 128x128 roots, up to 4 levels",
              "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
              "adapt": "pic_adapt (mesh + split/merge) every 10 steps inside the timed region",
              "l2": "inputs larger than L2 (particle state >> 129 MB)", "parallelism": f"replicas x{ws}",
              "poisson_rel_tol": 1e-8}
     else:
-        d = {"workload": WORKLOAD, "cells": "512x16 uniform quadtree leaves", "particles_per_species": 819200,
+        d = {"workload": f"ccp-512x16-ppc100-{precision}", "cells": "512x16 uniform quadtree leaves", "particles_per_species": 819200,
              "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
              "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
              "poisson_rel_tol": 1e-8}
@@ -191,8 +190,45 @@ def _oracle_rate(sim, steps, adapt_every=0):
 def _sample_text(name, steps, t):
     if name == "streamer":
         return (f"{steps} steps (adaptation every 10) of the streamer workload at {ORACLE_STREAMER_PARTICLES:,} "
-                f"particles (the GPU runs 5e7) on a mesh the oracle adapted itself, FP64, single thread, {t:.1f} s")
-    return f"{steps} steps of the full workload (2 x 819,200 particles), FP64 oracle, single thread, {t:.1f} s"
+                f"particles (the GPU runs 5e7) on a mesh the oracle adapted itself, FP64, one thread, {t:.1f} s")
+    return f"{steps} steps of the full workload (2 x 819,200 particles), FP64 oracle, one thread, {t:.1f} s"
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(seed, name, steps, barrier, queue):
+    """One core's share of the all-core baseline: its own bounded sample, timed after every
+    worker has finished its setup."""
+    sim = _oracle_sim(seed, name)
+    sim.step(1)
+    barrier.wait()
+    queue.put(_oracle_rate(sim, steps, 10 if name == "streamer" else 0))
+
+
+def cpu_baseline_all_cores(seed, steps, name):
+    """The oracle as it stands (one thread per process) on every host core at once: one
+    independent bounded sample per core (seeds seed + k), started together; the job's rate is
+    the sum of the processes' rates.  Processes are spawned, never forked after CUDA use."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(seed + k, name, steps, barrier, queue)) for k in range(n)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    return sum(r for r, _ in res), max(t for _, t in res), n
 
 
 def cpu_baseline(seed, steps=12, name="ccp"):
@@ -210,7 +246,16 @@ def cpu_baseline(seed, steps=12, name="ccp"):
     sim = _oracle_sim(seed, name)
     sim.step(1)  # warm-up (imports, first solve)
     rate, t = _oracle_rate(sim, steps, 10 if name == "streamer" else 0)
-    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": _sample_text(name, steps, t)}
+    del sim
+    single = {"value": rate, "cores": 1, "sample": _sample_text(name, steps, t)}
+    try:
+        rate_all, t_all, n = cpu_baseline_all_cores(seed, steps, name)
+    except Exception as e:  # the single-thread figure stands alone
+        return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
+                "sample": _sample_text(name, steps, t), "all_cores_error": str(e)[:200]}
+    return {"value": rate_all, "unit": METRIC, "cores": n, "kind": "oracle", "cpu_model": _cpu_model(),
+            "nproc": n, "sample": f"{n} processes at once, each: " + _sample_text(name, steps, t_all),
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -227,16 +272,15 @@ def run_reference(args):
                 "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
-    sim = _oracle_sim(args.seed, args.workload)
-    for _ in range(args.warmup):
-        sim.step(1)
-    rate, t = _oracle_rate(sim, args.steps, 10 if args.workload == "streamer" else 0)
+    # every host core runs its own bounded sample of the workload (warm-up steps included in
+    # each process's setup), started together; the rate is the sum over the processes
+    rate, t, n = cpu_baseline_all_cores(args.seed, args.steps, args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config_json(1, args.workload),
-            "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": _sample_text(args.workload, args.steps, t)},
+            "data": "synthetic", "config": _config_json(1, args.workload, precision=args.precision),
+            "cpu_baseline": {"value": rate, "unit": METRIC, "cores": n, "kind": "oracle", "cpu_model": _cpu_model(),
+                             "sample": f"{n} processes at once, each: " + _sample_text(args.workload, args.steps, t)},
             "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -388,10 +432,11 @@ def run_gpu(args):
     final = counts_all()
 
     # Roofline of the fused push (k_push, both species, lists updated in place): algorithmic
-    # bytes = the record (u, v, vx, vy, vz, w, id) read once and its five changed words
-    # (u, v, vx, vy, vz) written once per particle, plus per leaf and species the 8 corner
-    # field values, the list bounds (start, end) and the staying count and weight sum written.
-    # The extra words of records that change slot (w, id, order key) are not counted.
+    # bytes = the record (u, v, vx, vy, vz, w in the state precision, id u32) read once and its
+    # five changed words (u, v, vx, vy, vz) written once per particle -- 11 rs + 4 bytes --
+    # plus per leaf and species the 8 corner field values, the list bounds (start, end) and
+    # the staying count and weight sum written.  The extra words of records that change slot
+    # (w, id, order key) are not counted.
     rs = 8 if args.precision == "fp64" else 4
     move_ms, move_launches = phases["move"]
     push_label = f"k_push<{'double' if rs == 8 else 'float'}> in-place push (both species)"
@@ -401,7 +446,7 @@ def run_gpu(args):
         move_ms = phases["graph"][0]
         push_label = "whole step (graph replay; push bytes over step time: a lower bound)"
     move_s = move_ms * 1e-3
-    alg_bytes = 12 * rs * particle_steps + leaf_steps * 2 * (10 * rs + 12)
+    alg_bytes = (11 * rs + 4) * particle_steps + leaf_steps * 2 * (10 * rs + 12)
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
     tr = _traffic_record(name) if args.precision == "fp32" else None
     tot_ms = sum(v[0] for v in phases.values())
@@ -412,6 +457,19 @@ def run_gpu(args):
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_step": alg_bytes / args.steps,
                 "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items() if v[1]}}
+    # The whole particle cycle (deposit, corner field, list preparation, push, scans and list
+    # repairs, per-leaf sorts): the push's algorithmic bytes plus the corner field written and
+    # the deposit's per-leaf charge, over the summed CUDA-event time of those phases.  Records
+    # that change leaf are written to free slots and sorted into place, traffic that is not
+    # counted here, so this fraction is a lower bound.
+    cycle_phases = ("deposit", "node_e", "lists", "scan", "move", "sort")
+    cycle_ms = sum(phases[k][0] for k in cycle_phases if k in phases)
+    cycle_bytes = alg_bytes + leaf_steps * (8 * rs + 8)
+    if cycle_ms > 0.0 and phases.get("graph", (0.0, 0))[0] == 0.0:
+        ca = cycle_bytes / (cycle_ms * 1e-3) / 1e9
+        roofline["particle_cycle"] = {"achieved": ca, "frac": ca / hbm_peak, "unit": "GB/s",
+                                      "phases": list(cycle_phases), "ms_per_step": cycle_ms / args.steps,
+                                      "alg_bytes_per_step": cycle_bytes / args.steps}
     list_stats = [G.pic_get_list_stats(ctx.ctx, 0, s_) for s_ in range(cfg["n_species"])]
     extra = {"precision": f"{args.precision} particle state and push, fp64 Poisson residual",
              "list_relayouts_since_load": [r for r, _, _ in list_stats],
@@ -422,7 +480,7 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32", "data": "synthetic",
-            "config": _config_json(ws, name, extra), "roofline": roofline, "clocks": clocks,
+            "config": _config_json(ws, name, extra, args.precision), "roofline": roofline, "clocks": clocks,
             "gpu_launches": int(launches),
             "phase_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]}}
 

@@ -524,15 +524,20 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
         vy[i] += qm * ey * p->dt;
         x[i] += vx[i] * p->dt;
         y[i] += vy[i] * p->dt;
-        /* walls: periodic wrap or absorption */
+        /* walls: periodic wrap (modulo the period, however far the particle moved) or
+         * absorption; a wrapped position that rounds onto the far wall is the near wall */
         int dead = 0;
         if (x[i] < 0.0 || x[i] >= p->lx) {
-            if (m->bc_x == BC_PERIODIC) { if (x[i] < 0.0) x[i] += p->lx; else x[i] -= p->lx; if (x[i] >= p->lx) x[i] = 0.0; }
-            else dead = 1;
+            if (m->bc_x == BC_PERIODIC) {
+                x[i] -= p->lx * floor(x[i] / p->lx);
+                if (x[i] >= p->lx || x[i] < 0.0) x[i] = 0.0;
+            } else dead = 1;
         }
         if (y[i] < 0.0 || y[i] >= p->ly) {
-            if (m->bc_y == BC_PERIODIC) { if (y[i] < 0.0) y[i] += p->ly; else y[i] -= p->ly; if (y[i] >= p->ly) y[i] = 0.0; }
-            else dead = 1;
+            if (m->bc_y == BC_PERIODIC) {
+                y[i] -= p->ly * floor(y[i] / p->ly);
+                if (y[i] >= p->ly || y[i] < 0.0) y[i] = 0.0;
+            } else dead = 1;
         }
         if (dead) { new_leaf[i] = -1; continue; }
         int64_t nl;

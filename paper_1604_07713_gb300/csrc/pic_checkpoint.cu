@@ -7,8 +7,8 @@
 //     the last solve (the adaptation's |E| criterion reads them);
 //   - the step counter (Philox counter word and RF phase) and the next particle id;
 //   - per species the cell lists: per-leaf counts and the records in list order, in the
-//     state's precision, plus the per-leaf weight sums that the last list update left for
-//     the next deposit.
+//     state's precision, plus the per-leaf weight sums (compensated pairs) that the last list
+//     update left for the next deposit.
 // Restoring it into a context with the same configuration continues bit for bit like the
 // run it was taken from: the lists get fresh segments, but no result depends on where a
 // segment lies.
@@ -16,7 +16,7 @@
 // Byte layout (host order; every block starts on an 8-byte boundary):
 //   Header, root u32[nl], morton u32[nl], level u8[nl], phi f64[nl], phi_prev f64[nl],
 //   then per species: SpeciesHeader, count i32[nl], u, v, vx, vy, vz, w R[n], id u32[n],
-//   and wsum f64[nl] when sums_valid.
+//   and the per-leaf deposit sums stay_hi, stay_lo, ent_hi, ent_lo R[nl] when sums_valid.
 #include <algorithm>
 #include <cstring>
 
@@ -27,7 +27,7 @@ namespace gbpic {
 namespace {
 constexpr int kT = 256;
 constexpr uint64_t kMagic = 0x314B435049504247ull;  // "GBPIPCK1"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 inline unsigned warp_blocks(int64_t nw) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((nw + kT / 32 - 1) / (kT / 32), 1 << 20));
 }
@@ -95,7 +95,7 @@ template <typename R> SoA<R> dense_soa(DeviceArena &T, int64_t n) {
 
 int64_t species_bytes(int64_t nl, int64_t n, size_t rs, bool sums) {
     return (int64_t)sizeof(SpeciesHeader) + pad8(4 * nl) + 6 * pad8(n * (int64_t)rs) + pad8(4 * n) +
-           (sums ? 8 * nl : 0);
+           (sums ? 4 * pad8(nl * (int64_t)rs) : 0);
 }
 
 int64_t total_bytes(pic_ctx *ctx, Instance &in) {
@@ -143,7 +143,9 @@ template <typename R> void write_species(pic_ctx *ctx, Instance &in, int s, Writ
     R *arr_h[6];
     for (int k = 0; k < 6; ++k) arr_h[k] = (R *)w.take(n * (int64_t)sizeof(R));
     uint32_t *id_h = (uint32_t *)w.take(4 * n);
-    double *wsum_h = h.sums_valid ? (double *)w.take(8 * nl) : nullptr;
+    void *sums_h[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (h.sums_valid)
+        for (int k = 0; k < 4; ++k) sums_h[k] = w.take(nl * (int64_t)sizeof(R));
     if (!sp.start) {
         std::fill(cnt_h, cnt_h + nl, 0);
         return;
@@ -162,7 +164,11 @@ template <typename R> void write_species(pic_ctx *ctx, Instance &in, int s, Writ
     for (int k = 0; k < 6; ++k)
         if (n) GB_CUDA(cudaMemcpyAsync(arr_h[k], src[k], n * sizeof(R), cudaMemcpyDeviceToHost, st));
     if (n) GB_CUDA(cudaMemcpyAsync(id_h, o.id, 4 * n, cudaMemcpyDeviceToHost, st));
-    if (wsum_h) GB_CUDA(cudaMemcpyAsync(wsum_h, sp.wsum, 8 * nl, cudaMemcpyDeviceToHost, st));
+    if (h.sums_valid) {
+        void *dev[4] = {sp.stay_hi, sp.stay_lo, sp.ent_hi, sp.ent_lo};
+        for (int k = 0; k < 4; ++k)
+            GB_CUDA(cudaMemcpyAsync(sums_h[k], dev[k], nl * sizeof(R), cudaMemcpyDeviceToHost, st));
+    }
     GB_CUDA(cudaStreamSynchronize(st));
     T.release_all();
 }
@@ -177,7 +183,9 @@ template <typename R> void read_species(pic_ctx *ctx, Instance &in, int s, Reade
     const R *arr_h[6];
     for (int k = 0; k < 6; ++k) arr_h[k] = (const R *)r.take(n * (int64_t)sizeof(R));
     const uint32_t *id_h = (const uint32_t *)r.take(4 * n);
-    const double *wsum_h = h.sums_valid ? (const double *)r.take(8 * nl) : nullptr;
+    const void *sums_h[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (h.sums_valid)
+        for (int k = 0; k < 4; ++k) sums_h[k] = r.take(nl * (int64_t)sizeof(R));
     if (!h.present) return;
     int64_t total = 0;
     for (int64_t L = 0; L < nl; ++L) {
@@ -207,8 +215,10 @@ template <typename R> void read_species(pic_ctx *ctx, Instance &in, int s, Reade
     k_place_records<R><<<warp_blocks(nl), kT, 0, st>>>(nl, first, sp.start, sp.end, src, soa<R>(sp, sp.cur));
     count_launch(ctx);
     check_launch("checkpoint_read");
-    if (wsum_h) {
-        GB_CUDA(cudaMemcpyAsync(sp.wsum, wsum_h, 8 * nl, cudaMemcpyHostToDevice, st));
+    if (h.sums_valid) {
+        void *dev[4] = {sp.stay_hi, sp.stay_lo, sp.ent_hi, sp.ent_lo};
+        for (int k = 0; k < 4; ++k)
+            GB_CUDA(cudaMemcpyAsync(dev[k], sums_h[k], nl * sizeof(R), cudaMemcpyHostToDevice, st));
         sp.sums_valid = true;
     }
     GB_CUDA(cudaStreamSynchronize(st));

@@ -127,9 +127,10 @@ struct Species {
     // [5] tail used up this step (re-layout), [6] leaves moved to the tail (statistics),
     // [7] the re-layout drops the inflow room to fit the buffer
     int32_t *flags = nullptr;
-    // per-leaf weight sums left by the last cell-list update for the next deposit
+    // per-leaf weight sums left by the last cell-list update for the next deposit: the staying
+    // particles' compensated sum (move pass) and the entering particles' (per-leaf sort)
     void *stay_hi = nullptr, *stay_lo = nullptr;               // R [nleaf]
-    double *wsum = nullptr;                                     // [nleaf]
+    void *ent_hi = nullptr, *ent_lo = nullptr;                 // R [nleaf]
     bool sums_valid = false;
     // the per-step list repairs as a graph of two IF nodes (pic_lists.cu), valid for the
     // mesh and list epochs it was built in

@@ -350,7 +350,7 @@ void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
     Species &sp = in.sp[s];
     DeviceArena &A = in.part_mem[s];
     void *olds[] = {sp.start, sp.end, sp.lim, sp.rank0, sp.start_new, sp.stay, sp.inc, sp.fill, sp.big,
-                    sp.moved, sp.spawn, sp.spawn_base, sp.stay_hi, sp.stay_lo, sp.wsum};
+                    sp.moved, sp.spawn, sp.spawn_base, sp.stay_hi, sp.stay_lo, sp.ent_hi, sp.ent_lo};
     const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
     sp.start = dalloc<int32_t>(A, nl + 1);
     sp.end = dalloc<int32_t>(A, nl + 1);
@@ -367,7 +367,8 @@ void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
     sp.spawn_base = dalloc<int32_t>(A, nl + 1 + 2 * scan_scratch_elems(nl) + 8);
     sp.stay_hi = A.alloc((nl + 1) * rs + 64);
     sp.stay_lo = A.alloc((nl + 1) * rs + 64);
-    sp.wsum = dalloc<double>(A, nl + 1);
+    sp.ent_hi = A.alloc((nl + 1) * rs + 64);
+    sp.ent_lo = A.alloc((nl + 1) * rs + 64);
     sp.sums_valid = false;
     cudaStream_t st = ctx->stream;
     GB_CUDA(cudaMemsetAsync(sp.start, 0, (nl + 1) * 4, st));
@@ -387,7 +388,7 @@ void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
     sp.start = sp.end = sp.lim = sp.rank0 = sp.start_new = sp.stay = sp.inc = sp.fill = sp.big = sp.moved = nullptr;
     sp.spawn = sp.spawn_base = nullptr;
     sp.stay_hi = sp.stay_lo = nullptr;
-    sp.wsum = nullptr;
+    sp.ent_hi = sp.ent_lo = nullptr;
     const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
     sp.cap = cap;
     for (int b = 0; b < 2; ++b) {

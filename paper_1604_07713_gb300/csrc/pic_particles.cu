@@ -132,13 +132,23 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
     }
 }
 
-// Deposit from the per-leaf weight sums that the last cell-list update left behind
-// (staying particles summed by the move pass, entering ones by the per-leaf sort).
-__global__ void k_deposit_sums(DepositArgs a, const double *__restrict__ ws0, const double *__restrict__ ws1) {
+// Deposit from the per-leaf weight sums that the last cell-list update left behind: the
+// staying particles' compensated sum (hi, lo) from the move pass and the entering particles'
+// (hi, lo) from the per-leaf sort, combined here in FP64 with one thread per leaf:
+//   w_l = ((double) stay_hi + (double) stay_lo) + ((double) ent_hi + (double) ent_lo).
+struct LeafSums {
+    const void *stay_hi, *stay_lo, *ent_hi, *ent_lo;
+};
+template <typename R> __device__ __forceinline__ double leaf_weight(const LeafSums &w, int64_t L) {
+    const double st = (double)((const R *)w.stay_hi)[L] + (double)((const R *)w.stay_lo)[L];
+    return st + ((double)((const R *)w.ent_hi)[L] + (double)((const R *)w.ent_lo)[L]);
+}
+template <typename R>
+__global__ void k_deposit_sums(DepositArgs a, LeafSums w0, LeafSums w1) {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= a.nleaf) return;
-    double total = a.q[0] * ws0[L];
-    if (a.nsp > 1) total += a.q[1] * ws1[L];
+    double total = a.q[0] * leaf_weight<R>(w0, L);
+    if (a.nsp > 1) total += a.q[1] * leaf_weight<R>(w1, L);
     const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
     a.charge[L] = total;
     double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
@@ -282,13 +292,14 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
         const int32_t s = 1 << (a.lmax - a.lev[L]);
         X = q.a[e] * (R)s; Y = q.b[e] * (R)s;  // exact: s is a power of two
         I = a.ix[L] + (int32_t)m_floor(X); J = a.iy[L] + (int32_t)m_floor(Y);
+        // periodic directions wrap modulo the period, however far the particle moved
         if (I < 0 || I >= a.NX) {
             if (!a.px) alive = false;
-            else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) alive = false; }
+            else { I %= a.NX; if (I < 0) I += a.NX; }
         }
         if (J < 0 || J >= a.NY) {
             if (!a.py) alive = false;
-            else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) alive = false; }
+            else { J %= a.NY; if (J < 0) J += a.NY; }
         }
         if (!alive) cand = 0;
     }
@@ -484,11 +495,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
                         bool in = true;
                         if (I < 0 || I >= a.NX) {
                             if (!a.px) in = false;
-                            else { I += I < 0 ? a.NX : -a.NX; if (I < 0 || I >= a.NX) in = false; }
+                            else { I %= a.NX; if (I < 0) I += a.NX; }
                         }
                         if (J < 0 || J >= a.NY) {
                             if (!a.py) in = false;
-                            else { J += J < 0 ? a.NY : -a.NY; if (J < 0 || J >= a.NY) in = false; }
+                            else { J %= a.NY; if (J < 0) J += a.NY; }
                         }
                         if (in && I >= lx && I < lx + s && J >= ly && J < ly + s) {
                             const R inv = (R)1 / (R)s;
@@ -587,8 +598,7 @@ struct SortArgs {
     const int32_t *spawn_base;          // electrons' spawn offsets per parent leaf
     const unsigned long long *next_id;
     uint32_t ion_bit;                   // 1 for the ion list
-    double *wsum;                       // with stay sums: the leaf's weight for the next deposit
-    const void *stay_hi, *stay_lo;
+    void *ent_hi, *ent_lo;              // non-null: the entering weights' compensated sum per leaf (R)
     int32_t *big;                       // long regions for k_sort_big, count at big[nleaf]
     int32_t *med;                       // medium regions for k_sort_medium, count at med[nleaf]
     int32_t *err;
@@ -734,7 +744,7 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
             }
         }
         __syncthreads();
-        if (a.wsum) {  // entering weights in list order: per-thread Kahan, warps combined in order
+        if (a.ent_hi) {  // entering weights in list order: per-thread Kahan, warps combined in order
             R sum = 0, c = 0;
             for (int32_t q = q0 + threadIdx.x; q < q0 + k; q += blockDim.x) kahan_add(sum, c, d.w[q]);
             R hi = sum, lo = -c;
@@ -742,9 +752,11 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
             if ((threadIdx.x & 31) == 0) { red_hi[threadIdx.x >> 5] = hi; red_lo[threadIdx.x >> 5] = lo; }
             __syncthreads();
             if (threadIdx.x == 0) {
-                double tt = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
+                double tt = 0.0;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += (double)red_hi[w] + (double)red_lo[w];
-                a.wsum[L] = tt;
+                const R th = (R)tt;
+                ((R *)a.ent_hi)[L] = th;
+                ((R *)a.ent_lo)[L] = (R)(tt - (double)th);
             }
         }
         if (threadIdx.x == 0) a.end[L] = q0 + k;
@@ -754,14 +766,14 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
 
 constexpr int kSortLane = 8;  // entering regions up to this long are sorted by a leaf's 8-lane group
 
-// The leaf's weight for the next deposit: staying sum + entering particles in order (a few
-// entering particles: one lane, in order; many: lanes, then an exact combine).
-template <typename R> __device__ __forceinline__ double leaf_weight_seq(const SortArgs &a, int64_t L, SoA<R> d,
-                                                                        int32_t q0, int32_t k) {
-    const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
+// The entering weights of a leaf in order (a few entering particles: one lane, Kahan), as the
+// (sum, -compensation) pair that the next deposit combines.
+template <typename R> __device__ __forceinline__ void entering_weight_seq(const SortArgs &a, int64_t L, SoA<R> d,
+                                                                          int32_t q0, int32_t k) {
     R sum = 0, c = 0;
     for (int32_t q = q0; q < q0 + k; ++q) kahan_add(sum, c, d.w[q]);
-    return st + ((double)sum - (double)c);
+    ((R *)a.ent_hi)[L] = sum;
+    ((R *)a.ent_lo)[L] = -c;
 }
 
 // Entering regions of every leaf, 8 lanes per leaf (4 leaves per warp pass): a short region
@@ -807,8 +819,9 @@ __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<
             const int32_t q = q0 + r;
             d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
         }
-        if (a.wsum) {
-            // the entering weights in key order, summed by the group's first lane
+        if (a.ent_hi) {
+            // the entering weights in key order, summed by the group's first lane; the next
+            // deposit combines the pair with the staying sum in FP64, one thread per leaf
             R sum = 0, c = 0;
 #pragma unroll
             for (int rr = 0; rr < kSortLane; ++rr) {
@@ -817,8 +830,8 @@ __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<
                 if (who) kahan_add(sum, c, wr);
             }
             if (shortr && gl == 0) {
-                const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
-                a.wsum[L] = st + ((double)sum - (double)c);
+                ((R *)a.ent_hi)[L] = sum;
+                ((R *)a.ent_lo)[L] = -c;
             }
         }
         if (gl == 0 && has && k >= 0) {
@@ -846,16 +859,18 @@ __global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R>
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
         sort_region<R>(a, span, b0, k, q0, lane, d, t, sm_keys[threadIdx.x >> 5]);
-        if (a.wsum) {
+        if (a.ent_hi) {
             if (k <= 16) {
-                if (lane == 0) a.wsum[L] = leaf_weight_seq<R>(a, L, d, q0, k);
+                if (lane == 0) entering_weight_seq<R>(a, L, d, q0, k);
             } else {
-                const double st = (double)((const R *)a.stay_hi)[L] + (double)((const R *)a.stay_lo)[L];
                 R sum = 0, c = 0;
                 for (int32_t q = q0 + lane; q < q0 + k; q += 32) kahan_add(sum, c, d.w[q]);
                 R hi = sum, lo = -c;
                 warp_two_sum(hi, lo);
-                if (lane == 0) a.wsum[L] = st + ((double)hi + (double)lo);
+                if (lane == 0) {
+                    ((R *)a.ent_hi)[L] = hi;
+                    ((R *)a.ent_lo)[L] = lo;
+                }
             }
         }
         if (lane == 0) a.end[L] = q0 + k;
@@ -932,7 +947,7 @@ __global__ void k_read(int64_t nleaf, const int32_t *__restrict__ start, const i
 }
 
 // Order the entering regions of every leaf: the warp-per-leaf pass (short regions, and the
-// weight sums when a.wsum is given), then the long regions (one block each).
+// entering weight sums when a.ent_hi is given), then the long regions (one block each).
 template <typename R> void sort_lists(pic_ctx *ctx, SortArgs a, SoA<R> d, SoA<R> t) {
     GB_CUDA(cudaMemsetAsync(a.big + a.nleaf, 0, 4, ctx->stream));
     GB_CUDA(cudaMemsetAsync(a.med + a.nleaf, 0, 4, ctx->stream));
@@ -958,8 +973,7 @@ template <typename R> SortArgs sort_args(Instance &in, Species &sp) {
     a.spawn_base = nullptr;
     a.next_id = in.d_next_id;
     a.ion_bit = 0;
-    a.wsum = nullptr;
-    a.stay_hi = sp.stay_hi; a.stay_lo = sp.stay_lo;
+    a.ent_hi = a.ent_lo = nullptr;
     a.big = sp.big;
     a.med = sp.moved;  // the moved-leaf list is free once the overflow repairs ran
     a.err = in.d_err;
@@ -1130,7 +1144,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                 a.spawn_base = e.spawn_base;
             }
             a.ion_bit = s == 1 ? 1u : 0u;
-            a.wsum = sp.wsum;
+            a.ent_hi = sp.ent_hi;
+            a.ent_lo = sp.ent_lo;
             sort_lists<R>(ctx, a, soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
             sp.sums_valid = true;
         }
@@ -1165,7 +1180,9 @@ void grow_species(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
     GB_CUDA(cudaMemcpyAsync(sp.spawn_base, os.spawn_base, (nl + 1 + 2 * scan_scratch_elems(nl) + 8) * 4,
                             cudaMemcpyDeviceToDevice, ctx->stream));
     if (os.sums_valid) {
-        GB_CUDA(cudaMemcpyAsync(sp.wsum, os.wsum, nl * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (auto pr : {std::make_pair(sp.stay_hi, os.stay_hi), std::make_pair(sp.stay_lo, os.stay_lo),
+                        std::make_pair(sp.ent_hi, os.ent_hi), std::make_pair(sp.ent_lo, os.ent_lo)})
+            GB_CUDA(cudaMemcpyAsync(pr.first, pr.second, nl * rs, cudaMemcpyDeviceToDevice, ctx->stream));
         sp.sums_valid = true;
     }
     GB_CUDA(cudaMemcpyAsync(sp.flags, os.flags, 8 * 4, cudaMemcpyDeviceToDevice, ctx->stream));  // tail, statistics
@@ -1296,9 +1313,15 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
     a.b = in.bvec;
     bool sums = true;
     for (int s = 0; s < in.cfg.n_species; ++s) sums = sums && in.sp[s].start && in.sp[s].sums_valid;
-    if (sums)
-        k_deposit_sums<<<blocks_for(in.nleaf), kT, 0, ctx->stream>>>(a, in.sp[0].wsum,
-                                                                   in.cfg.n_species > 1 ? in.sp[1].wsum : nullptr);
+    if (sums) {
+        const Species &s1 = in.sp[in.cfg.n_species > 1 ? 1 : 0];
+        const LeafSums w0{in.sp[0].stay_hi, in.sp[0].stay_lo, in.sp[0].ent_hi, in.sp[0].ent_lo};
+        const LeafSums w1{s1.stay_hi, s1.stay_lo, s1.ent_hi, s1.ent_lo};
+        if (in.cfg.precision == PIC_FP64)
+            k_deposit_sums<double><<<blocks_for(in.nleaf), kT, 0, ctx->stream>>>(a, w0, w1);
+        else
+            k_deposit_sums<float><<<blocks_for(in.nleaf), kT, 0, ctx->stream>>>(a, w0, w1);
+    }
     else if (in.cfg.precision == PIC_FP64)
         k_deposit<double><<<warp_blocks(in.nleaf), kT, 0, ctx->stream>>>(a);
     else

@@ -250,7 +250,7 @@ def streamer_snapshot(n_particles=50_000_000, nx0=128, lmax=4, seed=DEFAULT_SEED
     w = n_e * area / n
     for s, (m, T) in enumerate(((ME, 5.0), (mi, 0.026))):
         u = rng.random(n)
-        x = 0.25 * box + 0.5 * box * u + 0.05 * box * rng.standard_normal(n) * (u < 0.0)
+        x = 0.25 * box + 0.5 * box * u
         tail = rng.random(n) < 0.1
         x[tail] = 0.5 * box + 0.3 * box * rng.standard_normal(int(tail.sum()))
         y = 0.5 * box + sig_y * rng.standard_normal(n)

@@ -188,12 +188,12 @@ def test_one_step_fp64_bit_exact_lists_with_ionization():
 
 
 def _dyadic_ccp(nx=64, ny=8, ppc=200, seed=7, te=30.0, ng=3e21):
-    """The capacitively coupled discharge on cells of side 2^-13 m with positions, velocities
-    and weights that the FP32 state holds exactly (float32 offsets in their cell, float32
-    velocities and weights), so that the FP32 path and the FP64 oracle start from identical
-    values."""
+    """The capacitively coupled discharge on cells of side 2^-10 m (close to the 6.7 cm / 64
+    of the recipe) with positions, velocities and weights that the FP32 state holds exactly
+    (float32 offsets in their cell, float32 velocities and weights), so that the FP32 path and
+    the FP64 oracle start from identical values."""
     cfg, mesh, parts = W.ccp(nx=nx, ny=ny, ppc=ppc, seed=seed, precision=W.FP32, te=te, ng=ng)
-    h_old, h = mesh["h0"], 2.0 ** -13
+    h_old, h = mesh["h0"], 2.0 ** -10
     mesh = dict(mesh, h0=h)
     f32 = np.float32
     for p in parts.values():

@@ -204,6 +204,26 @@ def test_single_particle_in_uniform_field_exact_leapfrog():
         assert sp.leaf[0] == M.locate(sp.x, sp.y)[0]
 
 
+def test_periodic_wrap_is_modulo_the_period():
+    """A particle that moves 2.3 periods in a periodic direction in one step ends at its
+    position modulo the period (and keeps its velocity); one that leaves through an
+    absorbing wall is removed.  Fails for: a single wrap (the particle would end outside the
+    domain or be clamped to the wall)."""
+    M = O.Mesh(4, 2, 0.25, 0, O.BC_DIRICHLET, O.BC_PERIODIC)
+    cfg = W.base_config(precision=W.FP64, n_species=1, dt=1.0, eps0=1.0, q=[-1.0], m=[1.0],
+                        bc_x=W.BC_DIRICHLET, bc_y=W.BC_PERIODIC)
+    sim = O.Sim(cfg, M)
+    sim.load(0, [0.3, 0.6, 0.9], [0.1, 0.2, 0.3], [0.0, 0.0, 0.5], [2.3 * 0.5, -2.3 * 0.5, 0.0],
+             [0.0, 0.0, 0.0], [0.0, 0.0, 0.0])
+    sim.step(1)
+    sp = sim.species[0]
+    assert sp.n == 2                                    # the third left through x = 1
+    o = np.argsort(sp.id)
+    assert np.allclose(sp.y[o], [(0.1 + 1.15) % 0.5, (0.2 - 1.15) % 0.5], atol=1e-15)
+    assert np.allclose(sp.x[o], [0.3, 0.6]) and np.allclose(sp.vy[o], [1.15, -1.15])
+    assert np.array_equal(sp.leaf, M.locate(sp.x, sp.y))
+
+
 def test_deposit_conserves_charge_and_cell_lists_are_consistent():
     cfg, mesh, parts = W.ccp(nx=32, ny=4, ppc=20, seed=3, precision=W.FP64)
     M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, O.BC_DIRICHLET, O.BC_PERIODIC)
