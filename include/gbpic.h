@@ -63,6 +63,13 @@ typedef enum {
 enum { PIC_FP32 = 0, PIC_FP64 = 1 };
 enum { PIC_BC_PERIODIC = 0, PIC_BC_DIRICHLET = 1, PIC_BC_NEUMANN = 2 };
 enum { PIC_ADAPT_MESH = 1, PIC_ADAPT_PARTICLES = 2 };
+/* Particle shapes (§3): NGP charge assignment at cell centres with the bilinear gather of the
+ * corner field (any mesh); on a uniform mesh (max_level 0) also the cloud-in-cell variants
+ * CIC-EM (momentum conserving: E at cell centres by central differences, gathered with the
+ * deposit's bilinear weights) and CIC-EC (energy conserving: E = -grad of the bilinear
+ * interpolant of phi over cell centres).  Beyond a non-periodic wall a cloud's share folds
+ * into the boundary cell; phi beyond it takes the Poisson operator's ghost value. */
+enum { PIC_SHAPE_NGP = 0, PIC_SHAPE_CIC_EM = 1, PIC_SHAPE_CIC_EC = 2 };
 
 /* Fields per leaf, in leaf (Morton key) order, for pic_read_fields. */
 enum {
@@ -124,6 +131,7 @@ typedef struct pic_config {
     int32_t mg_max_cycles;      /* Poisson: V-cycle limit per solve                        */
     int32_t instance;           /* instance id mixed into the Philox counter               */
     int64_t particle_capacity;  /* per species; 0 = automatic (grows as needed)            */
+    int32_t shape;              /* PIC_SHAPE_*: charge assignment and field gather (§3)    */
 } pic_config;
 
 /* Create a context of n_instances independent PIC instances, one config each (cfg points

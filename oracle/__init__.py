@@ -101,7 +101,9 @@ def _declare(L):
     L.or_cell_emag.argtypes = [C.POINTER(_Mesh), _p, _p, _p]
     L.or_deposit.argtypes = [_i64, _i64, _p, _p, C.c_double, _p]
     L.or_push_mcc.argtypes = [C.POINTER(_Mesh), C.POINTER(_PushParams), _p, _i64, _p, _p, _p,
-                              _p, _p, _p, _p, _p, _p, _p, _p, _p]
+                              _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+    L.or_cic_deposit.argtypes = [_i32, _i32, C.c_double, _i32, _i32, _i64, _p, _p, _p, C.c_double, _p]
+    L.or_cic_gather.argtypes = [_i32, _i32, C.c_double, _i32, _i32, _p, _p, _i32, _i64, _p, _p, _p, _p]
     L.or_push_mcc.restype = _i64
 
 
@@ -333,13 +335,38 @@ class Sim:
         return np.array([lo, c.get("phi_right", 0.0), 0.0, 0.0])
 
     # -- §3 NGP deposit -------------------------------------------------------------------
+    def shape(self):
+        """0: NGP deposit with the bilinear corner gather; 1: CIC-EM; 2: CIC-EC (§3, uniform
+        meshes only)."""
+        sh = int(self.cfg.get("shape", 0))
+        if sh and self.mesh.lmax != 0:
+            raise ValueError("cloud-in-cell shapes need a uniform mesh")
+        return sh
+
     def charge(self):
         Q = np.zeros(self.mesh.nleaf)
+        M = self.mesh
         for sp in self.species:
             if sp is None or sp.n == 0:
                 continue
-            lib().or_deposit(self.mesh.nleaf, sp.n, _ptr(sp.leaf), _ptr(sp.w), sp.q, _ptr(Q))
+            if self.shape():
+                # uniform mesh: leaf index = i + j nx0 (Morton order of the roots is row-major)
+                lib().or_cic_deposit(M.nx0, M.ny0, M.h0, int(M.bc_x == BC_PERIODIC),
+                                     int(M.bc_y == BC_PERIODIC), sp.n, _ptr(sp.x), _ptr(sp.y),
+                                     _ptr(sp.w), sp.q, _ptr(Q))
+            else:
+                lib().or_deposit(self.mesh.nleaf, sp.n, _ptr(sp.leaf), _ptr(sp.w), sp.q, _ptr(Q))
         return Q
+
+    def cic_field(self, sp, phi=None, walls=None):
+        """(ex, ey) at the particles of ``sp`` with the cloud-in-cell shape of the config."""
+        M = self.mesh
+        phi = np.ascontiguousarray(self.phi if phi is None else phi, np.float64)
+        w = np.ascontiguousarray(self.last_walls if walls is None else walls, np.float64)
+        ex = np.empty(sp.n); ey = np.empty(sp.n)
+        lib().or_cic_gather(M.nx0, M.ny0, M.h0, M.bc_x, M.bc_y, _ptr(phi), _ptr(w), self.shape(), sp.n,
+                            _ptr(sp.x), _ptr(sp.y), _ptr(ex), _ptr(ey))
+        return ex, ey
 
     def rho(self):
         return self.charge() / self.mesh.area() + self.cfg.get("rho_background", 0.0)
@@ -454,10 +481,14 @@ class Sim:
             sv = np.zeros(3 * n); svi = np.zeros(3 * n)
             p = self.push_params(s)
             dec = np.empty(4 * n)
+            e_part = None
+            if self.shape():
+                ex, ey = self.cic_field(sp)
+                e_part = np.ascontiguousarray(np.stack([ex, ey], 1).reshape(-1))
             lib().or_push_mcc(C.byref(self.mesh._c), C.byref(p), _ptr(Eflat), n, _ptr(sp.x),
                               _ptr(sp.y), _ptr(sp.vx), _ptr(sp.vy), _ptr(sp.vz), _ptr(sp.id),
                               _ptr(sp.leaf), _ptr(new_leaf), _ptr(spawn), _ptr(sv), _ptr(svi),
-                              _ptr(dec))
+                              _ptr(dec), _ptr(e_part))
             # the collision decisions of this step by particle id: (U0, P, U1 sigma_T, sigma_iz)
             self.last_decisions[s] = (sp.id.copy(), dec.reshape(n, 4))
             results.append((new_leaf, spawn, sv.reshape(n, 3), svi.reshape(n, 3)))

@@ -499,12 +499,14 @@ static void iso_dir(double uc, double up, double d[3])
  * (spawn_vi[3i..]).  When dec is not NULL it receives the quantities of each particle's
  * collision decisions, dec[4i..4i+3] = (U0, P, U1 sigma_T, sigma_iz): collide iff U0 < P,
  * ionize iff U1 sigma_T < sigma_iz (electrons; ions 0, 0); U0 = -1 where no collision test
- * was made (absorbed particle, collisions off).  Returns the number of ionizations.
+ * was made (absorbed particle, collisions off).  When e_part is not NULL it holds each
+ * particle's field (ex, ey) at x^n, gathered with a cloud-in-cell shape, and replaces the
+ * bilinear corner gather.  Returns the number of ionizations.
  */
 int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *node_e_arr,
                     int64_t n, double *x, double *y, double *vx, double *vy, double *vz,
                     const uint64_t *id, const int64_t *leaf, int64_t *new_leaf, uint8_t *spawn,
-                    double *spawn_v, double *spawn_vi, double *dec)
+                    double *spawn_v, double *spawn_vi, double *dec, const double *e_part)
 {
     double hf = m->h0 / (double)(1 << m->lmax);
     int64_t nspawn = 0;
@@ -514,10 +516,16 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
         int64_t l = leaf[i];
         double h = m->s[l] * hf;
         double u = (x[i] - m->ix[l] * hf) / h, v = (y[i] - m->iy[l] * hf) / h;
-        const double *E = node_e_arr + 8 * l;
-        double w00 = (1 - u) * (1 - v), w10 = u * (1 - v), w01 = (1 - u) * v, w11 = u * v;
-        double ex = w00 * E[0] + w10 * E[2] + w01 * E[4] + w11 * E[6];
-        double ey = w00 * E[1] + w10 * E[3] + w01 * E[5] + w11 * E[7];
+        double ex, ey;
+        if (e_part) { /* a cloud-in-cell field gathered beforehand (or_cic_gather) */
+            ex = e_part[2 * i];
+            ey = e_part[2 * i + 1];
+        } else {      /* bilinear over the leaf's corners */
+            const double *E = node_e_arr + 8 * l;
+            double w00 = (1 - u) * (1 - v), w10 = u * (1 - v), w01 = (1 - u) * v, w11 = u * v;
+            ex = w00 * E[0] + w10 * E[2] + w01 * E[4] + w11 * E[6];
+            ey = w00 * E[1] + w10 * E[3] + w01 * E[5] + w11 * E[7];
+        }
         /* leapfrog kick and drift */
         double qm = p->q / p->m;
         vx[i] += qm * ex * p->dt;
@@ -606,4 +614,109 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
         }
     }
     return nspawn;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Cloud-in-cell shapes on a uniform mesh (§3: the momentum-conserving CIC-EM and the     */
+/* energy-conserving CIC-EC variants on uniform meshes).  nx x ny cells of side h, cell    */
+/* (i, j) with its centre at ((i + 1/2) h, (j + 1/2) h), lattice index i + j nx.  A         */
+/* particle at x has the reference centre i0 = floor(x / h - 1/2) and the fraction          */
+/* fx = x / h - 1/2 - i0: weights 1 - fx and fx on the centres i0 and i0 + 1 (likewise in y, */
+/* bilinear in 2D).  A centre beyond a non-periodic wall is replaced by the adjacent cell   */
+/* (its weight folds into it, so charge is conserved); periodic directions wrap.            */
+/* ------------------------------------------------------------------------------------ */
+static int cic_cell(int i, int n, int periodic)
+{
+    if (periodic) return ((i % n) + n) % n;
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+static void cic_weights(double x, double h, int *i0, double *f)
+{
+    double g = x / h - 0.5;
+    double fl = floor(g);
+    *i0 = (int)fl;
+    *f = g - fl;
+}
+
+/* Q[cell] += q w W(cell) for every particle (the charge per unit depth). */
+void or_cic_deposit(int nx, int ny, double h, int px, int py, int64_t n, const double *x, const double *y,
+                    const double *w, double q, double *Q)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        int i0, j0;
+        double fx, fy;
+        cic_weights(x[p], h, &i0, &fx);
+        cic_weights(y[p], h, &j0, &fy);
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                double wt = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+                int c = cic_cell(i0 + a, nx, px) + nx * cic_cell(j0 + b, ny, py);
+                Q[c] += q * w[p] * wt;
+            }
+    }
+}
+
+/* phi at lattice (i, j) with the Poisson operator's ghost rule outside the walls:
+ * periodic wrap; Dirichlet 2 phi_wall - phi_inside; Neumann phi_inside.
+ * walls = phi on the x-low, x-high, y-low, y-high walls. */
+static double cic_phi(int nx, int ny, int bcx, int bcy, const double *phi, const double *walls, int i, int j)
+{
+    double add = 0.0, sgn = 1.0;
+    if (i < 0 || i >= nx) {
+        if (bcx == BC_PERIODIC) i = ((i % nx) + nx) % nx;
+        else {
+            int in = i < 0 ? 0 : nx - 1;
+            if (bcx == BC_DIRICHLET) { add = 2.0 * walls[i < 0 ? 0 : 1]; sgn = -1.0; }
+            i = in;
+        }
+    }
+    if (j < 0 || j >= ny) {
+        if (bcy == BC_PERIODIC) j = ((j % ny) + ny) % ny;
+        else {
+            int in = j < 0 ? 0 : ny - 1;
+            if (bcy == BC_DIRICHLET) { add += 2.0 * walls[j < 0 ? 2 : 3] * sgn; sgn = -sgn; }
+            j = in;
+        }
+    }
+    return add + sgn * phi[i + nx * j];
+}
+
+/* E at the particles.  shape 1 (CIC-EM): E at the cell centres by central differences of
+ * phi (with the ghost rule), gathered with the particle's CIC weights (folded at walls as in
+ * the deposit).  shape 2 (CIC-EC): E = -grad of the bilinear interpolant of phi over the cell
+ * centres (ghost values beyond walls) at the particle. */
+void or_cic_gather(int nx, int ny, double h, int bcx, int bcy, const double *phi, const double *walls, int shape,
+                   int64_t n, const double *x, const double *y, double *ex, double *ey)
+{
+    int px = bcx == BC_PERIODIC, py = bcy == BC_PERIODIC;
+    for (int64_t p = 0; p < n; ++p) {
+        int i0, j0;
+        double fx, fy;
+        cic_weights(x[p], h, &i0, &fx);
+        cic_weights(y[p], h, &j0, &fy);
+        if (shape == 1) {
+            double sx = 0.0, sy = 0.0;
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    double wt = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+                    int i = cic_cell(i0 + a, nx, px), j = cic_cell(j0 + b, ny, py);
+                    double gx = (cic_phi(nx, ny, bcx, bcy, phi, walls, i + 1, j) -
+                                 cic_phi(nx, ny, bcx, bcy, phi, walls, i - 1, j)) / (2.0 * h);
+                    double gy = (cic_phi(nx, ny, bcx, bcy, phi, walls, i, j + 1) -
+                                 cic_phi(nx, ny, bcx, bcy, phi, walls, i, j - 1)) / (2.0 * h);
+                    sx += wt * gx;
+                    sy += wt * gy;
+                }
+            ex[p] = -sx;
+            ey[p] = -sy;
+        } else {
+            double p00 = cic_phi(nx, ny, bcx, bcy, phi, walls, i0, j0);
+            double p10 = cic_phi(nx, ny, bcx, bcy, phi, walls, i0 + 1, j0);
+            double p01 = cic_phi(nx, ny, bcx, bcy, phi, walls, i0, j0 + 1);
+            double p11 = cic_phi(nx, ny, bcx, bcy, phi, walls, i0 + 1, j0 + 1);
+            ex[p] = -((1.0 - fy) * (p10 - p00) + fy * (p11 - p01)) / h;
+            ey[p] = -((1.0 - fx) * (p01 - p00) + fx * (p11 - p10)) / h;
+        }
+    }
 }

@@ -35,6 +35,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_set_stream", "pic_set_mesh", "pic_
             "pic_checkpoint_write", "pic_checkpoint_read", "pic_inject_fault", "pic_diag_enable",
             "pic_diag_reset", "pic_read_eedf", "pic_last_error"]
 PIC_FAULT_NONE, PIC_FAULT_ALLOC, PIC_FAULT_BALANCE = 0, 1, 2
+PIC_SHAPE_NGP, PIC_SHAPE_CIC_EM, PIC_SHAPE_CIC_EC = 0, 1, 2
 
 
 class PicConfig(C.Structure):
@@ -51,7 +52,7 @@ class PicConfig(C.Structure):
         ("adapt_every", C.c_int32), ("e_ref", C.c_double), ("refine_field", C.c_double),
         ("coarsen_field", C.c_double), ("refine_count", C.c_int32), ("coarsen_count", C.c_int32),
         ("mg_rel_tol", C.c_double), ("mg_max_cycles", C.c_int32), ("instance", C.c_int32),
-        ("particle_capacity", C.c_int64),
+        ("particle_capacity", C.c_int64), ("shape", C.c_int32),
     ]
 
 

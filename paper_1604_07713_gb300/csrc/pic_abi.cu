@@ -190,6 +190,9 @@ void validate(const pic_config &c) {
     }
     if (c.instance < 0 || c.instance > 255) fail(PIC_EINVAL, "instance must be in [0, 255]");
     if (!(c.mg_rel_tol > 0.0)) fail(PIC_EINVAL, "mg_rel_tol must be positive");
+    if (c.shape < PIC_SHAPE_NGP || c.shape > PIC_SHAPE_CIC_EC) fail(PIC_EINVAL, "unknown particle shape");
+    if (c.shape != PIC_SHAPE_NGP && c.max_level != 0)
+        fail(PIC_EINVAL, "cloud-in-cell shapes need a uniform mesh (max_level 0)");
 }
 
 Instance &get_inst(pic_ctx *ctx, int32_t inst) {
@@ -235,10 +238,23 @@ void gbpic::set_mesh_impl(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h
     mesh_build(ctx, in, nx0, ny0, h0, n_leaves, root, morton, level);
     poisson_setup(ctx, in);
     diag_reset(ctx, in);
+    field_arrays(ctx, in);
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+// The corner field array (and, for cloud-in-cell shapes, the per-quarter coefficients and
+// the deposit's per-leaf partial charges) of the current mesh, zeroed.
+void gbpic::field_arrays(pic_ctx *ctx, Instance &in) {
     const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
     in.stencil = in.mesh_mem.alloc(8 * rs * in.nleaf + 64);
     GB_CUDA(cudaMemsetAsync(in.stencil, 0, 8 * rs * in.nleaf, ctx->stream));
-    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    in.patch = nullptr;
+    in.cic_part = nullptr;
+    if (in.cfg.shape != PIC_SHAPE_NGP) {
+        in.patch = in.mesh_mem.alloc(32 * rs * in.nleaf + 64);
+        GB_CUDA(cudaMemsetAsync(in.patch, 0, 32 * rs * in.nleaf, ctx->stream));
+        in.cic_part = dalloc<double>(in.mesh_mem, 9 * in.nleaf);
+    }
 }
 
 // Field half of a step for every instance: deposits, then one batched launch for all

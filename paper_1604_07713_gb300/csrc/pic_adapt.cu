@@ -806,9 +806,7 @@ void adapt_mesh(pic_ctx *ctx, Instance &in) {
     mesh_build_device(ctx, in, n_new);
     poisson_setup(ctx, in);
     GB_CUDA(cudaMemcpyAsync(in.phi, nphi, n_new * 8, cudaMemcpyDeviceToDevice, st));
-    const size_t rs = in.cfg.precision == PIC_FP64 ? 8 : 4;
-    in.stencil = in.mesh_mem.alloc(8 * rs * n_new + 64);
-    GB_CUDA(cudaMemsetAsync(in.stencil, 0, 8 * rs * n_new, st));
+    field_arrays(ctx, in);
     GB_CUDA(cudaStreamSynchronize(st));
     old_mesh.release_all();
     T.release_all();

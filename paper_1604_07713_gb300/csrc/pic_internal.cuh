@@ -191,6 +191,8 @@ struct Instance {
     double *red_host = nullptr;  // pinned
     int32_t *cnt_host = nullptr; // pinned
     void *stencil = nullptr;     // node E per leaf corner: 8 x R per leaf
+    void *patch = nullptr;       // cloud-in-cell shapes: per leaf 4 quarters x 2 components x 4 R
+    double *cic_part = nullptr;  // cloud-in-cell deposit: per leaf its charge on the 3 x 3 cells around it
     Species sp[2];
     int64_t next_id = 0;                     // host mirror (exact after a sync)
     unsigned long long *d_next_id = nullptr; // device counter of the next particle id
@@ -407,6 +409,10 @@ void graph_release(pic_ctx *ctx);
 void report_all(pic_ctx *ctx);            // exact totals, error flags, solver stats of every instance (syncs)
 void fields_all(pic_ctx *ctx, int64_t step);
 void species_compact(pic_ctx *ctx, Instance &in, int s);  // leaf-order re-layout, tail freed
+// pic_cic.cu (uniform meshes)
+void cic_patch(pic_ctx *ctx, Instance &in, const double walls[4]);
+void cic_deposit(pic_ctx *ctx, Instance &in, const double walls[4]);
+void field_arrays(pic_ctx *ctx, Instance &in);  // corner field (and CIC arrays) for the current mesh
 // pic_checkpoint.cu
 int64_t checkpoint_write(pic_ctx *ctx, Instance &in, void *buf, int64_t cap);  // bytes needed
 void checkpoint_read(pic_ctx *ctx, Instance &in, const void *buf, int64_t bytes);

@@ -542,6 +542,7 @@ void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {
     }
     count_launch(ctx);
     check_launch("node_e");
+    if (in.cfg.shape != PIC_SHAPE_NGP) cic_patch(ctx, in, walls);  // the push gathers from it
 }
 
 void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev) {

@@ -212,6 +212,7 @@ template <typename R> struct PushArgs {
     const int32_t *ion_total;  // electrons with ionization: the ion total (spawned ions' keys)
     const uint8_t *lev;
     const R *stencil;
+    const R *patch;       // cloud-in-cell shapes: 32 coefficients per leaf
     SoA<R> d;             // this species' lists, updated in place
     ListPut<R> self;      // entering records and spawned electrons of this species
     ListPut<R> ion;       // electrons with ionization: the spawned ions (ion.fill null otherwise)
@@ -408,7 +409,9 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
 // chunk lies beyond every slot it writes in this one.  Entering and spawned records only go
 // to free slots past end[], which no warp reads during the pass.
 // NT threads per block (a tuned launch shape); 768 threads per SM either way: 80 registers.
-template <typename R, int NT>
+// CIC: the field is gathered from the leaf's per-quarter cloud-in-cell coefficients (32 per
+// leaf, lane k holding coefficient k) instead of the bilinear corner field.
+template <typename R, int NT, bool CIC>
 __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
     extern __shared__ unsigned char push_smem[];
     Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
@@ -456,14 +459,18 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
         const int32_t s = 1 << (a.lmax - lv);
         const int32_t lx = a.ix[L], ly = a.iy[L];
         const R dth = a.dth[lv];
-        R E[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) E[k] = a.stencil[8 * (int64_t)L + k];
         // the bilinear form in the leaf's corner field, E(u, v) = e0 + u e_u + v (e_v + u e_uv)
         // per component (corners 00, 10, 01, 11 at E[0..1], E[2..3], E[4..5], E[6..7])
-        R Bx[4], By[4];
-        Bx[0] = E[0]; Bx[1] = E[2] - E[0]; Bx[2] = E[4] - E[0]; Bx[3] = (E[0] - E[2]) - (E[4] - E[6]);
-        By[0] = E[1]; By[1] = E[3] - E[1]; By[2] = E[5] - E[1]; By[3] = (E[1] - E[3]) - (E[5] - E[7]);
+        R Bx[4], By[4], pc = 0;
+        if constexpr (CIC) {
+            pc = a.patch[32 * (int64_t)L + lane];
+        } else {
+            R E[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) E[k] = a.stencil[8 * (int64_t)L + k];
+            Bx[0] = E[0]; Bx[1] = E[2] - E[0]; Bx[2] = E[4] - E[0]; Bx[3] = (E[0] - E[2]) - (E[4] - E[6]);
+            By[0] = E[1]; By[1] = E[3] - E[1]; By[2] = E[5] - E[1]; By[3] = (E[1] - E[3]) - (E[5] - E[7]);
+        }
         int32_t stay_run = 0;
         for (int32_t c0 = p0; c0 < p1; c0 += 32) {
             const int32_t p = c0 + lane;
@@ -474,10 +481,26 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
             if (p + 32 < p1) fetch(p + 32);
             else if (c0 + 32 >= p1 && np0 + lane < np1) fetch(np0 + lane);
             U4 r0{0u, 0u, 0u, 0u};
+            R ex = 0, ey = 0;
+            if constexpr (CIC) {
+                // the quarter (qx, qy) of the leaf and the fractions (fx, fy) from its reference
+                // cell centre; its 8 coefficients from the lanes that hold them (all lanes
+                // take part in the shuffles)
+                const int qx = u >= (R)0.5 ? 1 : 0, qy = v >= (R)0.5 ? 1 : 0;
+                const R fx = u + (R)0.5 - (R)qx, fy = v + (R)0.5 - (R)qy;
+                const int base = 8 * (qx + 2 * qy);
+                R c[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) c[t] = __shfl_sync(0xFFFFFFFFu, pc, base + t);
+                ex = c[0] + fx * c[1] + fy * (c[2] + fx * c[3]);
+                ey = c[4] + fx * c[5] + fy * (c[6] + fx * c[7]);
+            }
             if (live) {
-                // gather: bilinear in the leaf's corner field
-                const R ex = Bx[0] + u * Bx[1] + v * (Bx[2] + u * Bx[3]);
-                const R ey = By[0] + u * By[1] + v * (By[2] + u * By[3]);
+                if constexpr (!CIC) {
+                    // gather: bilinear in the leaf's corner field
+                    ex = Bx[0] + u * Bx[1] + v * (Bx[2] + u * Bx[3]);
+                    ey = By[0] + u * By[1] + v * (By[2] + u * By[3]);
+                }
                 // leapfrog kick and drift in leaf units
                 vx += a.qm_dt * ex;
                 vy += a.qm_dt * ey;
@@ -1013,6 +1036,7 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     a.ion_total = nullptr;
     a.map = g.map; a.ix = g.ix; a.iy = g.iy; a.lev = g.lev;
     a.stencil = (const R *)in.stencil;
+    a.patch = (const R *)in.patch;
     a.d = soa<R>(sp, sp.cur);
     a.self = list_put_args<R>(sp, in.nleaf);
     a.ion = ListPut<R>{};
@@ -1079,21 +1103,28 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     // tuned share allows), in blocks of 128 or 256 threads (a tuned launch shape)
     const int nt = ctx->tune.push_threads == 128 ? 128 : 256;
     const size_t push_smem = (size_t)(nt / 32) * sizeof(Queue<R>);
-    static int resident[2] = {0, 0}, sms = 0;  // per process: one device model; [128, 256]
+    // per process (one device model): resident blocks of [NGP, CIC][128, 256]
+    static int resident[2][2] = {{0, 0}, {0, 0}}, sms = 0;
     if (!sms) {
         const size_t sm128 = 4 * sizeof(Queue<R>), sm256 = 8 * sizeof(Queue<R>);
-        GB_CUDA(cudaFuncSetAttribute(k_push<R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
-        GB_CUDA(cudaFuncSetAttribute(k_push<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_push<R, 128>, 128, sm128));
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_push<R, 256>, 256, sm256));
-        if (resident[0] < 1 || resident[1] < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
+        GB_CUDA(cudaFuncSetAttribute(k_push<R, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0][0], k_push<R, 128, false>, 128, sm128));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0][1], k_push<R, 256, false>, 256, sm256));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1][0], k_push<R, 128, true>, 128, sm128));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1][1], k_push<R, 256, true>, 256, sm256));
+        for (auto &rr : resident)
+            if (rr[0] < 1 || rr[1] < 1) fail(PIC_ECUDA, "push kernel does not fit on an SM");
         int dev = 0;
         GB_CUDA(cudaGetDevice(&dev));
         GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
+    const bool cic = in.cfg.shape != PIC_SHAPE_NGP;
     const int wpb = nt / 32;
     const unsigned wb = (unsigned)std::max<int64_t>(1, (nl + wpb - 1) / wpb);
-    int bps = resident[nt == 128 ? 0 : 1];
+    int bps = resident[cic ? 1 : 0][nt == 128 ? 0 : 1];
     if (ctx->tune.push_bps > 0) bps = std::min(bps, ctx->tune.push_bps * (256 / nt));  // 256-thread units
     // a captured ensemble step runs instances on parallel branches: a push that takes a
     // share of the GPU lets several instances' pushes run side by side
@@ -1124,8 +1155,13 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
                     a.ion_total = ion->rank0 + nl;
                 }
             }
-            if (nt == 128) k_push<R, 128><<<pb, 128, push_smem, st>>>(a);
-            else k_push<R, 256><<<pb, 256, push_smem, st>>>(a);
+            if (cic) {
+                if (nt == 128) k_push<R, 128, true><<<pb, 128, push_smem, st>>>(a);
+                else k_push<R, 256, true><<<pb, 256, push_smem, st>>>(a);
+            } else {
+                if (nt == 128) k_push<R, 128, false><<<pb, 128, push_smem, st>>>(a);
+                else k_push<R, 256, false><<<pb, 256, push_smem, st>>>(a);
+            }
             count_launch(ctx);
         }
     }
@@ -1290,6 +1326,10 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
 }
 
 void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
+    if (in.cfg.shape != PIC_SHAPE_NGP) {  // cloud-in-cell (pic_cic.cu)
+        cic_deposit(ctx, in, walls);
+        return;
+    }
     DepositArgs a{};
     a.nleaf = in.nleaf;
     a.nsp = 0;

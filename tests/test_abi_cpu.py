@@ -60,7 +60,8 @@ def test_missing_library_fails_loudly(monkeypatch):
 def test_bad_configuration_is_refused_before_any_device_call():
     from paper_1604_07713_gb300 import workloads as W
     G.build()
-    for bad in (dict(precision=7), dict(n_species=3), dict(dt=0.0), dict(max_level=12), dict(mg_rel_tol=0.0)):
+    for bad in (dict(precision=7), dict(n_species=3), dict(dt=0.0), dict(max_level=12), dict(mg_rel_tol=0.0),
+                dict(shape=3), dict(shape=1, max_level=2)):
         cfg = W.base_config(**bad)
         with pytest.raises(G.PicError) as e:
             G.pic_create(cfg)

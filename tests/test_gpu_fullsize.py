@@ -93,7 +93,7 @@ def test_streamer_full_size_properties_and_sampled_step():
         pp = sim.push_params(s)
         O.lib().or_push_mcc(C.byref(M._c), C.byref(pp), O._ptr(E), n, O._ptr(x), O._ptr(y), O._ptr(vx), O._ptr(vy),
                             O._ptr(vz), O._ptr(ids), O._ptr(leaf), O._ptr(new_leaf), O._ptr(spawn), O._ptr(sv),
-                            O._ptr(svi), O._ptr(dec))
+                            O._ptr(svi), O._ptr(dec), None)
         U0, P, U1st, siz = dec.reshape(n, 4).T
         # rounding margin of the collision decisions (FP32 against FP64 arithmetic)
         margin = (U0 >= 0) & (np.abs(U0 - P) <= 1e-6 * np.maximum(P, 1e-30))

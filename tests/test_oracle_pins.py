@@ -731,3 +731,119 @@ def test_time_averages_restart_when_the_grid_changes():
     sim2.step(3)
     st = sim2.adapt(mesh=True, particles=False)["mesh"]
     assert st["refined"] > 0 and sim2.diag["samples"] == 0 and sim2.diag["we"].size == sim2.mesh.nleaf
+
+
+# --------------------------------------------------------------------------------------
+# Cloud-in-cell shapes on uniform meshes (§3: CIC-EM momentum-conserving, CIC-EC energy-
+# conserving)
+# --------------------------------------------------------------------------------------
+def _cic_weights_of(x, y, nx, ny, h, px=True, py=True):
+    """The charge each cell receives from a unit charge at (x, y), from the oracle's deposit."""
+    Q = np.zeros(nx * ny)
+    O.lib().or_cic_deposit(nx, ny, h, int(px), int(py), 1, O._ptr(np.array([x])), O._ptr(np.array([y])),
+                           O._ptr(np.array([1.0])), 1.0, O._ptr(Q))
+    return Q
+
+
+def test_cic_weights_are_the_overlap_of_a_cell_sized_cloud():
+    """The CIC weight of a cell is the area of the cell shared with a square of the cell's size
+    centred on the particle (worked out geometrically here), in the interior; a particle at a
+    cell centre gives that cell everything; at a Dirichlet wall the weight beyond the wall folds
+    into the boundary cell, so the total stays 1.  Fails for: weights of the wrong corner,
+    a half-cell offset missing, or the folded weight dropped."""
+    nx, ny, h = 8, 6, 0.5
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x, y = 1.0 + 2.0 * rng.random(), 1.0 + 1.0 * rng.random()
+        Q = _cic_weights_of(x, y, nx, ny, h)
+        ref = np.zeros(nx * ny)
+        for j in range(ny):
+            for i in range(nx):
+                ox = max(0.0, min(x + h / 2, (i + 1) * h) - max(x - h / 2, i * h))
+                oy = max(0.0, min(y + h / 2, (j + 1) * h) - max(y - h / 2, j * h))
+                ref[i + nx * j] = ox * oy / (h * h)
+        assert np.abs(Q - ref).max() < 1e-14
+    Q = _cic_weights_of(2.75, 1.25, nx, ny, h)
+    assert Q[5 + nx * 2] == 1.0 and Q.sum() == 1.0
+    Q = _cic_weights_of(0.1, 1.25, nx, ny, h, px=False)       # within half a cell of x = 0
+    assert abs(Q.sum() - 1.0) < 1e-15 and Q[0 + nx * 2] == 1.0
+
+
+def _cic_sim(shape, n=60, seed=4, bcx=W.BC_PERIODIC):
+    M = O.Mesh(16, 8, 0.125, 0, bcx, O.BC_PERIODIC)
+    cfg = W.base_config(precision=W.FP64, n_species=1, dt=0.01, eps0=1.0, q=[-1.0], m=[1.0], bc_x=bcx,
+                        bc_y=W.BC_PERIODIC, shape=shape, phi_right=0.7)
+    sim = O.Sim(cfg, M)
+    rng = np.random.default_rng(seed)
+    x = rng.random(n) * M.lx; y = rng.random(n) * M.ly; w = rng.random(n) + 0.5
+    z = np.zeros(n)
+    cfg["rho_background"] = w.sum() / (M.lx * M.ly)             # neutral periodic box
+    sim.load(0, x, y, z, z, z, w)
+    sim.fields()
+    return sim
+
+
+def test_cic_em_conserves_momentum_and_cic_ec_does_not():
+    """CIC-EM gathers E (central differences at the cell centres) with the deposit's weights,
+    so the total force on all particles of a periodic box vanishes to rounding (no self-force,
+    action equals reaction); CIC-EC's gradient of the interpolated potential does not.  Fails
+    for: an EM gather whose weights differ from the deposit's (e.g. the nearest centre), or
+    one-sided differences."""
+    for shape, zero in ((1, True), (2, False)):
+        sim = _cic_sim(shape)
+        sp = sim.species[0]
+        ex, ey = sim.cic_field(sp)
+        F = np.array([np.sum(sp.q * sp.w * ex), np.sum(sp.q * sp.w * ey)])
+        scale = np.sum(np.abs(sp.q * sp.w) * np.hypot(ex, ey))
+        assert (np.abs(F).max() < 1e-12 * scale) == zero, (shape, F, scale)
+
+
+def test_cic_ec_force_is_minus_the_gradient_of_the_interpolated_potential():
+    """CIC-EC: E at a particle is -grad of Phi(x) = sum_c W_c(x) phi_c with the deposit's own
+    weights W_c (taken here from the deposit of a unit charge), checked by central differences
+    inside one cell quarter (Phi is bilinear there, so they are exact); CIC-EM is not.  Fails
+    for: EM-style gathering of centre fields, or a sign error."""
+    for shape in (1, 2):
+        sim = _cic_sim(shape)
+        M = sim.mesh
+        rng = np.random.default_rng(9)
+        worst = 0.0
+        for _ in range(40):
+            # a point in the interior of a cell quarter, at least d away from its edges
+            i, j = rng.integers(0, 2 * M.nx0), rng.integers(0, 2 * M.ny0)
+            q = M.h0 / 2
+            x, y = (i + 0.2 + 0.6 * rng.random()) * q, (j + 0.2 + 0.6 * rng.random()) * q
+            d = 0.05 * q
+            phi_at = lambda a, b: _cic_weights_of(a, b, M.nx0, M.ny0, M.h0) @ sim.phi
+            gx = (phi_at(x + d, y) - phi_at(x - d, y)) / (2 * d)
+            gy = (phi_at(x, y + d) - phi_at(x, y - d)) / (2 * d)
+            sp = O.Species(-1.0, 1.0, np.array([x]), np.array([y]), *[np.zeros(1) for _ in range(4)],
+                           np.zeros(1, np.uint64), M.locate([x], [y]))
+            ex, ey = sim.cic_field(sp)
+            worst = max(worst, abs(ex[0] + gx), abs(ey[0] + gy))
+        scale = np.abs(np.diff(sim.phi)).max() / M.h0
+        assert (worst < 1e-9 * scale) == (shape == 2), (shape, worst, scale)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_cic_uniform_field_between_plates_is_exact(shape):
+    """No charge, plates at x = 0 (0 V) and x = Lx (0.7 V): phi is linear and both gathers give
+    E = -0.7 / Lx at every particle, walls included."""
+    M = O.Mesh(16, 8, 0.125, 0, O.BC_DIRICHLET, O.BC_PERIODIC)
+    cfg = W.base_config(precision=W.FP64, n_species=1, dt=0.01, eps0=1.0, q=[-1.0], m=[1.0],
+                        bc_x=W.BC_DIRICHLET, bc_y=W.BC_PERIODIC, shape=shape, phi_right=0.7)
+    sim = O.Sim(cfg, M)
+    rng = np.random.default_rng(2)
+    n = 200
+    x = rng.random(n) * M.lx; y = rng.random(n) * M.ly; z = np.zeros(n)
+    sim.load(0, x, y, z, z, z, z)
+    sim.fields()
+    ex, ey = sim.cic_field(sim.species[0])
+    assert np.abs(ex + 0.7 / M.lx).max() < 1e-12 and np.abs(ey).max() < 1e-12
+
+
+def test_cic_deposit_conserves_charge_at_walls():
+    sim = _cic_sim(1, bcx=W.BC_DIRICHLET)
+    sp = sim.species[0]
+    Q = sim.charge()
+    assert abs(Q.sum() - sp.q * sp.w.sum()) < 1e-13 * sp.w.sum()
