@@ -445,7 +445,11 @@ def run_gpu(args):
     rs = 8 if args.precision == "fp64" else 4
     move_ms, move_launches = phases["move"]
     push_label = f"k_push<{'double' if rs == 8 else 'float'}> in-place push (both species)"
-    if move_ms == 0.0 and phases.get("graph", (0.0, 0))[0] > 0.0:
+    graph_ms = phases.get("graph", (0.0, 0))[0]
+    if ensemble and move_ms > 0.0 and graph_ms > 0.0:
+        # the batched step's replays time their phases inside the graph (event nodes)
+        push_label = f"k_push_batch<{'double' if rs == 8 else 'float'}> (every instance, both species)"
+    if move_ms == 0.0 and graph_ms > 0.0:
         # an ensemble replays whole steps as one graph: the push cannot be timed alone, so the
         # whole step's time stands in (a lower bound of the push's fraction)
         move_ms = phases["graph"][0]
@@ -454,14 +458,17 @@ def run_gpu(args):
     alg_bytes = (11 * rs + 4) * particle_steps + leaf_steps * 2 * (10 * rs + 12)
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
     tr = _traffic_record(name) if args.precision == "fp32" else None
-    tot_ms = sum(v[0] for v in phases.values())
+    # with phases timed inside graph replays, the replay's total is not a phase of its own
+    inner = graph_ms > 0.0 and any(v[0] > 0.0 for k, v in phases.items() if k != "graph")
+    tot_ms = sum(v[0] for k, v in phases.items() if not (inner and k == "graph"))
     roofline = {"bound": "hbm", "kernel": push_label,
                 "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": tr["move_dram_bytes_per_step"] if tr else None,
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_step": alg_bytes / args.steps,
-                "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items() if v[1]}}
+                "phase_share": {k: round(v[0] / max(1e-9, tot_ms), 4) for k, v in phases.items()
+                                if v[1] and not (inner and k == "graph")}}
     # The whole particle cycle (deposit, corner field, list preparation, push, scans and list
     # repairs, per-leaf sorts): the push's algorithmic bytes plus the corner field written and
     # the deposit's per-leaf charge, over the summed CUDA-event time of those phases.  Records
@@ -470,7 +477,7 @@ def run_gpu(args):
     cycle_phases = ("deposit", "node_e", "lists", "scan", "move", "sort")
     cycle_ms = sum(phases[k][0] for k in cycle_phases if k in phases)
     cycle_bytes = alg_bytes + leaf_steps * (8 * rs + 8)
-    if cycle_ms > 0.0 and phases.get("graph", (0.0, 0))[0] == 0.0:
+    if cycle_ms > 0.0 and (graph_ms == 0.0 or inner):
         ca = cycle_bytes / (cycle_ms * 1e-3) / 1e9
         roofline["particle_cycle"] = {"achieved": ca, "frac": ca / hbm_peak, "unit": "GB/s",
                                       "phases": list(cycle_phases), "ms_per_step": cycle_ms / args.steps,

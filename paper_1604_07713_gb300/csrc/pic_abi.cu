@@ -132,10 +132,17 @@ void DeviceArena::release_all() {
     blocks.clear();
 }
 
+// Outside a capture the events are recorded on the stream; while a batched step is captured
+// with phase timing they become event nodes of the graph (external records), read after each
+// replay.
 Phase::Phase(pic_ctx *c, int p) : ctx(c), phase(p), launches0(c->launches) {
     if (ctx->timing) {
         cudaEventCreate(&a);
         cudaEventRecord(a, ctx->stream);
+    } else if (ctx->capturing && ctx->capture_phases && ctx->event_pool.size() >= 2) {
+        a = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        GB_CUDA(cudaEventRecordWithFlags(a, ctx->stream, cudaEventRecordExternal));
     }
 }
 Phase::~Phase() {
@@ -144,6 +151,11 @@ Phase::~Phase() {
         cudaEventCreate(&b);
         cudaEventRecord(b, ctx->stream);
         ctx->trec.push_back(TimingRec{phase, a, b, ctx->launches - launches0});
+    } else if (a && ctx->capturing && ctx->capture_phases) {
+        cudaEvent_t b = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        cudaEventRecordWithFlags(b, ctx->stream, cudaEventRecordExternal);
+        ctx->graph_trec.push_back(TimingRec{phase, a, b, ctx->launches - launches0});
     }
 }
 
@@ -383,6 +395,7 @@ pic_status pic_destroy(pic_ctx *ctx) {
     }
     ctx->batch_mem.release_all();
     graph_release(ctx);
+    for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
     for (auto st : ctx->fork) cudaStreamDestroy(st);
     for (auto ev : ctx->fork_ev) cudaEventDestroy(ev);
     if (ctx->d_step) cudaFree(ctx->d_step);
@@ -770,6 +783,10 @@ pic_status pic_set_timing(pic_ctx *ctx, int32_t on) {
             cudaEventDestroy(r.b);
         }
         ctx->trec.clear();
+        for (int k = 0; k < 16; ++k) {
+            ctx->graph_ms[k] = 0.0;
+            ctx->graph_launches[k] = 0;
+        }
         ctx->timing = on != 0;
         return PIC_OK;
     });
@@ -790,6 +807,10 @@ pic_status pic_get_timing(pic_ctx *ctx, double *ms, int64_t *launches, int32_t n
             GB_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
             if (ms) ms[r.phase] += t;
             if (launches) launches[r.phase] += r.launches;
+        }
+        for (int k = 0; k < m && k < 16; ++k) {  // phases inside graph replays
+            if (ms) ms[k] += ctx->graph_ms[k];
+            if (launches) launches[k] += ctx->graph_launches[k];
         }
         return PIC_OK;
     });

@@ -92,10 +92,24 @@ void join_into(pic_ctx *ctx, cudaStream_t main) {
 
 void capture_step(pic_ctx *ctx) {
     graph_release(ctx);
-    ensure_branches(ctx);
     const int n = (int)ctx->inst.size();
     std::vector<std::array<double, 4>> walls(n);
     for (int i = 0; i < n; ++i) walls_at(ctx->inst[i], ctx->step, walls[i].data());
+    std::vector<Instance *> list;
+    std::vector<const double *> wl;
+    for (int i = 0; i < n; ++i) {
+        list.push_back(&ctx->inst[i]);
+        wl.push_back(walls[i].data());
+    }
+    const bool batched = batch_possible(ctx);
+    if (batched) {  // the tables of the batched launches, uploaded before the capture
+        poisson_batch_items(ctx, list);
+        batch_prepare_particles(ctx);
+        batch_prepare_node_e(ctx);
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        ensure_branches(ctx);
+    }
     cudaStream_t cs;
     GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t saved = ctx->stream;
@@ -103,36 +117,54 @@ void capture_step(pic_ctx *ctx) {
     const int64_t l0 = ctx->launches;
     ctx->timing = false;
     ctx->capturing = true;
+    ctx->capture_phases = batched && saved_timing;  // a linear graph: phases in sequence
+    if (ctx->capture_phases)
+        while (ctx->event_pool.size() < 32) {  // two per phase of the step
+            cudaEvent_t ev = nullptr;
+            GB_CUDA(cudaEventCreate(&ev));
+            ctx->event_pool.push_back(ev);
+        }
     ctx->stream = cs;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     try {
         if (e != cudaSuccess) GB_CUDA(e);
-        // deposits, branch per instance
-        fork_from(ctx, cs);
-        for (int i = 0; i < n; ++i) {
-            ctx->stream = ctx->fork[i % ctx->fork.size()];
-            deposit(ctx, ctx->inst[i], walls[i].data());
+        if (batched) {
+            // one launch per phase over every instance
+            {
+                Phase ph(ctx, PIC_PHASE_DEPOSIT);
+                deposit_batch(ctx);
+            }
+            {
+                Phase ph(ctx, PIC_PHASE_POISSON);
+                poisson_solve_batch(ctx, list, wl);
+            }
+            {
+                Phase ph(ctx, PIC_PHASE_NODE_E);
+                node_e_batch(ctx);
+            }
+            particle_step_batch(ctx);
+        } else {
+            // deposits, branch per instance
+            fork_from(ctx, cs);
+            for (int i = 0; i < n; ++i) {
+                ctx->stream = ctx->fork[i % ctx->fork.size()];
+                deposit(ctx, ctx->inst[i], walls[i].data());
+            }
+            ctx->stream = cs;
+            join_into(ctx, cs);
+            // one launch solves every instance's Poisson problem
+            poisson_solve_batch(ctx, list, wl);
+            // corner fields and particle steps, branch per instance
+            fork_from(ctx, cs);
+            for (int i = 0; i < n; ++i) {
+                ctx->stream = ctx->fork[i % ctx->fork.size()];
+                node_e(ctx, ctx->inst[i], walls[i].data());
+                particle_step(ctx, ctx->inst[i], ctx->step, false);
+            }
+            ctx->stream = cs;
+            join_into(ctx, cs);
         }
-        ctx->stream = cs;
-        join_into(ctx, cs);
-        // one launch solves every instance's Poisson problem
-        std::vector<Instance *> list;
-        std::vector<const double *> wl;
-        for (int i = 0; i < n; ++i) {
-            list.push_back(&ctx->inst[i]);
-            wl.push_back(walls[i].data());
-        }
-        poisson_solve_batch(ctx, list, wl);
-        // corner fields and particle steps, branch per instance
-        fork_from(ctx, cs);
-        for (int i = 0; i < n; ++i) {
-            ctx->stream = ctx->fork[i % ctx->fork.size()];
-            node_e(ctx, ctx->inst[i], walls[i].data());
-            particle_step(ctx, ctx->inst[i], ctx->step, false);
-        }
-        ctx->stream = cs;
-        join_into(ctx, cs);
         e = cudaStreamEndCapture(cs, &graph);
     } catch (...) {
         cudaStreamEndCapture(cs, &graph);
@@ -140,6 +172,7 @@ void capture_step(pic_ctx *ctx) {
         ctx->stream = saved;
         ctx->timing = saved_timing;
         ctx->capturing = false;
+        ctx->capture_phases = false;
         ctx->launches = l0;
         cudaStreamDestroy(cs);
         throw;
@@ -147,6 +180,9 @@ void capture_step(pic_ctx *ctx) {
     ctx->stream = saved;
     ctx->timing = saved_timing;
     ctx->capturing = false;
+    ctx->graph_timed = ctx->capture_phases;
+    ctx->capture_phases = false;
+    ctx->batch.on = batched;
     ctx->graph_nodes = ctx->launches - l0;
     ctx->launches = l0;
     cudaStreamDestroy(cs);
@@ -159,8 +195,10 @@ void capture_step(pic_ctx *ctx) {
 }
 
 bool graph_current(const pic_ctx *ctx) {
+    // a batched step is captured with phase events exactly when timing is on
+    const bool timed_ok = !batch_possible(const_cast<pic_ctx *>(ctx)) || ctx->graph_timed == ctx->timing;
     return ctx->step_graph && ctx->graph_mesh_epoch == ctx->mesh_epoch && ctx->graph_lists_epoch == ctx->lists_epoch &&
-           ctx->graph_tune_epoch == ctx->tune.epoch;
+           ctx->graph_tune_epoch == ctx->tune.epoch && timed_ok;
 }
 }  // namespace
 
@@ -212,6 +250,15 @@ void graph_step(pic_ctx *ctx) {
         GB_CUDA(cudaGraphLaunch(ctx->step_graph, ctx->stream));
         count_launch(ctx, ctx->graph_nodes);
     }
+    if (ctx->timing && ctx->graph_timed) {  // the phases inside this replay
+        GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (const TimingRec &r : ctx->graph_trec) {
+            float t = 0.f;
+            GB_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            ctx->graph_ms[r.phase] += t;
+            ctx->graph_launches[r.phase] += r.launches;
+        }
+    }
     // the host side of what the replay did
     for (Instance &in : ctx->inst) {
         walls_at(in, ctx->step, in.last_walls);
@@ -225,6 +272,47 @@ void graph_release(pic_ctx *ctx) {
         cudaGraphExecDestroy(ctx->step_graph);
         ctx->step_graph = nullptr;
     }
+    if (!ctx->graph_trec.empty()) {
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &r : ctx->graph_trec) {  // back to the pool
+            ctx->event_pool.push_back(r.a);
+            ctx->event_pool.push_back(r.b);
+        }
+        ctx->graph_trec.clear();
+    }
+    ctx->graph_timed = false;
+    if (!ctx->batch.bufs.empty()) {  // a replay in flight may still read the tables
+        cudaStreamSynchronize(ctx->stream);
+        for (void *p : ctx->batch.bufs) cudaFree(p);
+    }
+    ctx->batch = BatchStep{};
+}
+
+// The batched step needs one kernel instantiation for all instances: every instance with the
+// nearest-grid-point shape (the cloud-in-cell push gathers from a patch per leaf) and one
+// precision.
+bool batch_possible(pic_ctx *ctx) {
+    for (const Instance &in : ctx->inst)
+        if (in.cfg.shape != PIC_SHAPE_NGP || in.cfg.precision != ctx->inst.front().cfg.precision) return false;
+    return !ctx->inst.empty();
+}
+
+void *batch_upload(pic_ctx *ctx, const void *src, size_t bytes) {
+    void *p = nullptr;
+    GB_CUDA(cudaMalloc(&p, std::max<size_t>(bytes, 16)));
+    ctx->batch.bufs.push_back(p);
+    if (src && bytes) GB_CUDA(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    else GB_CUDA(cudaMemsetAsync(p, 0, std::max<size_t>(bytes, 16), ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));  // the host table may go out of scope
+    return p;
+}
+
+std::vector<int4> batch_chunks(const std::vector<int64_t> &nleaf, int64_t per) {
+    std::vector<int4> ch;
+    for (size_t k = 0; k < nleaf.size(); ++k)
+        for (int64_t lb = 0; lb < nleaf[k]; lb += per)
+            ch.push_back(make_int4((int)k, (int)lb, (int)std::min<int64_t>(nleaf[k], lb + per), 0));
+    return ch;
 }
 
 void report_all(pic_ctx *ctx) {

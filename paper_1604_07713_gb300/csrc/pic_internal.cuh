@@ -233,8 +233,32 @@ struct Tuning {
     int push_bps = 0;        // resident push blocks per SM (0: as many as fit)
     int graph_div = 4;       // captured ensemble steps: each push takes 1/graph_div of the GPU
     int branches = 16;       // captured ensemble steps: parallel branches
+    int batch_leaves = 64;   // batched ensemble steps: leaves per push block (a multiple of 32)
     double best_ms = 0.0;    // best step time the tuner measured
     int64_t epoch = 0;       // bumped on every change (a captured step is captured again)
+};
+// Device tables of the batched ensemble step (one launch per phase over every instance):
+// `tab` holds one entry per instance or per (instance, species), `chunks` one int4
+// {entry, first leaf, end leaf, 0} per block.  Built and uploaded before the step is
+// captured; freed when it is captured again.
+struct BatchTab {
+    const void *tab = nullptr;
+    const int4 *chunks = nullptr;
+    int n = 0, nchunks = 0;
+};
+// A segmented exclusive scan: per segment {in, out, n, first tile}, per block {segment, tile}.
+struct ScanPlan {
+    const void *segs = nullptr;
+    const int2 *tiles = nullptr;
+    int nseg = 0, ntiles = 0;
+    int32_t *scratch = nullptr;
+};
+struct BatchStep {
+    bool on = false;  // the captured step is the batched one
+    BatchTab dep, nodee, lists, push[2], sort, sort_med, bump;
+    ScanPlan ranks, spawns, relay5, relay7;
+    int32_t *flag = nullptr;  // device word: any instance has records in its overflow store
+    std::vector<void *> bufs;
 };
 }  // namespace gbpic
 
@@ -246,7 +270,7 @@ struct pic_ctx {
     int64_t launches = 0;
     bool timing = false;
     std::vector<gbpic::TimingRec> trec;
-    std::vector<cudaEvent_t> event_pool;
+    std::vector<cudaEvent_t> event_pool;  // created before a timed capture, taken by its phases
     std::vector<gbpic::Instance> inst;
     int precision = PIC_FP32;
     // batched one-block Poisson solves (instances whose meshes fit one block)
@@ -271,6 +295,13 @@ struct pic_ctx {
     int64_t report_epoch = -1;
     gbpic::Tuning tune;
     int64_t graph_tune_epoch = -1;
+    gbpic::BatchStep batch;          // tables of the batched ensemble step (pic_graph.cu)
+    // phase timing inside replays of the batched step: event nodes captured per phase (when
+    // timing was on at the capture), read after each timed replay
+    bool capture_phases = false, graph_timed = false;
+    std::vector<gbpic::TimingRec> graph_trec;
+    double graph_ms[16] = {};
+    int64_t graph_launches[16] = {};
     int32_t fault_balance_sweeps = 0;  // injected fault: bound of the adaptation's balance closure (0: none)
 };
 
@@ -364,6 +395,8 @@ void mesh_build(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t
 void mesh_build_device(pic_ctx *ctx, Instance &in, int64_t n);  // from in.root/morton/lev
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]);
 void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev);
+void batch_prepare_node_e(pic_ctx *ctx);
+void node_e_batch(pic_ctx *ctx);
 // pic_abi.cu
 void set_mesh_impl(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t n_leaves,
                    const uint32_t *root, const uint32_t *morton, const uint8_t *level);
@@ -373,6 +406,7 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]);
 void poisson_reset_warm_start(pic_ctx *ctx, Instance &in);
 void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list,
                          const std::vector<const double *> &walls);
+void poisson_batch_items(pic_ctx *ctx, const std::vector<Instance *> &list);  // outside a capture
 // pic_particles.cu
 void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *x,
                     const double *y, const double *vx, const double *vy, const double *vz,
@@ -386,6 +420,10 @@ void ensure_capacity(pic_ctx *ctx, Instance &in);
 void ensure_slots(pic_ctx *ctx, Instance &in, int s, int64_t slots);
 void refresh_counts(pic_ctx *ctx, Instance &in);  // sp.n := exact record totals (syncs)
 void walls_at(const Instance &in, int64_t step, double walls[4]);
+// the batched ensemble step: tables (before the capture), then the launches (captured)
+void batch_prepare_particles(pic_ctx *ctx);
+void deposit_batch(pic_ctx *ctx);
+void particle_step_batch(pic_ctx *ctx);
 // pic_lists.cu
 void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap);
 void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl);
@@ -396,6 +434,9 @@ void list_ranks(pic_ctx *ctx, Species &sp, int64_t nl);       // rank0 from star
 void count_totals(pic_ctx *ctx, Instance &in);  // flags[1] of every species, device side
 void place_overflow(pic_ctx *ctx, Instance &in, int s);  // tail moves, else re-layout
 void repairs_release(Instance &in);                       // the cached repair graphs
+BatchTab batch_prepare_lists(pic_ctx *ctx);                // per (instance, species) list arrays
+void lists_prep_batch(pic_ctx *ctx);                      // step reset and record counts
+void repairs_batch(pic_ctx *ctx);                         // overflow repairs of every instance
 // Capture into the graph that stream `st` is capturing: a one-thread kernel that reads *value,
 // then an IF node whose body (the launches `body` issues on ctx->stream) runs when it was
 // nonzero.  The body's launches are not counted (they run only when needed).
@@ -406,6 +447,13 @@ void one_step(pic_ctx *ctx);  // one step of every instance (graph replay or lau
 void graph_step(pic_ctx *ctx);            // one step of every instance as one graph replay
 void graph_prepare(pic_ctx *ctx);         // capture (if out of date) and upload the step graph
 void graph_release(pic_ctx *ctx);
+bool batch_possible(pic_ctx *ctx);        // every instance NGP, one precision: one launch per phase
+void *batch_upload(pic_ctx *ctx, const void *src, size_t bytes);  // device copy, freed with the tables
+template <typename T> const T *batch_upload(pic_ctx *ctx, const std::vector<T> &v) {
+    return (const T *)batch_upload(ctx, (const void *)v.data(), v.size() * sizeof(T));
+}
+// Blocks over the leaves of every entry: {entry, first, end, 0}, `per` leaves each.
+std::vector<int4> batch_chunks(const std::vector<int64_t> &nleaf, int64_t per);
 void report_all(pic_ctx *ctx);            // exact totals, error flags, solver stats of every instance (syncs)
 void fields_all(pic_ctx *ctx, int64_t step);
 void species_compact(pic_ctx *ctx, Instance &in, int s);  // leaf-order re-layout, tail freed
@@ -438,5 +486,10 @@ pic_status guarded_call(pic_ctx *ctx, pic_status (*fn)(void *), void *arg);
 void exclusive_scan_i32(pic_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
                         int32_t *scratch, const int32_t *gate = nullptr);
 int64_t scan_scratch_elems(int64_t n);
+// segments {in, out, n}: out[0..n) = exclusive scan of in, out[n] = total, one launch per pass
+// With gates, segment k does nothing while *gate[k] == 0.
+ScanPlan scan_plan(pic_ctx *ctx, const std::vector<const int32_t *> &in, const std::vector<int32_t *> &out,
+                   const std::vector<int64_t> &n, const std::vector<const int32_t *> &gate = {});
+void exclusive_scan_i32_batch(pic_ctx *ctx, const ScanPlan &p);
 
 }  // namespace gbpic

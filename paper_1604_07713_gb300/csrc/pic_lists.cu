@@ -30,13 +30,19 @@ inline unsigned warp_blocks(int64_t nw) {
 
 // seg[L] = c + list_slack(c) with c = a[L] (+ b[L]); with `room` (a re-layout: b = this
 // step's entering records) the leaf also keeps room for one more step of that inflow.
-__global__ void k_seg_sizes(int64_t nl, const int32_t *__restrict__ a, const int32_t *__restrict__ b, int room,
-                            int32_t *__restrict__ seg, const int32_t *__restrict__ gate) {
+__device__ __forceinline__ void seg_sizes(int64_t nl, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                                          int room, int32_t *__restrict__ seg, const int32_t *__restrict__ gate,
+                                          int64_t i0, int64_t stride) {
     if (gate && *gate == 0) return;
-    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < nl; L += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t L = i0; L < nl; L += stride) {
         const int32_t c = a[L] + (b ? b[L] : 0);
         seg[L] = c + list_slack(c) + (room ? b[L] : 0);
     }
+}
+__global__ void k_seg_sizes(int64_t nl, const int32_t *__restrict__ a, const int32_t *__restrict__ b, int room,
+                            int32_t *__restrict__ seg, const int32_t *__restrict__ gate) {
+    seg_sizes(nl, a, b, room, seg, gate, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+              (int64_t)gridDim.x * blockDim.x);
 }
 
 // A re-layout whose inflow room does not fit the buffer lays out without it (flags[7]).
@@ -96,15 +102,16 @@ __device__ __forceinline__ void copy_record(SoA<R> t, int64_t q, SoA<R> d, int64
 // for its staying and entering records and free slots, the staying records and the entering
 // records already in free slots copied there.  A leaf that does not fit any more marks the
 // tail as used up (flags[5]) and keeps its segment; the re-layout then takes over.
+// The warp takes the moved leaves warp, warp + nw, ...
 template <typename R>
-__global__ void k_move_to_tail(const int32_t *__restrict__ moved, int64_t nl, int64_t cap,
-                               int32_t *__restrict__ start, int32_t *__restrict__ end, int32_t *__restrict__ lim,
-                               const int32_t *__restrict__ stay, const int32_t *__restrict__ fill, SoA<R> d,
-                               uint32_t *__restrict__ key, uint32_t *__restrict__ aux, int32_t *__restrict__ flags) {
+__device__ __forceinline__ void move_to_tail(const int32_t *__restrict__ moved, int64_t nl, int64_t cap,
+                                             int32_t *__restrict__ start, int32_t *__restrict__ end,
+                                             int32_t *__restrict__ lim, const int32_t *__restrict__ stay,
+                                             const int32_t *__restrict__ fill, SoA<R> d, uint32_t *__restrict__ key,
+                                             uint32_t *__restrict__ aux, int32_t *__restrict__ flags, int64_t warp,
+                                             int64_t nw) {
     if (flags[0] == 0) return;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nm = moved[nl];
     for (int64_t i = warp; i < nm; i += nw) {
         const int32_t L = moved[i];
@@ -132,47 +139,67 @@ __global__ void k_move_to_tail(const int32_t *__restrict__ moved, int64_t nl, in
         }
     }
 }
+template <typename R>
+__global__ void k_move_to_tail(const int32_t *__restrict__ moved, int64_t nl, int64_t cap,
+                               int32_t *__restrict__ start, int32_t *__restrict__ end, int32_t *__restrict__ lim,
+                               const int32_t *__restrict__ stay, const int32_t *__restrict__ fill, SoA<R> d,
+                               uint32_t *__restrict__ key, uint32_t *__restrict__ aux, int32_t *__restrict__ flags) {
+    move_to_tail<R>(moved, nl, cap, start, end, lim, stay, fill, d, key, aux, flags,
+                    ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
 
 // Repair 2: the overflow store's records join their moved leaf at their slot.
+// The thread takes the records i0, i0 + stride, ...; `first` does the statistics.
 template <typename R>
-__global__ void k_place_ovf(const int32_t *__restrict__ end, int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
-                            const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
-                            const int32_t *__restrict__ oslot, SoA<R> d, uint32_t *__restrict__ key,
-                            uint32_t *__restrict__ aux, const int32_t *__restrict__ moved, int64_t nl,
-                            int32_t *__restrict__ flags) {
+__device__ __forceinline__ void place_ovf(const int32_t *__restrict__ end, int64_t cap, SoA<R> o,
+                                          const uint32_t *__restrict__ okey, const uint32_t *__restrict__ oaux,
+                                          const int32_t *__restrict__ odest, const int32_t *__restrict__ oslot,
+                                          SoA<R> d, uint32_t *__restrict__ key, uint32_t *__restrict__ aux,
+                                          const int32_t *__restrict__ moved, int64_t nl, int32_t *__restrict__ flags,
+                                          int64_t i0, int64_t stride, bool first) {
     const int32_t n = flags[0] < cap ? flags[0] : (int32_t)cap;  // beyond cap: err is set already
     if (n == 0) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {  // statistics
+    if (first) {  // statistics
         flags[3] += n;
         flags[6] += moved[nl];
     }
     if (flags[5]) return;  // the re-layout places them
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = i0; i < n; i += stride) {
         const int32_t q = end[odest[i]] + oslot[i];
         copy_record(d, q, o, i);
         key[q] = okey[i];
         aux[q] = oaux[i];
     }
 }
+template <typename R>
+__global__ void k_place_ovf(const int32_t *__restrict__ end, int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
+                            const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
+                            const int32_t *__restrict__ oslot, SoA<R> d, uint32_t *__restrict__ key,
+                            uint32_t *__restrict__ aux, const int32_t *__restrict__ moved, int64_t nl,
+                            int32_t *__restrict__ flags) {
+    place_ovf<R>(end, cap, o, okey, oaux, odest, oslot, d, key, aux, moved, nl, flags,
+                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                 blockIdx.x == 0 && threadIdx.x == 0);
+}
 
 // Re-layout, step 1 (one warp per leaf): the staying records and the entering records that
 // found a free slot go to the scratch buffer at the new segment starts; staying records
 // first, entering records at their slot after them.
 template <typename R>
-__global__ void k_relayout_move(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
-                                const int32_t *__restrict__ lim, const int32_t *__restrict__ stay,
-                                const int32_t *__restrict__ fill, const int32_t *__restrict__ start_new, int64_t cap,
-                                SoA<R> d, const uint32_t *__restrict__ key, const uint32_t *__restrict__ aux,
-                                SoA<R> t, uint32_t *__restrict__ tkey, uint32_t *__restrict__ taux,
-                                const int32_t *__restrict__ flags, int32_t *__restrict__ err) {
+__device__ __forceinline__ void relayout_move(int64_t nl, const int32_t *__restrict__ start,
+                                              const int32_t *__restrict__ end, const int32_t *__restrict__ lim,
+                                              const int32_t *__restrict__ stay, const int32_t *__restrict__ fill,
+                                              const int32_t *__restrict__ start_new, int64_t cap, SoA<R> d,
+                                              const uint32_t *__restrict__ key, const uint32_t *__restrict__ aux,
+                                              SoA<R> t, uint32_t *__restrict__ tkey, uint32_t *__restrict__ taux,
+                                              const int32_t *__restrict__ flags, int32_t *__restrict__ err,
+                                              int64_t warp, int64_t nw, bool first) {
     if (flags[5] == 0) return;
     if ((int64_t)start_new[nl] > cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(err, 1);
+        if (first) atomicExch(err, 1);
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = warp; L < nl; L += nw) {
         const int32_t s0 = start[L], q0 = start_new[L], ns = stay[L];
         for (int32_t j = lane; j < ns; j += 32) copy_record(t, q0 + j, d, s0 + j);
@@ -185,52 +212,84 @@ __global__ void k_relayout_move(int64_t nl, const int32_t *__restrict__ start, c
         }
     }
 }
+template <typename R>
+__global__ void k_relayout_move(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                                const int32_t *__restrict__ lim, const int32_t *__restrict__ stay,
+                                const int32_t *__restrict__ fill, const int32_t *__restrict__ start_new, int64_t cap,
+                                SoA<R> d, const uint32_t *__restrict__ key, const uint32_t *__restrict__ aux,
+                                SoA<R> t, uint32_t *__restrict__ tkey, uint32_t *__restrict__ taux,
+                                const int32_t *__restrict__ flags, int32_t *__restrict__ err) {
+    relayout_move<R>(nl, start, end, lim, stay, fill, start_new, cap, d, key, aux, t, tkey, taux, flags, err,
+                     ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
+                     blockIdx.x == 0 && threadIdx.x == 0);
+}
 
 // Re-layout, step 2: the records of the overflow store join them at their slot.
 template <typename R>
-__global__ void k_relayout_ovf(const int32_t *__restrict__ stay, const int32_t *__restrict__ start_new, int64_t nl,
-                               int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
-                               const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
-                               const int32_t *__restrict__ oslot, SoA<R> t, uint32_t *__restrict__ tkey,
-                               uint32_t *__restrict__ taux, const int32_t *__restrict__ flags) {
+__device__ __forceinline__ void relayout_ovf(const int32_t *__restrict__ stay, const int32_t *__restrict__ start_new,
+                                             int64_t nl, int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
+                                             const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
+                                             const int32_t *__restrict__ oslot, SoA<R> t,
+                                             uint32_t *__restrict__ tkey, uint32_t *__restrict__ taux,
+                                             const int32_t *__restrict__ flags, int64_t i0, int64_t stride) {
     if (flags[5] == 0) return;
     const int32_t n = flags[0] < cap ? flags[0] : (int32_t)cap;
     if ((int64_t)start_new[nl] > cap) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = i0; i < n; i += stride) {
         const int32_t L = odest[i];
         const int32_t q = start_new[L] + stay[L] + oslot[i];
         copy_record(t, q, o, i);
         tkey[q] = okey[i]; taux[q] = oaux[i];
     }
 }
+template <typename R>
+__global__ void k_relayout_ovf(const int32_t *__restrict__ stay, const int32_t *__restrict__ start_new, int64_t nl,
+                               int64_t cap, SoA<R> o, const uint32_t *__restrict__ okey,
+                               const uint32_t *__restrict__ oaux, const int32_t *__restrict__ odest,
+                               const int32_t *__restrict__ oslot, SoA<R> t, uint32_t *__restrict__ tkey,
+                               uint32_t *__restrict__ taux, const int32_t *__restrict__ flags) {
+    relayout_ovf<R>(stay, start_new, nl, cap, o, okey, oaux, odest, oslot, t, tkey, taux, flags,
+                    (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
 
 // Re-layout, step 3: the scratch buffer back into the lists, the new segments, and end[L] at
 // the first entering record (where the entering sort expects it).
 template <typename R>
-__global__ void k_relayout_back(int64_t nl, const int32_t *__restrict__ start_new, const int32_t *__restrict__ stay,
-                                int64_t cap, SoA<R> t, const uint32_t *__restrict__ tkey,
-                                const uint32_t *__restrict__ taux, SoA<R> d, uint32_t *__restrict__ key,
-                                uint32_t *__restrict__ aux, int32_t *__restrict__ start, int32_t *__restrict__ end,
-                                int32_t *__restrict__ lim, int32_t *__restrict__ flags) {
+__device__ __forceinline__ void relayout_back(int64_t nl, const int32_t *__restrict__ start_new,
+                                              const int32_t *__restrict__ stay, int64_t cap, SoA<R> t,
+                                              const uint32_t *__restrict__ tkey, const uint32_t *__restrict__ taux,
+                                              SoA<R> d, uint32_t *__restrict__ key, uint32_t *__restrict__ aux,
+                                              int32_t *__restrict__ start, int32_t *__restrict__ end,
+                                              int32_t *__restrict__ lim, int32_t *__restrict__ flags, int64_t i0,
+                                              int64_t stride, bool first) {
     if (flags[5] == 0) return;
     const int64_t span = start_new[nl];
     if (span > cap) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < span; i += stride) {
+    for (int64_t i = i0; i < span; i += stride) {
         copy_record(d, i, t, i);
         key[i] = tkey[i]; aux[i] = taux[i];
     }
-    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L <= nl; L += stride) {
+    for (int64_t L = i0; L <= nl; L += stride) {
         start[L] = start_new[L];
         if (L < nl) {
             end[L] = start_new[L] + stay[L];
             lim[L] = start_new[L + 1];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first) {
         flags[2] += 1;  // statistics
         flags[4] = (int32_t)span;
     }
+}
+template <typename R>
+__global__ void k_relayout_back(int64_t nl, const int32_t *__restrict__ start_new, const int32_t *__restrict__ stay,
+                                int64_t cap, SoA<R> t, const uint32_t *__restrict__ tkey,
+                                const uint32_t *__restrict__ taux, SoA<R> d, uint32_t *__restrict__ key,
+                                uint32_t *__restrict__ aux, int32_t *__restrict__ start, int32_t *__restrict__ end,
+                                int32_t *__restrict__ lim, int32_t *__restrict__ flags) {
+    relayout_back<R>(nl, start_new, stay, cap, t, tkey, taux, d, key, aux, start, end, lim, flags,
+                     (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                     blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 // Every list of species s laid out again in leaf order with fresh free slots (the kernels
@@ -342,7 +401,202 @@ __global__ void k_compact_prep(int64_t nl, const int32_t *__restrict__ start, co
 __global__ void k_compact_done(int32_t *__restrict__ flags) {
     if (threadIdx.x == 0 && blockIdx.x == 0) flags[5] = 0;
 }
+
+// ---- the batched ensemble step: one entry per (instance, species) ------------------------
+struct ListEntry {
+    int64_t nl, cap;
+    int32_t *start, *end, *lim, *stay, *fill, *flags, *moved, *inc;
+    int32_t *spawn;  // ionizing electrons: spawn counts per leaf (else null)
+    void *d[7], *o[7];  // record arrays of the current buffer and of the overflow store (id last)
+    uint32_t *key, *aux, *okey, *oaux;
+    int32_t *odest, *oslot;
+    // the re-layout: new segment starts, the other buffer as scratch, the error flag
+    int32_t *start_new, *err;
+    void *t[7];
+    uint32_t *tkey, *taux;
+};
+template <typename R> __device__ __forceinline__ SoA<R> soa_of(void *const p[7]) {
+    SoA<R> a;
+    a.u = (R *)p[0]; a.v = (R *)p[1]; a.vx = (R *)p[2]; a.vy = (R *)p[3]; a.vz = (R *)p[4]; a.w = (R *)p[5];
+    a.id = (uint32_t *)p[6];
+    return a;
+}
+
+// Before the pushes, per entry: what k_step_reset clears, and the record counts whose scan
+// gives the list ranks (block = leaves [c.y, c.z) of entry c.x).
+__global__ void k_lists_prep_batch(const ListEntry *__restrict__ tab, const int4 *__restrict__ chunks) {
+    const int4 c = chunks[blockIdx.x];
+    const ListEntry &e = tab[c.x];
+    const int64_t L = (int64_t)c.y + threadIdx.x;
+    if (L < c.z) {
+        e.fill[L] = 0;
+        if (e.spawn) e.spawn[L] = 0;
+        e.inc[L] = e.end[L] - e.start[L];
+    }
+    if (L == 0) {
+        e.flags[0] = 0;
+        e.flags[5] = 0;
+        e.moved[e.nl] = 0;
+    }
+}
+
+// *out = 1 if flags[word] of any entry is nonzero, else 0 (one block).
+__global__ void k_any_flag(const ListEntry *__restrict__ tab, int n, int word, int32_t *__restrict__ out) {
+    int32_t any = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) any |= tab[i].flags[word] != 0 ? 1 : 0;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) *out = any;
+}
+
+// Repair 1 of every entry (blocks (x, entry)); entries without overflow return at once.
+template <typename R> __global__ void k_move_to_tail_batch(const ListEntry *__restrict__ tab) {
+    const ListEntry &e = tab[blockIdx.y];
+    move_to_tail<R>(e.moved, e.nl, e.cap, e.start, e.end, e.lim, e.stay, e.fill, soa_of<R>(e.d), e.key, e.aux,
+                    e.flags, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                    ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+template <typename R> __global__ void k_place_ovf_batch(const ListEntry *__restrict__ tab) {
+    const ListEntry &e = tab[blockIdx.y];
+    place_ovf<R>(e.end, e.cap, soa_of<R>(e.o), e.okey, e.oaux, e.odest, e.oslot, soa_of<R>(e.d), e.key, e.aux,
+                 e.moved, e.nl, e.flags, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (int64_t)gridDim.x * blockDim.x, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// The re-layout of every entry whose tail was used up (flags[5]); blocks (x, entry), the
+// other entries return at once.  Same steps as relayout_lists.
+__global__ void k_seg_sizes_batch(const ListEntry *__restrict__ tab, int room, int gate_word) {
+    const ListEntry &e = tab[blockIdx.y];
+    seg_sizes(e.nl, e.stay, e.fill, room, e.inc, e.flags + gate_word,
+              (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+__global__ void k_relayout_fit_batch(const ListEntry *__restrict__ tab, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const ListEntry &e = tab[i];
+        e.flags[7] = (e.flags[5] && (int64_t)e.start_new[e.nl] > e.cap) ? 1 : 0;
+    }
+}
+template <typename R> __global__ void k_relayout_move_batch(const ListEntry *__restrict__ tab) {
+    const ListEntry &e = tab[blockIdx.y];
+    relayout_move<R>(e.nl, e.start, e.end, e.lim, e.stay, e.fill, e.start_new, e.cap, soa_of<R>(e.d), e.key, e.aux,
+                     soa_of<R>(e.t), e.tkey, e.taux, e.flags, e.err,
+                     ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
+                     blockIdx.x == 0 && threadIdx.x == 0);
+}
+template <typename R> __global__ void k_relayout_ovf_batch(const ListEntry *__restrict__ tab) {
+    const ListEntry &e = tab[blockIdx.y];
+    relayout_ovf<R>(e.stay, e.start_new, e.nl, e.cap, soa_of<R>(e.o), e.okey, e.oaux, e.odest, e.oslot,
+                    soa_of<R>(e.t), e.tkey, e.taux, e.flags, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                    (int64_t)gridDim.x * blockDim.x);
+}
+template <typename R> __global__ void k_relayout_back_batch(const ListEntry *__restrict__ tab) {
+    const ListEntry &e = tab[blockIdx.y];
+    relayout_back<R>(e.nl, e.start_new, e.stay, e.cap, soa_of<R>(e.t), e.tkey, e.taux, soa_of<R>(e.d), e.key, e.aux,
+                     e.start, e.end, e.lim, e.flags, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                     (int64_t)gridDim.x * blockDim.x, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+template <typename R> void relayout_batch(pic_ctx *ctx) {
+    const BatchTab &t = ctx->batch.lists;
+    const ListEntry *tab = (const ListEntry *)t.tab;
+    const unsigned n = (unsigned)t.n;
+    cudaStream_t st = ctx->stream;
+    k_seg_sizes_batch<<<dim3(4, n), kT, 0, st>>>(tab, 1, 5);
+    exclusive_scan_i32_batch(ctx, ctx->batch.relay5);
+    k_relayout_fit_batch<<<(n + kT - 1) / kT, kT, 0, st>>>(tab, (int)n);
+    k_seg_sizes_batch<<<dim3(4, n), kT, 0, st>>>(tab, 0, 7);
+    exclusive_scan_i32_batch(ctx, ctx->batch.relay7);
+    k_relayout_move_batch<R><<<dim3(8, n), kT, 0, st>>>(tab);
+    k_relayout_ovf_batch<R><<<dim3(4, n), kT, 0, st>>>(tab);
+    k_relayout_back_batch<R><<<dim3(16, n), kT, 0, st>>>(tab);
+    count_launch(ctx, 6);
+}
+
+template <typename R> void repairs_batch_impl(pic_ctx *ctx) {
+    const BatchTab &t = ctx->batch.lists;
+    const ListEntry *tab = (const ListEntry *)t.tab;
+    int32_t *flag = ctx->batch.flag;
+    k_any_flag<<<1, kT, 0, ctx->stream>>>(tab, t.n, 0, flag);
+    count_launch(ctx);
+    capture_if(ctx, ctx->stream, flag, [&]() {
+        k_move_to_tail_batch<R><<<dim3(2, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
+        k_place_ovf_batch<R><<<dim3(4, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
+        // a tail used up: those species' lists are laid out again
+        k_any_flag<<<1, kT, 0, ctx->stream>>>(tab, t.n, 5, flag + 1);
+        capture_if(ctx, ctx->stream, flag + 1, [&]() { relayout_batch<R>(ctx); });
+    });
+    count_launch(ctx);
+}
 }  // namespace
+
+// Entries (instance, species) in instance order, and the prep blocks over their leaves.
+BatchTab batch_prepare_lists(pic_ctx *ctx) {
+    std::vector<ListEntry> tab;
+    std::vector<int64_t> nls;
+    for (Instance &in : ctx->inst) {
+        const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
+        for (int s = 0; s < in.cfg.n_species; ++s) {
+            Species &sp = in.sp[s];
+            ListEntry e{};
+            e.nl = in.nleaf;
+            e.cap = sp.cap;
+            e.start = sp.start; e.end = sp.end; e.lim = sp.lim; e.stay = sp.stay; e.fill = sp.fill;
+            e.flags = sp.flags; e.moved = sp.moved; e.inc = sp.inc;
+            e.spawn = s == 0 && ionize ? sp.spawn : nullptr;
+            for (int k = 0; k < 6; ++k) {
+                e.d[k] = sp.arr[sp.cur][k];
+                e.o[k] = sp.ovf[k];
+            }
+            e.d[6] = sp.id[sp.cur];
+            e.o[6] = sp.ovf_id;
+            e.key = sp.key; e.aux = sp.aux; e.okey = sp.ovf_key; e.oaux = sp.ovf_aux;
+            e.odest = sp.ovf_dest; e.oslot = sp.ovf_slot;
+            e.start_new = sp.start_new;
+            e.err = in.d_err;
+            for (int k = 0; k < 6; ++k) e.t[k] = sp.arr[sp.cur ^ 1][k];
+            e.t[6] = sp.id[sp.cur ^ 1];
+            e.tkey = sp.key + sp.cap;
+            e.taux = sp.aux + sp.cap;
+            tab.push_back(e);
+            nls.push_back(in.nleaf);
+        }
+    }
+    // the re-layout's two gated scans of the new segment sizes
+    std::vector<const int32_t *> in;
+    std::vector<int32_t *> out;
+    std::vector<const int32_t *> g5, g7;
+    for (const ListEntry &e : tab) {
+        in.push_back(e.inc);
+        out.push_back(e.start_new);
+        g5.push_back(e.flags + 5);
+        g7.push_back(e.flags + 7);
+    }
+    ctx->batch.relay5 = scan_plan(ctx, in, out, nls, g5);
+    ctx->batch.relay7 = scan_plan(ctx, in, out, nls, g7);
+    const std::vector<int4> ch = batch_chunks(nls, kT);
+    BatchTab t;
+    t.tab = batch_upload(ctx, tab);
+    t.chunks = batch_upload(ctx, ch);
+    t.n = (int)tab.size();
+    t.nchunks = (int)ch.size();
+    return t;
+}
+
+void lists_prep_batch(pic_ctx *ctx) {
+    const BatchTab &t = ctx->batch.lists;
+    k_lists_prep_batch<<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>((const ListEntry *)t.tab, t.chunks);
+    count_launch(ctx);
+    check_launch("lists_prep_batch");
+}
+
+// The overflow repairs of every entry: one reduction and one IF node per step; its body (run
+// only when some entry has records in its overflow store) moves leaves to the tail and places
+// the records for every entry at once, then re-lays out the species whose tail was used up.
+void repairs_batch(pic_ctx *ctx) {
+    if (ctx->inst.front().cfg.precision == PIC_FP64) repairs_batch_impl<double>(ctx);
+    else repairs_batch_impl<float>(ctx);
+    check_launch("repairs_batch");
+}
 
 // Per-leaf arrays of one species for nl leaves (segments empty).
 void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {

@@ -527,6 +527,72 @@ template <typename T> FieldView<T> field_view(const Instance &in, const double w
     return F;
 }
 
+// The corner field of every instance of an ensemble in one launch: block b takes the 4 corners
+// of the leaves [c.y, c.z) of instance c.x, whose view (with the step's wall potentials read
+// from the device) sits in shared memory.
+template <typename R> struct NodeEEntry {
+    FieldView<R> F;
+    R *stencil;
+};
+template <typename R>
+__global__ void __launch_bounds__(kT) k_node_e_batch(const NodeEEntry<R> *__restrict__ tab,
+                                                     const int4 *__restrict__ chunks) {
+    __shared__ NodeEEntry<R> se;
+    const int4 c = chunks[blockIdx.x];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(tab + c.x);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&se);
+        for (int k = threadIdx.x; k < (int)(sizeof(NodeEEntry<R>) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) se.F.wall[threadIdx.x] = se.F.wall_dev[threadIdx.x];
+    __syncthreads();
+    const int64_t l = (int64_t)c.y + (threadIdx.x >> 2);
+    if (l >= c.z) return;
+    const int cc = (int)(threadIdx.x & 3);
+    const FieldView<R> &F = se.F;
+    const int32_t s = F.L.side((int32_t)l);
+    R ex, ey;
+    F.node(F.L.ix[l] + ((cc & 1) ? s : 0), F.L.iy[l] + ((cc & 2) ? s : 0), ex, ey);
+    se.stencil[8 * l + 2 * cc] = ex;
+    se.stencil[8 * l + 2 * cc + 1] = ey;
+}
+
+template <typename R> void batch_prepare_node_e_impl(pic_ctx *ctx) {
+    std::vector<NodeEEntry<R>> tab;
+    std::vector<int64_t> nls;
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    for (Instance &in : ctx->inst) {
+        NodeEEntry<R> e;
+        e.F = field_view<R>(in, zero);
+        e.F.wall_dev = in.d_walls;
+        e.stencil = (R *)in.stencil;
+        tab.push_back(e);
+        nls.push_back(in.lv[0].n);
+    }
+    const std::vector<int4> ch = batch_chunks(nls, kT / 4);
+    BatchTab &t = ctx->batch.nodee;
+    t.tab = batch_upload(ctx, tab);
+    t.chunks = batch_upload(ctx, ch);
+    t.n = (int)tab.size();
+    t.nchunks = (int)ch.size();
+}
+
+void batch_prepare_node_e(pic_ctx *ctx) {
+    if (ctx->inst.front().cfg.precision == PIC_FP64) batch_prepare_node_e_impl<double>(ctx);
+    else batch_prepare_node_e_impl<float>(ctx);
+}
+
+void node_e_batch(pic_ctx *ctx) {
+    const BatchTab &t = ctx->batch.nodee;
+    if (ctx->inst.front().cfg.precision == PIC_FP64)
+        k_node_e_batch<double><<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>((const NodeEEntry<double> *)t.tab, t.chunks);
+    else
+        k_node_e_batch<float><<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>((const NodeEEntry<float> *)t.tab, t.chunks);
+    count_launch(ctx);
+    check_launch("node_e_batch");
+}
+
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {
     Level &g = in.lv[0];
     // a captured step reads the wall potentials of its time from the device

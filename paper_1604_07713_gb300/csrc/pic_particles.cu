@@ -144,9 +144,8 @@ template <typename R> __device__ __forceinline__ double leaf_weight(const LeafSu
     return st + ((double)((const R *)w.ent_hi)[L] + (double)((const R *)w.ent_lo)[L]);
 }
 template <typename R>
-__global__ void k_deposit_sums(DepositArgs a, LeafSums w0, LeafSums w1) {
-    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= a.nleaf) return;
+__device__ __forceinline__ void deposit_sums_leaf(const DepositArgs &a, const LeafSums &w0, const LeafSums &w1,
+                                                  int64_t L) {
     double total = a.q[0] * leaf_weight<R>(w0, L);
     if (a.nsp > 1) total += a.q[1] * leaf_weight<R>(w1, L);
     const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
@@ -154,6 +153,22 @@ __global__ void k_deposit_sums(DepositArgs a, LeafSums w0, LeafSums w1) {
     double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
     for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * (a.wall_dev ? a.wall_dev[k] : a.wall[k]);
     a.b[L] = bl;
+}
+template <typename R>
+__global__ void k_deposit_sums(DepositArgs a, LeafSums w0, LeafSums w1) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < a.nleaf) deposit_sums_leaf<R>(a, w0, w1, L);
+}
+// Every instance of an ensemble: block b takes the leaves [c.y, c.z) of instance c.x.
+struct DepositEntry {
+    DepositArgs a;
+    LeafSums w0, w1;
+};
+template <typename R>
+__global__ void k_deposit_sums_batch(const DepositEntry *__restrict__ tab, const int4 *__restrict__ chunks) {
+    const int4 c = chunks[blockIdx.x];
+    const int64_t L = (int64_t)c.y + threadIdx.x;
+    if (L < c.z) deposit_sums_leaf<R>(tab[c.x].a, tab[c.x].w0, tab[c.x].w1, L);
 }
 
 // ------------------------------------------------------------------------------------
@@ -411,13 +426,12 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
 // NT threads per block (a tuned launch shape); 768 threads per SM either way: 80 registers.
 // CIC: the field is gathered from the leaf's per-quarter cloud-in-cell coefficients (32 per
 // leaf, lane k holding coefficient k) instead of the bilinear corner field.
+// The warp walks the leaves first, first + nw, ... below last (all lanes call it).
 template <typename R, int NT, bool CIC>
-__global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
-    extern __shared__ unsigned char push_smem[];
-    Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
+__device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, const int64_t first, const int64_t last,
+                                            const int64_t nw) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = first;
     // order keys: an entering record's list rank before the step; a spawned record's is the
     // species total plus its parent's rank, so it sorts after every entering record
     const uint32_t span = (uint32_t)a.rank0[a.nleaf];
@@ -436,15 +450,15 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
         nid = a.d.id[qq]; nwt = a.d.w[qq];
     };
     int32_t np0 = 0, np1 = 0;
-    if (warp < a.nleaf) {
+    if (warp < last) {
         np0 = a.start[warp]; np1 = a.end[warp];
         if (np0 + lane < np1) fetch(np0 + lane);
     }
-    for (int64_t Lw = warp; Lw < a.nleaf; Lw += nw) {
+    for (int64_t Lw = warp; Lw < last; Lw += nw) {
         const int32_t L = (int32_t)Lw;
         const int32_t p0 = np0, p1 = np1;
         np0 = np1 = 0;
-        if (Lw + nw < a.nleaf) { np0 = a.start[Lw + nw]; np1 = a.end[Lw + nw]; }
+        if (Lw + nw < last) { np0 = a.start[Lw + nw]; np1 = a.end[Lw + nw]; }
         if (p0 == p1) {
             if (lane == 0) {
                 a.stay[L] = 0;
@@ -602,6 +616,34 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push(PushArgs<R> a) {
     if (qn > 0) run_deferred(a, q, (qhead + lane) & (kQueue - 1), lane < qn, span, ion_span, step, run_leaf, run_count);
 }
 
+// One instance: persistent warps over all its leaves.
+template <typename R, int NT, bool CIC>
+__global__ void __launch_bounds__(NT, 768 / NT) k_push(const __grid_constant__ PushArgs<R> a) {
+    extern __shared__ unsigned char push_smem[];
+    Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    push_leaves<R, NT, CIC>(a, q, warp, a.nleaf, nw);
+}
+
+// Every instance of an ensemble in one launch: block b takes the leaves [c.y, c.z) of
+// instance c.x (c = chunks[b]), the instance's arguments copied to shared memory.
+template <typename R, int NT, bool CIC>
+__global__ void __launch_bounds__(NT, 768 / NT) k_push_batch(const PushArgs<R> *__restrict__ tab,
+                                                             const int4 *__restrict__ chunks) {
+    extern __shared__ unsigned char push_smem[];
+    __shared__ PushArgs<R> sa;
+    const int4 c = chunks[blockIdx.x];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(tab + c.x);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+        for (int k = threadIdx.x; k < (int)(sizeof(PushArgs<R>) / 4); k += NT) dst[k] = src[k];
+    }
+    __syncthreads();
+    Queue<R> &q = reinterpret_cast<Queue<R> *>(push_smem)[threadIdx.x >> 5];
+    push_leaves<R, NT, CIC>(sa, q, (int64_t)c.y + (threadIdx.x >> 5), (int64_t)c.z, NT / 32);
+}
+
 __global__ void k_bump_next_id(unsigned long long *next_id, const int32_t *__restrict__ spawn_total) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *next_id += 2ull * (unsigned long long)(*spawn_total);
 }
@@ -715,12 +757,11 @@ constexpr int kSortBig = 16384;  // one block sorts up to this many entries in s
 // leaf, bitonic network on (key, slot) pairs in dynamic shared memory, gather through the
 // scratch buffer.  Regions longer than kSortBig rank every key against all others.
 template <typename R>
-__global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t) {
-    extern __shared__ unsigned long long bk[];
-    __shared__ R red_hi[16], red_lo[16];
+__device__ __forceinline__ void sort_big_leaves(const SortArgs &a, const SoA<R> &d, const SoA<R> &t, int32_t first,
+                                                int32_t stride, unsigned long long *bk, R *red_hi, R *red_lo) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
     const int32_t nbig = a.big[a.nleaf];
-    for (int32_t li = blockIdx.x; li < nbig; li += gridDim.x) {
+    for (int32_t li = first; li < nbig; li += stride) {
         const int32_t L = a.big[li];
         int32_t b0, k, q0;
         entering_region(a, L, b0, k, q0);
@@ -787,6 +828,13 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t) {
+    extern __shared__ unsigned long long bk[];
+    __shared__ R red_hi[16], red_lo[16];
+    sort_big_leaves<R>(a, d, t, blockIdx.x, gridDim.x, bk, red_hi, red_lo);
+}
+
 constexpr int kSortLane = 8;  // entering regions up to this long are sorted by a leaf's 8-lane group
 
 // The entering weights of a leaf in order (a few entering particles: one lane, Kahan), as the
@@ -806,14 +854,15 @@ template <typename R> __device__ __forceinline__ void entering_weight_seq(const 
 // overlap).  Medium regions (up to kSortSmem) are queued for k_sort_medium, long ones for
 // k_sort_big.  Sets end[L] and, with stay sums, the leaf's deposit weight: the staying sum
 // plus the entering weights in key order.
+// The warp takes the groups of 4 leaves W = first, first + stride, ... with leaves below last.
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<R> t) {
+__device__ __forceinline__ void sort_entering_groups(const SortArgs &a, const SoA<R> &d, const SoA<R> &t,
+                                                     int64_t first, int64_t last, int64_t stride) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t W = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; W * 4 < a.nleaf; W += nwarp) {
+    for (int64_t W = first; W * 4 < last; W += stride) {
         const int64_t L = W * 4 + g;
-        const bool has = L < a.nleaf;
+        const bool has = L < last;
         int32_t b0 = 0, k = 0, q0 = 0;
         if (has && gl == 0) entering_region(a, L, b0, k, q0);
         b0 = __shfl_sync(0xFFFFFFFFu, b0, 0, 8);
@@ -865,23 +914,28 @@ __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<
     }
 }
 
-// Medium entering regions (kSortLane < k <= kSortSmem): one warp per listed leaf.
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R> t) {
-    __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
+__global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<R> t) {
+    sort_entering_groups<R>(a, d, t, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, a.nleaf,
+                            ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// Medium entering regions (kSortLane < k <= kSortSmem): one warp per listed leaf; the warp
+// takes the list entries first, first + stride, ... below last.
+template <typename R>
+__device__ __forceinline__ void sort_medium_leaves(const SortArgs &a, const SoA<R> &d, const SoA<R> &t, int64_t first,
+                                                   int64_t last, int64_t stride, unsigned long long *wsm) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t nmed = a.med[a.nleaf];
-    for (int64_t i = warp; i < nmed; i += nw) {
+    const int64_t nmed = min((int64_t)a.med[a.nleaf], last);
+    for (int64_t i = first; i < nmed; i += stride) {
         const int64_t L = a.med[i];
         int32_t b0, k, q0;
         if (lane == 0) entering_region(a, L, b0, k, q0);
         b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
-        sort_region<R>(a, span, b0, k, q0, lane, d, t, sm_keys[threadIdx.x >> 5]);
+        sort_region<R>(a, span, b0, k, q0, lane, d, t, wsm);
         if (a.ent_hi) {
             if (k <= 16) {
                 if (lane == 0) entering_weight_seq<R>(a, L, d, q0, k);
@@ -898,6 +952,77 @@ __global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R>
         }
         if (lane == 0) a.end[L] = q0 + k;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R> t) {
+    __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
+    sort_medium_leaves<R>(a, d, t, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, a.nleaf,
+                          ((int64_t)gridDim.x * blockDim.x) >> 5, sm_keys[threadIdx.x >> 5]);
+}
+
+// ---- the sorts of every (instance, species) of an ensemble, one launch per pass ----------
+template <typename R> struct SortEntry {
+    SortArgs a;
+    SoA<R> d, t;
+};
+template <typename T> __device__ __forceinline__ void copy_words(T &dst, const T &src) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+    uint32_t *o = reinterpret_cast<uint32_t *>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(T) / 4); k += blockDim.x) o[k] = s[k];
+}
+
+// Before the entering sorts: the medium and long region lists of every entry are empty.
+template <typename R> __global__ void k_sort_prep_batch(const SortEntry<R> *__restrict__ tab, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        tab[i].a.big[tab[i].a.nleaf] = 0;
+        tab[i].a.med[tab[i].a.nleaf] = 0;
+    }
+}
+// Block b: the leaves [c.y, c.z) of entry c.x (c.y a multiple of 4).
+template <typename R>
+__global__ void __launch_bounds__(kT) k_sort_entering_batch(const SortEntry<R> *__restrict__ tab,
+                                                            const int4 *__restrict__ chunks) {
+    __shared__ SortEntry<R> se;
+    const int4 c = chunks[blockIdx.x];
+    copy_words(se, tab[c.x]);
+    __syncthreads();
+    sort_entering_groups<R>(se.a, se.d, se.t, (int64_t)(c.y >> 2) + (threadIdx.x >> 5), (int64_t)c.z, kT / 32);
+}
+// Block b: the entries [c.y, c.z) of the medium-region list of entry c.x (the list can hold
+// every leaf; blocks past its length return at once).
+template <typename R>
+__global__ void __launch_bounds__(kT) k_sort_medium_batch(const SortEntry<R> *__restrict__ tab,
+                                                          const int4 *__restrict__ chunks) {
+    __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
+    __shared__ SortEntry<R> se;
+    const int4 c = chunks[blockIdx.x];
+    if (c.y >= tab[c.x].a.med[tab[c.x].a.nleaf]) return;
+    copy_words(se, tab[c.x]);
+    __syncthreads();
+    sort_medium_leaves<R>(se.a, se.d, se.t, (int64_t)c.y + (threadIdx.x >> 5), (int64_t)c.z, kT / 32,
+                          sm_keys[threadIdx.x >> 5]);
+}
+template <typename R>
+__global__ void __launch_bounds__(512) k_sort_big_batch(const SortEntry<R> *__restrict__ tab) {
+    extern __shared__ unsigned long long bk[];
+    __shared__ R red_hi[16], red_lo[16];
+    __shared__ SortEntry<R> se;
+    copy_words(se, tab[blockIdx.y]);
+    __syncthreads();
+    sort_big_leaves<R>(se.a, se.d, se.t, blockIdx.x, gridDim.x, bk, red_hi, red_lo);
+}
+
+// After the sorts: every ionizing instance's next id moves past its spawned pairs.
+struct BumpEntry {
+    unsigned long long *next_id;
+    const int32_t *spawn_total;
+};
+__global__ void k_bump_batch(const BumpEntry *__restrict__ tab, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) *tab[i].next_id += 2ull * (unsigned long long)(*tab[i].spawn_total);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1079,6 +1204,36 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     return a;
 }
 
+// The push of species s in a step: with ionization the electrons count their spawns per leaf
+// and put the spawned ions into the ion lists.
+template <typename R> PushArgs<R> step_push_args(Instance &in, int s, int64_t step) {
+    PushArgs<R> a = push_args<R>(in, s, step);
+    const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
+    if (s == 0 && ionize) {
+        a.spawn = in.sp[0].spawn;
+        if (in.cfg.n_species > 1) {
+            a.ion = list_put_args<R>(in.sp[1], in.nleaf);
+            a.ion_total = in.sp[1].rank0 + in.nleaf;
+        }
+    }
+    return a;
+}
+
+// The entering sort of species s in a step (spawned records get their ids; the entering
+// weight sums feed the next deposit).
+template <typename R> SortArgs step_sort_args(Instance &in, int s) {
+    Species &sp = in.sp[s];
+    SortArgs a = sort_args<R>(in, sp);
+    if (in.cfg.mcc && in.cfg.sigma_iz0 > 0.0) {
+        a.span = sp.rank0 + in.nleaf;  // the species total before the step
+        a.spawn_base = in.sp[0].spawn_base;
+    }
+    a.ion_bit = s == 1 ? 1u : 0u;
+    a.ent_hi = sp.ent_hi;
+    a.ent_lo = sp.ent_lo;
+    return a;
+}
+
 // Per species before a push: no entering records yet, nothing in the overflow store, no
 // moved leaves, the tail not used up, and (electrons with ionization) no spawns counted.
 __global__ void k_step_reset(int64_t nl, int32_t *__restrict__ fill, int32_t *__restrict__ flags,
@@ -1132,7 +1287,6 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     const unsigned pb = std::min<unsigned>(wb, ctx->capturing ? std::max(1u, full / (unsigned)std::max(1, ctx->tune.graph_div)) : full);
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
-    Species *ion = nsp > 1 ? &in.sp[1] : nullptr;
     {
         Phase ph(ctx, PIC_PHASE_LISTS);
         for (int s = 0; s < nsp; ++s) {
@@ -1146,15 +1300,8 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     {
         Phase ph(ctx, PIC_PHASE_MOVE);
         for (int s = 0; s < nsp; ++s) {
-            PushArgs<R> a = push_args<R>(in, s, step);
+            PushArgs<R> a = step_push_args<R>(in, s, step);
             if (ctx->capturing) a.step_dev = ctx->d_step;  // a captured step reads its number on the device
-            if (s == 0 && ionize) {
-                a.spawn = e.spawn;
-                if (ion) {
-                    a.ion = list_put_args<R>(*ion, nl);
-                    a.ion_total = ion->rank0 + nl;
-                }
-            }
             if (cic) {
                 if (nt == 128) k_push<R, 128, true><<<pb, 128, push_smem, st>>>(a);
                 else k_push<R, 256, true><<<pb, 256, push_smem, st>>>(a);
@@ -1174,15 +1321,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         Phase ph(ctx, PIC_PHASE_SORT);
         for (int s = 0; s < nsp; ++s) {
             Species &sp = in.sp[s];
-            SortArgs a = sort_args<R>(in, sp);
-            if (ionize) {
-                a.span = sp.rank0 + nl;  // the species total before the step
-                a.spawn_base = e.spawn_base;
-            }
-            a.ion_bit = s == 1 ? 1u : 0u;
-            a.ent_hi = sp.ent_hi;
-            a.ent_lo = sp.ent_lo;
-            sort_lists<R>(ctx, a, soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
+            sort_lists<R>(ctx, step_sort_args<R>(in, s), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
             sp.sums_valid = true;
         }
         if (ionize) {
@@ -1467,6 +1606,195 @@ void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, dou
     GB_CUDA(cudaStreamSynchronize(st));
     tmp.release_all();
     check_launch("particles_read");
+}
+
+// ------------------------------------------------------------------------------------
+// The batched ensemble step: every instance's particle phases in one launch per phase,
+// each block taking a range of leaves of one instance (or (instance, species) entry) from a
+// table built here before the step is captured.  Each instance's arithmetic is the one of
+// its own step (the same device functions on the same arguments), so a batched instance
+// equals the instance run alone bit for bit.
+// ------------------------------------------------------------------------------------
+namespace {
+template <typename R> void batch_prepare_impl(pic_ctx *ctx) {
+    BatchStep &B = ctx->batch;
+    std::vector<int64_t> nl_inst;
+    std::vector<DepositEntry> dep;
+    for (Instance &in : ctx->inst) {
+        nl_inst.push_back(in.nleaf);
+        DepositEntry e{};
+        DepositArgs &a = e.a;
+        a.nleaf = in.nleaf;
+        a.nsp = in.cfg.n_species;
+        for (int s = 0; s < a.nsp; ++s) {
+            a.start[s] = in.sp[s].start;
+            a.end[s] = in.sp[s].end;
+            a.w[s] = in.sp[s].arr[in.sp[s].cur][5];
+            a.q[s] = in.cfg.q[s];
+        }
+        a.lev = in.lv[0].lev;
+        a.lmax = in.lmax;
+        a.hf = in.h0 / (double)(1 << in.lmax);
+        a.rho_bg = in.cfg.rho_background;
+        a.inv_eps0 = 1.0 / in.cfg.eps0;
+        a.bcw = in.lv[0].bcw;
+        a.wall_dev = in.d_walls;
+        a.charge = in.charge;
+        a.b = in.bvec;
+        const Species &s1 = in.sp[in.cfg.n_species > 1 ? 1 : 0];
+        e.w0 = LeafSums{in.sp[0].stay_hi, in.sp[0].stay_lo, in.sp[0].ent_hi, in.sp[0].ent_lo};
+        e.w1 = LeafSums{s1.stay_hi, s1.stay_lo, s1.ent_hi, s1.ent_lo};
+        dep.push_back(e);
+    }
+    std::vector<int4> ch = batch_chunks(nl_inst, kT);
+    B.dep.tab = batch_upload(ctx, dep);
+    B.dep.chunks = batch_upload(ctx, ch);
+    B.dep.n = (int)dep.size();
+    B.dep.nchunks = (int)ch.size();
+
+    B.lists = batch_prepare_lists(ctx);
+
+    // pushes: species 0 of every instance, then species 1 of those that have it
+    for (int s = 0; s < 2; ++s) {
+        std::vector<PushArgs<R>> tab;
+        std::vector<int64_t> nls;
+        for (Instance &in : ctx->inst) {
+            if (s >= in.cfg.n_species) continue;
+            PushArgs<R> a = step_push_args<R>(in, s, ctx->step);
+            a.step_dev = ctx->d_step;
+            tab.push_back(a);
+            nls.push_back(in.nleaf);
+        }
+        B.push[s] = BatchTab{};
+        if (tab.empty()) continue;
+        ch = batch_chunks(nls, std::max(32, ctx->tune.batch_leaves));
+        B.push[s].tab = batch_upload(ctx, tab);
+        B.push[s].chunks = batch_upload(ctx, ch);
+        B.push[s].n = (int)tab.size();
+        B.push[s].nchunks = (int)ch.size();
+    }
+
+    // list ranks of every entry; spawn offsets of every ionizing instance
+    std::vector<const int32_t *> sin;
+    std::vector<int32_t *> sout;
+    std::vector<int64_t> sn;
+    for (Instance &in : ctx->inst)
+        for (int s = 0; s < in.cfg.n_species; ++s) {
+            sin.push_back(in.sp[s].inc);
+            sout.push_back(in.sp[s].rank0);
+            sn.push_back(in.nleaf);
+        }
+    B.ranks = scan_plan(ctx, sin, sout, sn);
+    sin.clear(); sout.clear(); sn.clear();
+    std::vector<BumpEntry> bump;
+    for (Instance &in : ctx->inst)
+        if (in.cfg.mcc && in.cfg.sigma_iz0 > 0.0) {
+            sin.push_back(in.sp[0].spawn);
+            sout.push_back(in.sp[0].spawn_base);
+            sn.push_back(in.nleaf);
+            bump.push_back(BumpEntry{in.d_next_id, in.sp[0].spawn_base + in.nleaf});
+        }
+    B.spawns = scan_plan(ctx, sin, sout, sn);
+    B.bump = BatchTab{};
+    if (!bump.empty()) {
+        B.bump.tab = batch_upload(ctx, bump);
+        B.bump.n = (int)bump.size();
+    }
+
+    // sorts of every entry
+    std::vector<SortEntry<R>> sorts;
+    std::vector<int64_t> nls;
+    for (Instance &in : ctx->inst)
+        for (int s = 0; s < in.cfg.n_species; ++s) {
+            Species &sp = in.sp[s];
+            sorts.push_back(SortEntry<R>{step_sort_args<R>(in, s), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1)});
+            nls.push_back(in.nleaf);
+        }
+    ch = batch_chunks(nls, kT);
+    B.sort.tab = batch_upload(ctx, sorts);
+    B.sort.chunks = batch_upload(ctx, ch);
+    B.sort.n = (int)sorts.size();
+    B.sort.nchunks = (int)ch.size();
+    ch = batch_chunks(nls, 4 * (kT / 32));  // medium regions: 4 leaves per warp
+    B.sort_med.tab = B.sort.tab;
+    B.sort_med.chunks = batch_upload(ctx, ch);
+    B.sort_med.n = B.sort.n;
+    B.sort_med.nchunks = (int)ch.size();
+    if (!B.flag) B.flag = (int32_t *)batch_upload(ctx, nullptr, 4 * sizeof(int32_t));
+
+    // shared-memory limits of the batched kernels (set outside the capture)
+    const size_t q256 = 8 * sizeof(Queue<R>), q128 = 4 * sizeof(Queue<R>);
+    GB_CUDA(cudaFuncSetAttribute(k_push_batch<R, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q256));
+    GB_CUDA(cudaFuncSetAttribute(k_push_batch<R, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q128));
+    GB_CUDA(cudaFuncSetAttribute(k_sort_big_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSortBig * sizeof(unsigned long long))));
+}
+
+template <typename R> void particle_step_batch_impl(pic_ctx *ctx) {
+    BatchStep &B = ctx->batch;
+    cudaStream_t st = ctx->stream;
+    {
+        Phase ph(ctx, PIC_PHASE_LISTS);
+        lists_prep_batch(ctx);
+        exclusive_scan_i32_batch(ctx, B.ranks);
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_MOVE);
+        const int nt = ctx->tune.push_threads == 128 ? 128 : 256;
+        const size_t smem = (size_t)(nt / 32) * sizeof(Queue<R>);
+        for (int s = 0; s < 2; ++s) {
+            const BatchTab &t = B.push[s];
+            if (!t.n) continue;
+            const PushArgs<R> *tab = (const PushArgs<R> *)t.tab;
+            if (nt == 128) k_push_batch<R, 128, false><<<(unsigned)t.nchunks, 128, smem, st>>>(tab, t.chunks);
+            else k_push_batch<R, 256, false><<<(unsigned)t.nchunks, 256, smem, st>>>(tab, t.chunks);
+            count_launch(ctx);
+        }
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_SCAN);
+        exclusive_scan_i32_batch(ctx, B.spawns);
+        repairs_batch(ctx);
+    }
+    {
+        Phase ph(ctx, PIC_PHASE_SORT);
+        const SortEntry<R> *tab = (const SortEntry<R> *)B.sort.tab;
+        const unsigned n = (unsigned)B.sort.n;
+        k_sort_prep_batch<R><<<(n + kT - 1) / kT, kT, 0, st>>>(tab, (int)n);
+        k_sort_entering_batch<R><<<(unsigned)B.sort.nchunks, kT, 0, st>>>(tab, B.sort.chunks);
+        k_sort_medium_batch<R><<<(unsigned)B.sort_med.nchunks, kT, 0, st>>>(tab, B.sort_med.chunks);
+        k_sort_big_batch<R><<<dim3(2, n), 512, kSortBig * sizeof(unsigned long long), st>>>(tab);
+        count_launch(ctx, 4);
+        if (B.bump.n) {
+            k_bump_batch<<<(unsigned)(B.bump.n + kT - 1) / kT, kT, 0, st>>>((const BumpEntry *)B.bump.tab, B.bump.n);
+            count_launch(ctx);
+        }
+        for (Instance &in : ctx->inst)
+            for (int s = 0; s < in.cfg.n_species; ++s) in.sp[s].sums_valid = true;
+    }
+    check_launch("particle_step_batch");
+}
+}  // namespace
+
+void batch_prepare_particles(pic_ctx *ctx) {
+    if (ctx->inst.front().cfg.precision == PIC_FP64) batch_prepare_impl<double>(ctx);
+    else batch_prepare_impl<float>(ctx);
+}
+
+void deposit_batch(pic_ctx *ctx) {
+    const BatchTab &t = ctx->batch.dep;
+    const DepositEntry *tab = (const DepositEntry *)t.tab;
+    if (ctx->inst.front().cfg.precision == PIC_FP64)
+        k_deposit_sums_batch<double><<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>(tab, t.chunks);
+    else
+        k_deposit_sums_batch<float><<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>(tab, t.chunks);
+    count_launch(ctx);
+    check_launch("deposit_batch");
+}
+
+void particle_step_batch(pic_ctx *ctx) {
+    if (ctx->inst.front().cfg.precision == PIC_FP64) particle_step_batch_impl<double>(ctx);
+    else particle_step_batch_impl<float>(ctx);
 }
 
 }  // namespace gbpic

@@ -1099,8 +1099,9 @@ void poisson_reset_warm_start(pic_ctx *ctx, Instance &in) {
 }
 
 // One launch for every instance whose mesh fits one block: block b solves instance b.
-void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list, const std::vector<const double *> &walls) {
-    if (list.empty()) return;
+// The batched solver's item table for `list` (copies issued on the context's stream, so a
+// step captured afterwards finds the table current and captures no copy).
+void poisson_batch_items(pic_ctx *ctx, const std::vector<Instance *> &list) {
     if (ctx->batch_epoch != ctx->mesh_epoch || ctx->batch_n != (int)list.size()) {
         ctx->batch_mem.release_all();
         ctx->batch_items = ctx->batch_mem.alloc(list.size() * sizeof(SmallSolve));
@@ -1113,6 +1114,11 @@ void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list, cons
         ctx->batch_epoch = ctx->mesh_epoch;
         ctx->batch_n = (int)list.size();
     }
+}
+
+void poisson_solve_batch(pic_ctx *ctx, const std::vector<Instance *> &list, const std::vector<const double *> &walls) {
+    if (list.empty()) return;
+    poisson_batch_items(ctx, list);
     for (size_t k = 0; k < list.size(); ++k) {
         for (int w = 0; w < 4; ++w) list[k]->last_walls[w] = walls[k][w];
         list[k]->mg_on_device = true;

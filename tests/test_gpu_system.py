@@ -115,12 +115,52 @@ def test_ensemble_steps_replay_one_graph_and_match_uncaptured_steps():
             ctx.step(1)
         ph = G.pic_get_timing(ctx.ctx)
         G.pic_set_timing(ctx.ctx, False)
-        assert ph["graph"][1] > 0 and ph["move"][1] == 0  # replays, no uncaptured particle step
+        # replays, their phases timed inside the graph: two batched pushes per replay
+        assert ph["graph"][1] > 0 and ph["move"][1] == 3 * 2
+        assert 0.0 < sum(v[0] for k, v in ph.items() if k != "graph") <= ph["graph"][0] * 1.01 + 0.05
         batched = [[ctx.particles(s, inst=i) for s in (0, 1)] for i in range(len(cases))]
     for i, (cfg, mesh, parts) in enumerate(cases):
         alone = _run_alone(cfg, mesh, parts, 4)
         for s in (0, 1):
             for k in ("id", "x", "vx", "w"):
+                assert np.array_equal(batched[i][s][k], alone[s][k]), (i, s, k)
+
+
+def test_batched_step_is_one_launch_per_phase_and_repairs_like_alone():
+    """The captured ensemble step runs every instance's phases in one launch each (about 20
+    graph nodes per step, whatever the number of instances), and its list repairs (tail moves,
+    re-layouts, spawned ions overflowing) equal those of each instance stepping alone."""
+    from test_gpu_lists import _beam_case
+    beam_iz = _beam_case(W.FP64, ionize=True)
+    tight = _beam_case(W.FP64, ionize=False, seed=12)
+    tight[0]["particle_capacity"] = tight[2][0]["x"].size + 40  # little room at the tail
+    cases = [beam_iz, tight, W.ccp(nx=32, ny=8, ppc=10, seed=3, precision=W.FP64, volt=200.0, ng=1e21, te=8.0)]
+    for i, (cfg, _, _) in enumerate(cases):
+        cfg["instance"] = i
+    steps = 4
+    with G.Context([c[0] for c in cases]) as ctx:
+        for i, (cfg, mesh, parts) in enumerate(cases):
+            ctx.set_mesh_dict(mesh, inst=i)
+            for s in sorted(parts):
+                ctx.load(s, **parts[s], inst=i)
+        ctx.step(1)
+        before = [[G.pic_get_list_stats(ctx.ctx, i, s) for s in (0, 1)] for i in range(len(cases))]
+        G.pic_set_timing(ctx.ctx, True)
+        ctx.step(steps - 1)
+        ph = G.pic_get_timing(ctx.ctx)
+        G.pic_set_timing(ctx.ctx, False)
+        after = [[G.pic_get_list_stats(ctx.ctx, i, s) for s in (0, 1)] for i in range(len(cases))]
+        batched = [[ctx.particles(s, inst=i) for s in (0, 1)] for i in range(len(cases))]
+    assert ph["move"][1] == 2 * (steps - 1) and ph["graph"][1] > 0  # every later step was a replay
+    assert ph["graph"][1] <= 24 * (steps - 1), ph["graph"]  # launches per replay
+    # the replays repaired lists: tail moves of the beam's electrons and spawned ions; the
+    # tight instance's electrons were laid out again (and repaired during the replays)
+    assert after[0][0][1] > before[0][0][1] and after[0][1][1] > before[0][1][1]
+    assert after[1][0][0] >= 1 and sum(after[1][0][:2]) > sum(before[1][0][:2])
+    for i, (cfg, mesh, parts) in enumerate(cases):
+        alone = _run_alone(cfg, mesh, parts, steps)
+        for s in (0, 1):
+            for k in ("id", "x", "y", "vx", "vy", "vz", "w"):
                 assert np.array_equal(batched[i][s][k], alone[s][k]), (i, s, k)
 
 
