@@ -689,35 +689,60 @@ __device__ __forceinline__ void entering_region(const SortArgs &a, int64_t L, in
 
 constexpr int kSortSmem = 512;  // per-warp shared-memory sort capacity (keys + slots)
 
-// Sort the k entries at [b0, b0 + k) into [q0, q0 + k) (one warp).  Up to 32 entries sort
+// Sort the k <= 32 P entries at [b0, b0 + k) into [q0, q0 + k) in registers (one warp): lane
+// j holds records b0 + j + 32 m; a record's rank is the number of smaller keys (keys are
+// distinct), counted against every key broadcast by shuffles.  Every record is in registers
+// before any is stored (the region and its destination may overlap).
+template <typename R, int P>
+__device__ __forceinline__ void sort_region_regs(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0,
+                                                 int lane, const SoA<R> &d) {
+    uint32_t key[P], id[P];
+    int rank[P];
+    R u[P], v[P], vx[P], vy[P], vz[P], w[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        const int32_t i = lane + 32 * m;
+        const int32_t p = b0 + i;
+        const bool act = i < k;
+        key[m] = act ? a.key[p] : 0xFFFFFFFFu;
+        rank[m] = 0;
+        u[m] = v[m] = vx[m] = vy[m] = vz[m] = w[m] = (R)0;
+        id[m] = 0;
+        if (act) {
+            u[m] = d.u[p]; v[m] = d.v[p]; vx[m] = d.vx[p]; vy[m] = d.vy[p]; vz[m] = d.vz[p]; w[m] = d.w[p];
+            id[m] = spawn_id(a, span, key[m], key[m] >= span ? a.aux[p] : 0u, d.id[p]);
+        }
+    }
+#pragma unroll
+    for (int mm = 0; mm < P; ++mm) {
+        const int nj = min(32, k - 32 * mm);  // keys of column mm (warp-uniform)
+        for (int j = 0; j < nj; ++j) {
+            const uint32_t o = __shfl_sync(0xFFFFFFFFu, key[mm], j);
+#pragma unroll
+            for (int m = 0; m < P; ++m) rank[m] += (o < key[m]) ? 1 : 0;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < P; ++m)
+        if (lane + 32 * m < k) {
+            const int32_t q = q0 + rank[m];
+            d.u[q] = u[m]; d.v[q] = v[m]; d.vx[q] = vx[m]; d.vy[q] = vy[m]; d.vz[q] = vz[m]; d.w[q] = w[m];
+            d.id[q] = id[m];
+        }
+    __syncwarp();
+}
+
+// Sort the k entries at [b0, b0 + k) into [q0, q0 + k) (one warp).  Up to 160 entries sort
 // in registers; up to 512 by a bitonic network on (key, slot) pairs in the warp's shared
 // memory followed by a gather through the scratch buffer `t`.
 template <typename R>
 __device__ void sort_region(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0, int lane, SoA<R> d,
                             SoA<R> t, unsigned long long *wsm) {
-    if (k <= 32) {
-        const bool act = lane < k;
-        const uint32_t kk = act ? a.key[b0 + lane] : 0xFFFFFFFFu;
-        int rank = 0;
-        for (int j = 0; j < k; ++j) {
-            const uint32_t o = __shfl_sync(0xFFFFFFFFu, kk, j);
-            rank += (o < kk) ? 1 : 0;
-        }
-        R u = 0, v = 0, vx = 0, vy = 0, vz = 0, w = 0;
-        uint32_t id = 0;
-        if (act) {
-            const int32_t p = b0 + lane;
-            u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p];
-            id = spawn_id(a, span, kk, kk >= span ? a.aux[p] : 0u, d.id[p]);
-        }
-        __syncwarp();
-        if (act) {
-            const int32_t q = q0 + rank;
-            d.u[q] = u; d.v[q] = v; d.vx[q] = vx; d.vy[q] = vy; d.vz[q] = vz; d.w[q] = w; d.id[q] = id;
-        }
-        __syncwarp();
-        return;
-    }
+    if (k <= 32) { sort_region_regs<R, 1>(a, span, b0, k, q0, lane, d); return; }
+    if (k <= 64) { sort_region_regs<R, 2>(a, span, b0, k, q0, lane, d); return; }
+    if (k <= 96) { sort_region_regs<R, 3>(a, span, b0, k, q0, lane, d); return; }
+    if (k <= 160) { sort_region_regs<R, 5>(a, span, b0, k, q0, lane, d); return; }
     // copy the region to the scratch buffer
     for (int32_t p = b0 + lane; p < b0 + k; p += 32) {
         t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p];
@@ -955,7 +980,7 @@ __device__ __forceinline__ void sort_medium_leaves(const SortArgs &a, const SoA<
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_medium(SortArgs a, SoA<R> d, SoA<R> t) {
+__global__ void __launch_bounds__(kT, 3) k_sort_medium(SortArgs a, SoA<R> d, SoA<R> t) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     sort_medium_leaves<R>(a, d, t, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, a.nleaf,
                           ((int64_t)gridDim.x * blockDim.x) >> 5, sm_keys[threadIdx.x >> 5]);
@@ -994,7 +1019,7 @@ __global__ void __launch_bounds__(kT) k_sort_entering_batch(const SortEntry<R> *
 // Block b: the entries [c.y, c.z) of the medium-region list of entry c.x (the list can hold
 // every leaf; blocks past its length return at once).
 template <typename R>
-__global__ void __launch_bounds__(kT) k_sort_medium_batch(const SortEntry<R> *__restrict__ tab,
+__global__ void __launch_bounds__(kT, 3) k_sort_medium_batch(const SortEntry<R> *__restrict__ tab,
                                                           const int4 *__restrict__ chunks) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     __shared__ SortEntry<R> se;
