@@ -83,6 +83,7 @@ class _PushParams(C.Structure):
 
 def _declare(L):
     L.or_philox4x32_10.argtypes = [_p, _p, _p]
+    L.or_philox2x32_10.argtypes = [_p, _u32, _p]
     L.or_philox_bulk.argtypes = [_i64, _p, _u32, _u32, _u32, _u32, _u32, _p]
     L.or_morton.argtypes = [_u32, _u32]
     L.or_morton.restype = _u32
@@ -109,6 +110,14 @@ def _declare(L):
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def philox2(ctr0: int, ctr1: int, key: int):
+    """Philox2x32-10 of one counter (Salmon et al., SC'11): the two output words."""
+    c = np.array([ctr0, ctr1], np.uint32)
+    out = np.zeros(2, np.uint32)
+    lib().or_philox2x32_10(_ptr(c), key & 0xFFFFFFFF, _ptr(out))
+    return int(out[0]), int(out[1])
 
 
 # ---------------------------------------------------------------------------------------

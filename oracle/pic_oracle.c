@@ -49,6 +49,21 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+/* Philox2x32-10 (same paper): a two-word counter, one 32 x 32 -> 64-bit product per round  */
+/* (multiplier 0xD256D193), the Weyl key schedule k + r 0x9E3779B9, ten rounds.            */
+void or_philox2x32_10(const uint32_t ctr_in[2], uint32_t key, uint32_t out[2])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) key += 0x9E3779B9u;
+        uint64_t p = (uint64_t)0xD256D193u * (uint64_t)c0;
+        uint32_t hi = (uint32_t)(p >> 32), lo = (uint32_t)p;
+        c0 = hi ^ c1 ^ key;
+        c1 = lo;
+    }
+    out[0] = c0; out[1] = c1;
+}
+
 /* Uniform in [0,1) from the top 24 bits: exactly representable in FP32 and FP64. */
 static double u24(uint32_t r) { return (double)(r >> 8) * (1.0 / 16777216.0); }
 
@@ -459,6 +474,16 @@ typedef struct {
     double lx, ly;
 } or_push_params;
 
+/* The collision test's uniform: Philox2x32-10 on the counter (id, step), keyed by the seed's */
+/* two words, the instance and the id's high word.                                            */
+static double draw_test(const or_push_params *p, uint64_t id)
+{
+    uint32_t ctr[2] = {(uint32_t)id, p->step}, r[2];
+    uint32_t key = p->key0 ^ p->key1 ^ (p->inst << 24) ^ (uint32_t)(id >> 32);
+    or_philox2x32_10(ctr, key, r);
+    return u24(r[0]);
+}
+
 static void draw4(const or_push_params *p, uint64_t id, uint32_t purpose, double u[4])
 {
     uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32) ^ (p->inst << 24), p->step, purpose};
@@ -554,8 +579,11 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
         if (!p->mcc) continue;
 
         /* Monte Carlo collision with the background gas */
+        /* U[0] decides whether the particle collides; U[1..3] (the purpose-0 4x32 words     */
+        /* after the first) decide the branch and the scattering angles                      */
         double U[4];
         draw4(p, id[i], 0, U);
+        U[0] = draw_test(p, id[i]);
         if (p->species == 0) {
             double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
             double speed = sqrt(v2);

@@ -369,6 +369,28 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
     return U4{c0, c1, c2, c3};
 }
 
+// Philox2x32-10 (same paper): a 2-word counter, one 32 x 32 -> 64-bit product per round and
+// the Weyl key schedule k + r W.  Round keys precomputed on the host as for the 4x32 form.
+struct PhiloxKeys2 { uint32_t k[10]; };
+inline PhiloxKeys2 philox2_keys(uint32_t key) {
+    PhiloxKeys2 K{};
+    for (int r = 0; r < 10; ++r) {
+        K.k[r] = key;
+        key += 0x9E3779B9u;
+    }
+    return K;
+}
+__device__ __forceinline__ uint32_t philox2x32_10_x(uint32_t c0, uint32_t c1, const PhiloxKeys2 &K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p = (uint64_t)0xD256D193u * c0;
+        const uint32_t n0 = (uint32_t)(p >> 32) ^ c1 ^ K.k[r];
+        c1 = (uint32_t)p;
+        c0 = n0;
+    }
+    return c0;  // the first output word
+}
+
 // Leaf geometry on its level's lattice.
 struct LeafGeom { int32_t ix, iy, s; };
 

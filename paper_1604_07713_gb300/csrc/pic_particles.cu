@@ -246,7 +246,8 @@ template <typename R> struct PushArgs {
     // the bound test of the pass: electrons sigma_el / sc, sigma_iz0 / sc, (n dt sc p_pad)^2 with
     // sc the larger nonzero cross section scale; ions 1 / (n dt sigma_el g_pad p_pad)
     R bnd_el, bnd_iz, bnd_q, bnd_inv;
-    PhiloxKeys keys;  // round keys of the seed
+    PhiloxKeys keys;    // round keys of the seed
+    PhiloxKeys2 keys2;  // the collision test's uniform: Philox2x32-10 keyed by seed and instance
     uint32_t inst_word, step;
     const int64_t *step_dev;  // non-null: the step number is read from here (captured steps)
 };
@@ -279,7 +280,7 @@ constexpr int kQueue = 64;
 template <typename R> struct Queue {
     R a[kQueue], b[kQueue];  // new offsets in the old leaf (a leaver's lie outside [0, 1))
     R vx[kQueue], vy[kQueue], vz[kQueue], w[kQueue];
-    uint32_t r[4][kQueue];  // collision candidates: the four purpose-0 Philox words
+    uint32_t r0[kQueue];    // collision candidates: the test's uniform word
     uint32_t id[kQueue], key[kQueue], cand[kQueue];
     int32_t L[kQueue], dst[kQueue];  // dst: a stayer's slot, -1 for a leaver
 };
@@ -323,7 +324,8 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
     bool spawns = false;
     if (cand) {
         const R v2 = vx * vx + vy * vy + vz * vz;
-        const R U0 = u24<R>(q.r[0][e]);
+        const R U0 = u24<R>(q.r0[e]);
+        const U4 r0 = philox4x32_10(id, a.inst_word, step, 0u, a.keys);  // the other uniforms
         if (a.species == 0) {
             // the exact test, from the same quantities as the bound of the pass
             const R eps = a.half_m_over_qe * v2;
@@ -331,9 +333,9 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
             const R st = a.sig_el + siz;
             const R xc = a.ng_dt * st * m_sqrt(v2);
             if (U0 < -m_expm1(-xc)) {
-                spawns = u24<R>(q.r[1][e]) * st < siz;
+                spawns = u24<R>(r0.y) * st < siz;
                 const R speed = m_sqrt(v2);
-                const R U2 = u24<R>(q.r[2][e]);
+                const R U2 = u24<R>(r0.z);
                 if (spawns) {
                     const R rest = eps - a.eps_th;
                     const R e1 = U2 * rest, e2 = ((R)1 - U2) * rest;
@@ -349,7 +351,7 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
                     si[0] = a.vt_gas * nn[0]; si[1] = a.vt_gas * nn[1]; si[2] = a.vt_gas * nn[2];
                 } else {
                     R d[3];
-                    iso_dir<R>(U2, u24<R>(q.r[3][e]), d);
+                    iso_dir<R>(U2, u24<R>(r0.w), d);
                     const R cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
                     const R eps2 = eps * ((R)1 - a.two_m_over_mn * ((R)1 - cchi));
                     const R s2 = m_sqrt(a.two_qe_over_m * eps2);
@@ -367,7 +369,7 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
             const R P = -m_expm1(-a.ng_dt * a.sig_el * gm);
             if (U0 < P) {
                 R d[3];
-                iso_dir<R>(u24<R>(q.r[2][e]), u24<R>(q.r[3][e]), d);
+                iso_dir<R>(u24<R>(r0.z), u24<R>(r0.w), d);
                 const R cx = a.red_m * vx + a.red_mn * vnx, cy = a.red_m * vy + a.red_mn * vny,
                         cz = a.red_m * vz + a.red_mn * vnz;
                 vx = cx + a.red_a * gm * d[0];
@@ -423,7 +425,8 @@ __device__ __forceinline__ void run_deferred(const PushArgs<R> &a, const Queue<R
 // so the leaf's own records are compacted in place; everything the warp reads of the next
 // chunk lies beyond every slot it writes in this one.  Entering and spawned records only go
 // to free slots past end[], which no warp reads during the pass.
-// NT threads per block (a tuned launch shape); 768 threads per SM either way: 80 registers.
+// NT threads per block (a tuned launch shape); 768 threads per SM either way: 80 registers
+// (a 64-register build for 1024 threads spills and runs slower).
 // CIC: the field is gathered from the leaf's per-quarter cloud-in-cell coefficients (32 per
 // leaf, lane k holding coefficient k) instead of the bilinear corner field.
 // The warp walks the leaves first, first + nw, ... below last (all lanes call it).
@@ -494,7 +497,7 @@ __device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, c
             uint32_t id = nid;
             if (p + 32 < p1) fetch(p + 32);
             else if (c0 + 32 >= p1 && np0 + lane < np1) fetch(np0 + lane);
-            U4 r0{0u, 0u, 0u, 0u};
+            uint32_t r0x = 0u;
             R ex = 0, ey = 0;
             if constexpr (CIC) {
                 // the quarter (qx, qy) of the leaf and the fractions (fx, fy) from its reference
@@ -550,8 +553,10 @@ __device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, c
                 }
                 if (a.mcc) {
                     const R v2 = vx * vx + vy * vy + vz * vz;
-                    r0 = philox4x32_10(id, a.inst_word, step, 0u, a.keys);
-                    const R U0 = u24<R>(r0.x);
+                    // the test's uniform: Philox2x32-10 on the counter (id, step); the deferred
+                    // work draws the collision's other uniforms from the 4x32 purpose-0 stream
+                    r0x = philox2x32_10_x(id, step, a.keys2);
+                    const R U0 = u24<R>(r0x);
                     // 1 - exp(-x) <= x: a uniform at or above the bound x (with a rounding
                     // margin) means no collision; below it the deferred work makes the exact test
                     if (a.species == 0) {
@@ -561,7 +566,7 @@ __device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, c
                         const R eps = a.half_m_over_qe * v2;
                         const R T = a.bnd_el * eps + a.bnd_iz * (eps > a.eps_th ? eps - a.eps_th : (R)0);
                         const R ue = U0 * eps;
-                        cand = ue * ue < a.bnd_q * v2 * (T * T) || r0.x < 256u;
+                        cand = ue * ue < a.bnd_q * v2 * (T * T) || r0x < 256u;
                     } else {
                         // the Box-Muller partner speed is at most 8.157 v_t (24-bit uniforms):
                         // U0 < B (|v| + g) iff U0 / B - g < 0 or (U0 / B - g)^2 < v^2
@@ -587,10 +592,7 @@ __device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, c
                     q.a[e] = u; q.b[e] = v;
                     q.vx[e] = vx; q.vy[e] = vy; q.vz[e] = vz; q.w[e] = w;
                     q.cand[e] = cand ? 1u : 0u;
-                    if (cand) {
-                        q.r[0][e] = r0.x; q.r[2][e] = r0.z; q.r[3][e] = r0.w;
-                        if (a.species == 0) q.r[1][e] = r0.y;
-                    }
+                    q.r0[e] = r0x;
                     q.id[e] = id; q.key[e] = key0 + (uint32_t)p;
                     q.L[e] = L; q.dst[e] = dst;
                 }
@@ -1224,6 +1226,7 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
     }
     a.keys = philox_keys(c.seed);
     a.inst_word = (uint32_t)c.instance << 24;
+    a.keys2 = philox2_keys((uint32_t)(c.seed & 0xFFFFFFFFu) ^ (uint32_t)(c.seed >> 32) ^ a.inst_word);
     a.step = (uint32_t)step;
     a.step_dev = nullptr;
     return a;

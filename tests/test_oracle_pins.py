@@ -24,6 +24,32 @@ def test_philox_known_answers():
         assert list(map(int, out)) == v[6:10]
 
 
+def test_philox2x32_known_answers():
+    # the collision test's uniform comes from the 2x32 form
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox2x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        assert O.philox2(v[0], v[1], v[2]) == (v[3], v[4])
+
+
+def test_philox2x32_round_structure_is_invertible():
+    # one odd multiplier: each round is undone with its inverse mod 2^32
+    M, W_ = 0xD256D193, 0x9E3779B9
+    inv = pow(M, -1, 1 << 32)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        c0, c1, k = (int(t) for t in rng.integers(0, 1 << 32, 3, dtype=np.uint64))
+        x0, x1 = O.philox2(c0, c1, k)
+        for r in range(9, -1, -1):
+            kr = (k + r * W_) & 0xFFFFFFFF
+            p0 = (x1 * inv) & 0xFFFFFFFF       # the round's input word 0
+            hi = (M * p0) >> 32
+            x0, x1 = p0, x0 ^ hi ^ kr           # and word 1
+        assert (x0, x1) == (c0, c1)
+
+
 def test_philox_round_structure_is_invertible():
     # The Philox S-box is a bijection: multipliers are odd, so each round can be undone with
     # their inverses mod 2^32.  Inverting ten rounds must give back the counter.
