@@ -26,6 +26,30 @@ constexpr double kCoarseTol2 = 1e-10;  // coarsest solve (multi-block path): ||r
 constexpr float kSmCoarseTol2 = 1e-6f; // coarsest solve inside a V-cycle in shared memory: 1e-3
 inline unsigned blocks_for(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_chain first).
+template <typename... KArgs, typename... Args>
+void pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GB_CUDA(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
+}
+
+// Programmatic dependent launch: a kernel of the solve's chain lets the next one be scheduled
+// at once and waits, before touching memory, for the previous one to complete (the waits are
+// no-ops for a kernel launched without the programmatic-serialization attribute).
+__device__ __forceinline__ void pdl_chain() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -40,33 +64,10 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;  // valid in thread 0
 }
 
-// r = b - A phi (FP64), partial sums of r^2 and b^2 per block (fixed grid).
-__global__ void k_residual64(int64_t n, const int32_t *__restrict__ col, const double *__restrict__ val,
-                             const double *__restrict__ diag, const double *__restrict__ phi,
-                             const double *__restrict__ b, double *__restrict__ r, float *__restrict__ r32,
-                             double *__restrict__ part) {
-    double rr = 0.0, bb = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double ax = diag[i] * phi[i];
-#pragma unroll
-        for (int j = 0; j < kEll; ++j) {
-            const int32_t c = col[(int64_t)j * n + i];
-            if (c >= 0) ax += val[(int64_t)j * n + i] * phi[c];
-        }
-        const double ri = b[i] - ax;
-        r[i] = ri;
-        r32[i] = (float)ri;
-        rr += ri * ri;
-        bb += b[i] * b[i];
-    }
-    const double s1 = block_sum(rr);
-    const double s2 = block_sum(bb);
-    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
-}
-
 // out = sums of the block partials (one warp: lanes in a fixed order, then a fixed tree,
 // so the result does not depend on timing).
 __global__ void k_finish_sums(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+    pdl_chain();
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) return;
     double a = 0.0, b = 0.0;
@@ -84,19 +85,61 @@ __device__ __forceinline__ double worst_residual(double a, double b) {
     return (a != a || b != b) ? __longlong_as_double(0x7FF8000000000000ll) : fmax(a, b);
 }
 
-// After a residual norm: the solve's statistics and whether another cycle runs (the
-// condition of the graph's WHILE node).  first = 1 before the first cycle.
-__global__ void k_mg_decide(cudaGraphConditionalHandle h, const double *__restrict__ sums, double tol, int maxc,
-                            double *__restrict__ stats, int first) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double rr = sums[0], bb = sums[1];
-    const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-    const double cyc = first ? 0.0 : stats[0] + 1.0;
-    const bool done = rel <= tol || (bb == 0.0 && rr == 0.0) || cyc >= (double)maxc;
-    stats[0] = cyc;
-    stats[1] = rel;
-    if (done) stats[2] = worst_residual(stats[2], rel);
-    cudaGraphSetConditional(h, done ? 0u : 1u);
+// r = b - A phi (FP64) with r^2 and b^2 summed per block (fixed grid), then, in the block that
+// arrives last on the ticket counter (after a fence, so every block's sums are visible), the
+// block sums added as k_finish_sums adds them, the solve's statistics and whether another
+// cycle runs (the condition of the graph's WHILE node; first = 1 before the first cycle),
+// and the counter reset for the next launch.
+__global__ void k_residual_decide(int64_t n, const int32_t *__restrict__ col, const double *__restrict__ val,
+                                  const double *__restrict__ diag, const double *__restrict__ phi,
+                                  const double *__restrict__ b, double *__restrict__ r, float *__restrict__ r32,
+                                  double *__restrict__ part, uint32_t *__restrict__ ticket,
+                                  cudaGraphConditionalHandle h, double tol, int maxc, double *__restrict__ stats,
+                                  int first) {
+    pdl_chain();
+    __shared__ bool last;
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double ax = diag[i] * phi[i];
+#pragma unroll
+        for (int j = 0; j < kEll; ++j) {
+            const int32_t c = col[(int64_t)j * n + i];
+            if (c >= 0) ax += val[(int64_t)j * n + i] * phi[c];
+        }
+        const double ri = b[i] - ax;
+        r[i] = ri;
+        r32[i] = (float)ri;
+        rr += ri * ri;
+        bb += b[i] * b[i];
+    }
+    const double s1 = block_sum(rr);
+    const double s2 = block_sum(bb);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1;
+        part[2 * blockIdx.x + 1] = s2;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    const int lane = threadIdx.x;
+    double a = 0.0, c = 0.0;
+    for (int k = lane; k < (int)gridDim.x; k += 32) { a += __ldcg(part + 2 * k); c += __ldcg(part + 2 * k + 1); }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    }
+    if (lane == 0) {
+        *ticket = 0u;
+        const double rel = c > 0.0 ? sqrt(a / c) : sqrt(a);
+        const double cyc = first ? 0.0 : stats[0] + 1.0;
+        const bool done = rel <= tol || (c == 0.0 && a == 0.0) || cyc >= (double)maxc;
+        stats[0] = cyc;
+        stats[1] = rel;
+        if (done) stats[2] = worst_residual(stats[2], rel);
+        cudaGraphSetConditional(h, done ? 0u : 1u);
+    }
 }
 
 // Zero-mean projections for a fully periodic (singular) problem: area weights a = s^2.
@@ -113,6 +156,7 @@ __global__ void k_area_moments(int64_t n, const uint8_t *__restrict__ lev, int l
 }
 __global__ void k_area_weighted(int64_t n, const uint8_t *__restrict__ lev, int lmax, const double *__restrict__ v,
                                 double *__restrict__ part) {
+    pdl_chain();
     double sv = 0.0, sa = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double s = (double)(1 << (lmax - lev[i]));
@@ -126,6 +170,7 @@ __global__ void k_area_weighted(int64_t n, const uint8_t *__restrict__ lev, int 
 // compatibility), mode 1 a constant (zero area-weighted mean of the potential).
 __global__ void k_project(int64_t n, const uint8_t *__restrict__ lev, int lmax, const double *__restrict__ sums,
                           double *__restrict__ v, int mode) {
+    pdl_chain();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double s = (double)(1 << (lmax - lev[i]));
@@ -144,6 +189,7 @@ __global__ void k_extrapolate(int64_t n, double *__restrict__ phi, double *__res
 }
 
 __global__ void k_add_correction(int64_t n, const float *__restrict__ e, double *__restrict__ phi) {
+    pdl_chain();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) phi[i] += (double)e[i];
 }
@@ -155,6 +201,7 @@ __global__ void k_rbgs_half(int64_t n, const int32_t *__restrict__ col, const fl
                             const float *__restrict__ dinv, const uint8_t *__restrict__ color, int c,
                             const float *__restrict__ b, const float *__restrict__ xin, float *__restrict__ xout,
                             int zero_in) {
+    pdl_chain();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (color[i] != c) {
@@ -178,6 +225,7 @@ __global__ void k_rbgs_half(int64_t n, const int32_t *__restrict__ col, const fl
 __global__ void k_rbgs_first(int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val,
                              const float *__restrict__ dinv, const uint8_t *__restrict__ color,
                              const float *__restrict__ b, float *__restrict__ xout) {
+    pdl_chain();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (color[i] != 1) {
@@ -201,6 +249,7 @@ __global__ void k_rbgs_half_prolong(int64_t n, const int32_t *__restrict__ col, 
                                     const float *__restrict__ b, const float *__restrict__ xin,
                                     const int32_t *__restrict__ parent, const float *__restrict__ xc,
                                     float *__restrict__ xout) {
+    pdl_chain();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (color[i] != c) {
@@ -221,6 +270,7 @@ __global__ void k_restrict_residual(int64_t nc, const int32_t *__restrict__ chil
                                     const int32_t *__restrict__ col, const float *__restrict__ val,
                                     const float *__restrict__ dinv, const float *__restrict__ bf,
                                     const float *__restrict__ xf, float *__restrict__ bc, float *__restrict__ xc) {
+    pdl_chain();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nc) return;
     float s = 0.0f;
@@ -247,6 +297,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(int64_t n, const int32_t *__
                                                     const float *__restrict__ b, float *__restrict__ x,
                                                     float *__restrict__ r, float *__restrict__ p,
                                                     float *__restrict__ q, int singular, int maxit) {
+    pdl_chain();
     __shared__ double red[32];
     __shared__ double bcast;
     auto bsum = [&](double v) -> double {
@@ -657,6 +708,7 @@ __device__ void sm_vcycle(const SmallDesc &D, float *sm, bool singular, float *r
 // Tail of a V-cycle started by the multi-block levels: b from global, x back to global.
 __global__ void __launch_bounds__(1024, 1) k_tail_vcycle(SmallDesc D, const float *__restrict__ gb,
                                                        float *__restrict__ gx, int singular) {
+    pdl_chain();
     extern __shared__ float sm[];
     __shared__ float redf[33];
     const SmallLevel &L = D.lv[0];
@@ -920,14 +972,14 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     if ((int)g >= g0) {
         const SmallDesc D = small_desc(in, (int)g);
         const size_t bytes = (size_t)D.smem_floats * 4;
-        k_tail_vcycle<<<1, 1024, bytes, s>>>(D, L.b, L.x, singular);
+        pdl(k_tail_vcycle, 1, 1024, bytes, s, D, L.b, L.x, singular);
         count_launch(ctx);
         return;
     }
     if (g + 1 == in.lv.size()) {
         const int maxit = (int)std::min<int64_t>(2 * L.n + 10, 500);
         // r, p, q: three slices of the coarsest level's work buffer (allocated 3n)
-        k_coarse_cg<<<1, 1024, 0, s>>>(L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, L.t + L.n, L.t + 2 * L.n,
+        pdl(k_coarse_cg, 1, 1024, 0, s, L.n, L.col, L.val, L.dinv, L.b, L.x, L.t, L.t + L.n, L.t + 2 * L.n,
                                        singular, maxit);
         count_launch(ctx);
         return;
@@ -935,23 +987,23 @@ void vcycle(pic_ctx *ctx, Instance &in, size_t g, bool singular) {
     Level &C = in.lv[g + 1];
     const unsigned nb = blocks_for(L.n);
     // pre-smoothing (x starts at zero): the first sweep's two half sweeps in one kernel
-    k_rbgs_first<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, L.b, L.x);
+    pdl(k_rbgs_first, nb, kT, 0, s, L.n, L.col, L.val, L.dinv, L.color, L.b, L.x);
     for (int k = 1; k < kNu; ++k)
         for (int c = 0; c < 2; ++c) {
-            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
+            pdl(k_rbgs_half, nb, kT, 0, s, L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
             std::swap(L.x, L.t);
         }
-    k_restrict_residual<<<blocks_for(C.n), kT, 0, s>>>(C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
+    pdl(k_restrict_residual, blocks_for(C.n), kT, 0, s, C.n, C.child4, L.n, L.col, L.val, L.dinv, L.b, L.x, C.b, C.x);
     count_launch(ctx, 2 * kNu);
     vcycle(ctx, in, g + 1, singular);
     // post-smoothing, the injection of the correction fused into its first half sweep
-    k_rbgs_half_prolong<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, 0, L.b, L.x, L.parent, C.x, L.t);
+    pdl(k_rbgs_half_prolong, nb, kT, 0, s, L.n, L.col, L.val, L.dinv, L.color, 0, L.b, L.x, L.parent, C.x, L.t);
     std::swap(L.x, L.t);
-    k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, 1, L.b, L.x, L.t, 0);
+    pdl(k_rbgs_half, nb, kT, 0, s, L.n, L.col, L.val, L.dinv, L.color, 1, L.b, L.x, L.t, 0);
     std::swap(L.x, L.t);
     for (int k = 1; k < kNu; ++k)
         for (int c = 0; c < 2; ++c) {
-            k_rbgs_half<<<nb, kT, 0, s>>>(L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
+            pdl(k_rbgs_half, nb, kT, 0, s, L.n, L.col, L.val, L.dinv, L.color, c, L.b, L.x, L.t, 0);
             std::swap(L.x, L.t);
         }
     count_launch(ctx, 2 * kNu);
@@ -1052,7 +1104,8 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     in.bvec = dalloc<double>(A, n);
     in.res = dalloc<double>(A, n);
     in.charge = dalloc<double>(A, n);
-    in.red = dalloc<double>(A, 2 * kRedBlocks + 8);
+    in.red = dalloc<double>(A, 2 * kRedBlocks + 8);  // block sums, totals, the residual's ticket
+    GB_CUDA(cudaMemsetAsync(in.red, 0, (2 * kRedBlocks + 8) * sizeof(double), ctx->stream));
     in.mg_stats = dalloc<double>(A, 4);
     GB_CUDA(cudaMemsetAsync(in.mg_stats, 0, 4 * 8, ctx->stream));
     GB_CUDA(cudaMemsetAsync(in.phi, 0, n * 8, ctx->stream));
@@ -1157,19 +1210,19 @@ void poisson_solve(pic_ctx *ctx, Instance &in, const double walls[4]) {
     const int maxc = std::max(1, in.cfg.mg_max_cycles);
     // launches go to ctx->stream, which is the capture stream while the solve is captured
     auto issue_residual = [&](int first, cudaGraphConditionalHandle h) {
-        k_residual64<<<kRedBlocks, kT, 0, ctx->stream>>>(n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b, in.red);
-        k_finish_sums<<<1, 32, 0, ctx->stream>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
-        k_mg_decide<<<1, 32, 0, ctx->stream>>>(h, in.red + 2 * kRedBlocks, in.cfg.mg_rel_tol, maxc, in.mg_stats, first);
-        count_launch(ctx, 3);
+        pdl(k_residual_decide, kRedBlocks, kT, 0, ctx->stream, n, L.col, L.val64, L.diag64, in.phi, in.bvec, in.res, L.b,
+                                                              in.red, (uint32_t *)(in.red + 2 * kRedBlocks + 4), h,
+                                                              in.cfg.mg_rel_tol, maxc, in.mg_stats, first);
+        count_launch(ctx);
     };
     auto issue_cycle = [&](cudaGraphConditionalHandle h) {
         vcycle(ctx, in, 0, singular);
-        k_add_correction<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.x, in.phi);
+        pdl(k_add_correction, blocks_for(n), kT, 0, ctx->stream, n, L.x, in.phi);
         count_launch(ctx);
         if (singular) {
-            k_area_weighted<<<kRedBlocks, kT, 0, ctx->stream>>>(n, L.lev, L.lmax, in.phi, in.red);
-            k_finish_sums<<<1, 32, 0, ctx->stream>>>(kRedBlocks, in.red, in.red + 2 * kRedBlocks);
-            k_project<<<blocks_for(n), kT, 0, ctx->stream>>>(n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
+            pdl(k_area_weighted, kRedBlocks, kT, 0, ctx->stream, n, L.lev, L.lmax, in.phi, in.red);
+            pdl(k_finish_sums, 1, 32, 0, ctx->stream, kRedBlocks, in.red, in.red + 2 * kRedBlocks);
+            pdl(k_project, blocks_for(n), kT, 0, ctx->stream, n, L.lev, L.lmax, in.red + 2 * kRedBlocks, in.phi, 1);
             count_launch(ctx, 3);
         }
         issue_residual(0, h);
