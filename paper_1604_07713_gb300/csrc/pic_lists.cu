@@ -501,14 +501,16 @@ template <typename R> void relayout_batch(pic_ctx *ctx) {
     const ListEntry *tab = (const ListEntry *)t.tab;
     const unsigned n = (unsigned)t.n;
     cudaStream_t st = ctx->stream;
-    k_seg_sizes_batch<<<dim3(4, n), kT, 0, st>>>(tab, 1, 5);
+    // x blocks per entry: a re-laid-out species keeps 64 blocks busy (the other entries'
+    // blocks return at once), so a few entries at a time still fill the GPU
+    k_seg_sizes_batch<<<dim3(16, n), kT, 0, st>>>(tab, 1, 5);
     exclusive_scan_i32_batch(ctx, ctx->batch.relay5);
     k_relayout_fit_batch<<<(n + kT - 1) / kT, kT, 0, st>>>(tab, (int)n);
-    k_seg_sizes_batch<<<dim3(4, n), kT, 0, st>>>(tab, 0, 7);
+    k_seg_sizes_batch<<<dim3(16, n), kT, 0, st>>>(tab, 0, 7);
     exclusive_scan_i32_batch(ctx, ctx->batch.relay7);
-    k_relayout_move_batch<R><<<dim3(8, n), kT, 0, st>>>(tab);
-    k_relayout_ovf_batch<R><<<dim3(4, n), kT, 0, st>>>(tab);
-    k_relayout_back_batch<R><<<dim3(16, n), kT, 0, st>>>(tab);
+    k_relayout_move_batch<R><<<dim3(64, n), kT, 0, st>>>(tab);
+    k_relayout_ovf_batch<R><<<dim3(16, n), kT, 0, st>>>(tab);
+    k_relayout_back_batch<R><<<dim3(64, n), kT, 0, st>>>(tab);
     count_launch(ctx, 6);
 }
 
@@ -519,8 +521,8 @@ template <typename R> void repairs_batch_impl(pic_ctx *ctx) {
     k_any_flag<<<1, kT, 0, ctx->stream>>>(tab, t.n, 0, flag);
     count_launch(ctx);
     capture_if(ctx, ctx->stream, flag, [&]() {
-        k_move_to_tail_batch<R><<<dim3(2, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
-        k_place_ovf_batch<R><<<dim3(4, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
+        k_move_to_tail_batch<R><<<dim3(8, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
+        k_place_ovf_batch<R><<<dim3(8, (unsigned)t.n), kT, 0, ctx->stream>>>(tab);
         // a tail used up: those species' lists are laid out again
         k_any_flag<<<1, kT, 0, ctx->stream>>>(tab, t.n, 5, flag + 1);
         capture_if(ctx, ctx->stream, flag + 1, [&]() { relayout_batch<R>(ctx); });
