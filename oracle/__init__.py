@@ -78,7 +78,7 @@ class _PushParams(C.Structure):
                 ("sigma_iz0", C.c_double), ("eps_th_ev", C.c_double), ("qe", C.c_double),
                 ("m_neutral", C.c_double), ("t_gas_ev", C.c_double), ("key0", _u32),
                 ("key1", _u32), ("inst", _u32), ("step", _u32), ("lx", C.c_double),
-                ("ly", C.c_double)]
+                ("ly", C.c_double), ("mode", _i32)]
 
 
 def _declare(L):
@@ -106,6 +106,8 @@ def _declare(L):
     L.or_cic_deposit.argtypes = [_i32, _i32, C.c_double, _i32, _i32, _i64, _p, _p, _p, C.c_double, _p]
     L.or_cic_gather.argtypes = [_i32, _i32, C.c_double, _i32, _i32, _p, _p, _i32, _i64, _p, _p, _p, _p]
     L.or_push_mcc.restype = _i64
+    L.or_assemble_kappa.argtypes = [C.POINTER(_Mesh), _p, _p, _p, _p, _p]
+    L.or_assemble_kappa.restype = _i64
 
 
 def _ptr(a):
@@ -232,13 +234,30 @@ class Mesh:
             self._op = (A, bc.reshape(n, 4))
         return self._op
 
-    def solve_poisson(self, rhs_charge_over_eps0, walls):
+    def operator_kappa(self, kappa):
+        """The operator with a relative permittivity ``kappa`` per leaf (the direct implicit
+        scheme's 1 + chi, §3): each face's conductance times the face's kappa (or_assemble_kappa)."""
+        import scipy.sparse as sp
+        n = self.nleaf
+        cap = 9 * n
+        kap = np.ascontiguousarray(kappa, np.float64)
+        row = np.empty(cap, np.int64); col = np.empty(cap, np.int64)
+        val = np.empty(cap, np.float64); bc = np.empty(4 * n, np.float64)
+        k = lib().or_assemble_kappa(C.byref(self._c), _ptr(kap), _ptr(row), _ptr(col), _ptr(val), _ptr(bc))
+        if k < 0:
+            raise ValueError("unbalanced tree")
+        A = sp.csr_matrix((val[:k], (row[:k], col[:k])), shape=(n, n))
+        A.sum_duplicates()
+        return A, bc.reshape(n, 4)
+
+    def solve_poisson(self, rhs_charge_over_eps0, walls, kappa=None):
         """Solve A phi = b on the leaves (sparse direct, FP64).  ``rhs_charge_over_eps0`` is
         rho*h^2/eps0 per leaf, ``walls`` = (phi_x_lo, phi_x_hi, phi_y_lo, phi_y_hi).
-        A fully periodic mesh is solved for the zero-mean potential (bordered system)."""
+        A fully periodic mesh is solved for the zero-mean potential (bordered system).  With
+        ``kappa`` the operator is the relative-permittivity one (operator_kappa)."""
         import scipy.sparse as sp
         import scipy.sparse.linalg as spla
-        A, bc = self.operator()
+        A, bc = self.operator() if kappa is None else self.operator_kappa(kappa)
         b = np.asarray(rhs_charge_over_eps0, np.float64) + bc @ np.asarray(walls, np.float64)
         if self.bc_x == BC_PERIODIC and self.bc_y == BC_PERIODIC:
             n = self.nleaf
@@ -380,12 +399,35 @@ class Sim:
     def rho(self):
         return self.charge() / self.mesh.area() + self.cfg.get("rho_background", 0.0)
 
+    # -- §3 direct implicit PIC (DIPIC) ---------------------------------------------------
+    def implicit(self):
+        """True when the config selects the direct implicit scheme (NGP only)."""
+        on = bool(self.cfg.get("implicit", 0))
+        if on and self.shape():
+            raise ValueError("the implicit scheme uses the NGP shape")
+        return on
+
+    def kappa(self):
+        """The implicit susceptibility as a relative permittivity per leaf: 1 + chi with
+        chi = dt^2 sum_s q_s^2 n_s / (m_s eps0) = (omega_ps dt)^2 summed over species, n_s the
+        species' weight per area in the leaf (at the predicted positions during a step)."""
+        c = self.cfg
+        M = self.mesh
+        chi = np.zeros(M.nleaf)
+        for sp in self.species:
+            if sp is None or sp.n == 0:
+                continue
+            W = np.bincount(sp.leaf, weights=sp.w, minlength=M.nleaf)
+            chi += (c["dt"] ** 2 * sp.q ** 2 / (sp.m * c["eps0"])) * W
+        return 1.0 + chi / M.area()
+
     def fields(self):
-        """Deposit -> Poisson -> node E for the current state (no particle update)."""
+        """Deposit -> Poisson -> node E for the current state (no particle update).  With the
+        implicit scheme the Poisson operator carries the susceptibility of the current state."""
         rho = self.rho()
         b = rho * self.mesh.area() / self.cfg["eps0"]
         walls = self.walls()
-        phi = self.mesh.solve_poisson(b, walls)
+        phi = self.mesh.solve_poisson(b, walls, self.kappa() if self.implicit() else None)
         E = self.mesh.node_e(phi, walls)
         self.phi, self.last_rho, self.last_node_e, self.last_walls = phi, rho, E, walls
         return rho, phi, E
@@ -460,24 +502,40 @@ class Sim:
         f = d["hist"] / (tot * deps) if tot > 0 else np.zeros(d["n_bins"])
         return f, d["samples"]
 
-    def push_params(self, s):
+    def push_params(self, s, mode=0):
         c = self.cfg
         k0, k1 = philox_key(c.get("seed", 0))
-        return _PushParams(c["dt"], c["q"][s], c["m"][s], s, int(c.get("mcc", 0)),
+        return _PushParams(c["dt"], c["q"][s], c["m"][s], s, int(c.get("mcc", 0)) if mode != 1 else 0,
                            c.get("gas_density", 0.0), c.get("sigma_el", 0.0),
                            c.get("sigma_iz0", 0.0), c.get("eps_th_ev", 0.0), c.get("qe", QE),
                            c.get("neutral_mass", 1.0), c.get("gas_temperature_ev", 0.0), k0, k1,
                            int(c.get("instance", 0)), self.step_count & 0xFFFFFFFF,
-                           self.mesh.lx, self.mesh.ly)
+                           self.mesh.lx, self.mesh.ly, mode)
 
     def step(self, n_steps=1):
         for _ in range(n_steps):
             self._step_once()
 
     def _step_once(self):
-        _, _, E = self.fields()
-        if self.diag is not None:
-            self._diag_sample()
+        if self.implicit():
+            # §3 DIPIC: predictor x~ = x + dt v (no kick, no collisions), then the field of the
+            # predicted charge with the susceptibility, then the corrector v += dt a(x~),
+            # x = x~ + dt^2 a(x~), and the collisions
+            self._particle_pass(np.zeros((self.mesh.nleaf, 4, 2)), 1)
+            _, _, E = self.fields()
+            if self.diag is not None:
+                self._diag_sample()
+            self._particle_pass(E, 2)
+        else:
+            _, _, E = self.fields()
+            if self.diag is not None:
+                self._diag_sample()
+            self._particle_pass(E, 0)
+        self.step_count += 1
+
+    def _particle_pass(self, E, mode):
+        """One push pass of every species (mode: 0 leapfrog, 1 implicit predictor, 2 implicit
+        corrector; or_push_mcc), then the §3.1 list update with the spawned pairs."""
         Eflat = np.ascontiguousarray(E.reshape(-1))
         results = []
         for s, sp in enumerate(self.species):
@@ -488,7 +546,7 @@ class Sim:
             new_leaf = np.empty(n, np.int64)
             spawn = np.zeros(n, np.uint8)
             sv = np.zeros(3 * n); svi = np.zeros(3 * n)
-            p = self.push_params(s)
+            p = self.push_params(s, mode)
             dec = np.empty(4 * n)
             e_part = None
             if self.shape():
@@ -499,7 +557,8 @@ class Sim:
                               _ptr(sp.leaf), _ptr(new_leaf), _ptr(spawn), _ptr(sv), _ptr(svi),
                               _ptr(dec), _ptr(e_part))
             # the collision decisions of this step by particle id: (U0, P, U1 sigma_T, sigma_iz)
-            self.last_decisions[s] = (sp.id.copy(), dec.reshape(n, 4))
+            if mode != 1:
+                self.last_decisions[s] = (sp.id.copy(), dec.reshape(n, 4))
             results.append((new_leaf, spawn, sv.reshape(n, 3), svi.reshape(n, 3)))
         # spawned pairs (electrons only): ids next_id + 2*rank (electron), +1 (ion), rank =
         # position among the ionizing electrons in list order
@@ -522,7 +581,6 @@ class Sim:
                 continue
             new_leaf = results[s][0]
             self.species[s] = self._rebin(sp, new_leaf, spawn_blocks.get(s))
-        self.step_count += 1
 
     @staticmethod
     def _rebin(sp: Species, new_leaf, spawned):

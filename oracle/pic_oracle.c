@@ -321,6 +321,53 @@ int64_t or_assemble(const or_mesh *m, int64_t *row, int64_t *col, double *val, d
     return k;
 }
 
+/* The same operator with a relative permittivity kappa per leaf (the direct implicit       */
+/* scheme's 1 + chi, §3): every face's conductance is multiplied by the face's kappa, the    */
+/* mean of the kappa on its two sides:                                                     */
+/*   same level: (k_C + k_N)/2;  Dirichlet wall: k_C;                                       */
+/*   coarse C and fine pair (F1, F2): (k_C + (k_F1 + k_F2)/2)/2, the same value in the      */
+/*   coarse cell's row and in both fine cells' rows, so the operator stays conservative.    */
+int64_t or_assemble_kappa(const or_mesh *m, const double *kappa, int64_t *row, int64_t *col, double *val,
+                          double *bc_coef)
+{
+    int64_t k = 0;
+    for (int64_t c = 0; c < m->nleaf; ++c) {
+        double diag = 0.0;
+        for (int w = 0; w < 4; ++w) bc_coef[4 * c + w] = 0.0;
+        for (int d = 0; d < 4; ++d) {
+            or_face f = face_of(m, c, d);
+            int bc = (d < 2) ? m->bc_x : m->bc_y;
+            double kf;
+            switch (f.type) {
+            case F_BOUNDARY:
+                if (bc == BC_DIRICHLET) { diag += 2.0 * kappa[c]; bc_coef[4 * c + d] = 2.0 * kappa[c]; }
+                break;
+            case F_SAME:
+                kf = 0.5 * (kappa[c] + kappa[f.n1]);
+                diag += kf;
+                row[k] = c; col[k] = f.n1; val[k] = -kf; ++k;
+                break;
+            case F_FINER:
+                kf = 0.5 * (kappa[c] + 0.5 * (kappa[f.n1] + kappa[f.n2]));
+                diag += 4.0 / 3.0 * kf;
+                row[k] = c; col[k] = f.n1; val[k] = -2.0 / 3.0 * kf; ++k;
+                row[k] = c; col[k] = f.n2; val[k] = -2.0 / 3.0 * kf; ++k;
+                break;
+            case F_COARSER:
+                kf = 0.5 * (kappa[f.n1] + 0.5 * (kappa[c] + kappa[f.sib]));
+                diag += 1.0 / 3.0 * kf;
+                row[k] = c; col[k] = f.sib; val[k] = 1.0 / 3.0 * kf; ++k;
+                row[k] = c; col[k] = f.n1; val[k] = -2.0 / 3.0 * kf; ++k;
+                break;
+            default:
+                return -1;
+            }
+        }
+        row[k] = c; col[k] = c; val[k] = diag; ++k;
+    }
+    return k;
+}
+
 /* Gradient d(phi)/dx across the vertical lattice line x = I at lattice row J, using the
  * face rule of the operator above.  phi_lo / phi_hi are the wall values (x = 0, x = Lx). */
 static double grad_x_at(const or_mesh *m, const double *phi, int32_t I, int32_t J,
@@ -472,6 +519,10 @@ typedef struct {
     double ng, sigma_el, sigma_iz0, eps_th_ev, qe, m_neutral, t_gas_ev;
     uint32_t key0, key1, inst, step;
     double lx, ly;
+    /* 0: leapfrog (kick, then drift by the new velocity); 1: the direct implicit scheme's
+     * predictor (drift by the old velocity, no kick; collisions off by the caller); 2: its
+     * corrector (kick, then drift by the kick's velocity increment times dt) */
+    int32_t mode;
 } or_push_params;
 
 /* The collision test's uniform: Philox2x32-10 on the counter (id, step), keyed by the seed's */
@@ -551,12 +602,23 @@ int64_t or_push_mcc(const or_mesh *m, const or_push_params *p, const double *nod
             ex = w00 * E[0] + w10 * E[2] + w01 * E[4] + w11 * E[6];
             ey = w00 * E[1] + w10 * E[3] + w01 * E[5] + w11 * E[7];
         }
-        /* leapfrog kick and drift */
+        /* leapfrog kick and drift (the implicit scheme's predictor and corrector: see mode) */
         double qm = p->q / p->m;
-        vx[i] += qm * ex * p->dt;
-        vy[i] += qm * ey * p->dt;
-        x[i] += vx[i] * p->dt;
-        y[i] += vy[i] * p->dt;
+        if (p->mode == 1) {
+            x[i] += vx[i] * p->dt;
+            y[i] += vy[i] * p->dt;
+        } else {
+            double dvx = qm * ex * p->dt, dvy = qm * ey * p->dt;
+            vx[i] += dvx;
+            vy[i] += dvy;
+            if (p->mode == 2) {
+                x[i] += dvx * p->dt;
+                y[i] += dvy * p->dt;
+            } else {
+                x[i] += vx[i] * p->dt;
+                y[i] += vy[i] * p->dt;
+            }
+        }
         /* walls: periodic wrap (modulo the period, however far the particle moved) or
          * absorption; a wrapped position that rounds onto the far wall is the near wall */
         int dead = 0;

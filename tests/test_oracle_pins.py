@@ -385,6 +385,77 @@ def test_cold_plasma_oscillates_at_plasma_frequency():
 
 
 # --------------------------------------------------------------------------------------
+# Direct implicit PIC (§3 DIPIC): the susceptibility operator and the implicit push
+# --------------------------------------------------------------------------------------
+def test_kappa_operator_special_cases_and_conservation():
+    r, l, m = W.random_tree(4, 4, 3, 0.3, 9, True, True)
+    M = O.Mesh(4, 4, 0.25, 3, O.BC_PERIODIC, O.BC_PERIODIC, r, l, m)
+    A, _ = M.operator()
+    # kappa = 1 is the explicit operator, a constant kappa scales it
+    A1, _ = M.operator_kappa(np.ones(M.nleaf))
+    assert abs(A1 - A).max() < 1e-15
+    A3, _ = M.operator_kappa(np.full(M.nleaf, 3.0))
+    assert abs(A3 - 3.0 * A).max() < 1e-14
+    # a varying kappa keeps the fluxes pairwise equal and opposite (columns sum to zero) and
+    # the operator as symmetric as the explicit one
+    kap = 1.0 + np.random.default_rng(4).random(M.nleaf) * 5.0
+    Ak, _ = M.operator_kappa(kap)
+    assert np.abs(np.asarray(Ak.sum(axis=0))).max() < 1e-13
+    assert abs(Ak - Ak.T).max() <= 10.0 * abs(A - A.T).max() + 1e-13
+    # Dirichlet walls: the wall coefficient is the wall cell's kappa times 2
+    M2 = O.Mesh(4, 2, 0.25, 0, O.BC_DIRICHLET, O.BC_PERIODIC)
+    kap2 = np.arange(1.0, M2.nleaf + 1.0)
+    _, bc = M2.operator_kappa(kap2)
+    _, bc1 = M2.operator()
+    assert np.array_equal(bc, bc1 * kap2[:, None])
+
+
+def test_kappa_operator_two_cell_hand_case():
+    # 2 x 1 cells, Dirichlet in x, Neumann in y: rows (2 k0 + (k0 + k1)/2, -(k0 + k1)/2),
+    # (-(k0 + k1)/2, (k0 + k1)/2 + 2 k1)
+    M = O.Mesh(2, 1, 0.5, 0, O.BC_DIRICHLET, O.BC_NEUMANN)
+    A, bc = M.operator_kappa(np.array([2.0, 6.0]))
+    assert np.allclose(A.toarray(), [[4.0 + 4.0, -4.0], [-4.0, 4.0 + 12.0]], rtol=0, atol=1e-15)
+    assert np.allclose(bc, [[4.0, 0, 0, 0], [0, 12.0, 0, 0]], rtol=0, atol=1e-15)
+
+
+def _implicit_mode_series(dt, nsteps, implicit=1):
+    cfg, mesh, parts = W.cold_plasma(n_side=64, ppc=16, dt=dt, quiet=True, amp=0.2)
+    cfg["implicit"] = implicit
+    M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, O.BC_PERIODIC, O.BC_PERIODIC)
+    sim = O.Sim(cfg, M)
+    sim.load(0, **parts[0])
+    xc, _ = M.centres()
+    mode = []
+    for _ in range(nsteps):
+        sim.step()
+        mode.append(np.sum(sim.last_node_e[:, 0, 0] * np.sin(2 * np.pi * xc)))
+    return np.array(mode)
+
+
+def test_implicit_cold_plasma_follows_the_schemes_discrete_dispersion():
+    # The implicit scheme v' = v + dt a(x'), x' = x + dt v' applied to a cold plasma mode of
+    # frequency w: x_{n+1} (1 + w^2 dt^2) - 2 x_n + x_{n-1} = 0, so the mode obeys
+    # m_{n+1} = a m_n + b m_{n-1} with a = 2 / (1 + W), b = -1 / (1 + W), W = (w dt)^2:
+    # damped by 1 / sqrt(1 + W) per step at the phase atan(w dt) -- stable at any dt.
+    # A factor 1/2 in the susceptibility, or the field without it, gives other (a, b).
+    for dt, n in ((0.5, 12),):
+        m = _implicit_mode_series(dt, n)
+        a, b = np.linalg.lstsq(np.stack([m[1:-1], m[:-2]], 1), m[2:], rcond=None)[0]
+        W_ = dt * dt  # omega_p = 1 in these units
+        assert abs(a - 2.0 / (1.0 + W_)) < 0.01 and abs(b + 1.0 / (1.0 + W_)) < 0.01, (a, b)
+
+
+def test_implicit_scheme_is_stable_beyond_the_explicit_limit():
+    # omega_p dt = 2.5 > 2: the leapfrog mode grows, the implicit one decays
+    # (until the leapfrog's sheets cross; the implicit mode decays to the NGP noise floor)
+    imp = _implicit_mode_series(2.5, 8)
+    exp_ = _implicit_mode_series(2.5, 8, implicit=0)
+    assert np.abs(imp[3:]).max() < 0.1 * abs(imp[0])
+    assert np.abs(exp_).max() > 4.0 * abs(exp_[0])
+
+
+# --------------------------------------------------------------------------------------
 # Ion collisions (§3 MCC of ions with neutrals): a Maxwellian neutral partner, isotropic
 # scattering in the centre-of-mass frame
 # --------------------------------------------------------------------------------------
