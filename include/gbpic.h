@@ -132,6 +132,10 @@ typedef struct pic_config {
     int32_t instance;           /* instance id mixed into the Philox counter               */
     int64_t particle_capacity;  /* per species; 0 = automatic (grows as needed)            */
     int32_t shape;              /* PIC_SHAPE_*: charge assignment and field gather (§3)    */
+    int32_t implicit;           /* 1: the direct implicit scheme (§3 DIPIC, NGP shape only):
+                                   a predictor drift, the field of the predicted charge with
+                                   the susceptibility 1 + (omega_p dt)^2 in the Poisson
+                                   operator, then the corrector and the collisions; 0: leapfrog */
 } pic_config;
 
 /* Create a context of n_instances independent PIC instances, one config each (cfg points

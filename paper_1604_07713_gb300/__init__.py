@@ -52,7 +52,7 @@ class PicConfig(C.Structure):
         ("adapt_every", C.c_int32), ("e_ref", C.c_double), ("refine_field", C.c_double),
         ("coarsen_field", C.c_double), ("refine_count", C.c_int32), ("coarsen_count", C.c_int32),
         ("mg_rel_tol", C.c_double), ("mg_max_cycles", C.c_int32), ("instance", C.c_int32),
-        ("particle_capacity", C.c_int64), ("shape", C.c_int32),
+        ("particle_capacity", C.c_int64), ("shape", C.c_int32), ("implicit", C.c_int32),
     ]
 
 

@@ -205,6 +205,8 @@ void validate(const pic_config &c) {
     if (c.shape < PIC_SHAPE_NGP || c.shape > PIC_SHAPE_CIC_EC) fail(PIC_EINVAL, "unknown particle shape");
     if (c.shape != PIC_SHAPE_NGP && c.max_level != 0)
         fail(PIC_EINVAL, "cloud-in-cell shapes need a uniform mesh (max_level 0)");
+    if (c.implicit != 0 && c.implicit != 1) fail(PIC_EINVAL, "implicit must be 0 or 1");
+    if (c.implicit && c.shape != PIC_SHAPE_NGP) fail(PIC_EINVAL, "the implicit scheme uses the NGP shape");
 }
 
 Instance &get_inst(pic_ctx *ctx, int32_t inst) {

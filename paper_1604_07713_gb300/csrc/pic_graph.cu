@@ -214,10 +214,13 @@ void one_step(pic_ctx *ctx) {
     if (graph_step_possible(ctx)) {
         graph_step(ctx);  // an ensemble in steady state: the whole step as one graph replay
     } else {
+        // the direct implicit scheme (§3 DIPIC): the predictor before the field of the step
+        for (Instance &in : ctx->inst)
+            if (in.cfg.implicit) particle_step(ctx, in, ctx->step, true, PUSH_PREDICT);
         fields_all(ctx, ctx->step);
         for (Instance &in : ctx->inst) {
             diag_accumulate(ctx, in);  // time averages of the step's state (when enabled)
-            particle_step(ctx, in, ctx->step);
+            particle_step(ctx, in, ctx->step, true, in.cfg.implicit ? PUSH_CORRECT : PUSH_LEAPFROG);
         }
     }
     ++ctx->step;
@@ -228,7 +231,7 @@ void one_step(pic_ctx *ctx) {
 bool graph_step_possible(pic_ctx *ctx) {
     if (ctx->inst.size() < 2) return false;
     for (Instance &in : ctx->inst) {
-        if (!in.has_mesh || !in.small_item || in.diag.on) return false;
+        if (!in.has_mesh || !in.small_item || in.diag.on || in.cfg.implicit) return false;
         for (int s = 0; s < in.cfg.n_species; ++s)
             if (!in.sp[s].start || !in.sp[s].sums_valid) return false;
     }

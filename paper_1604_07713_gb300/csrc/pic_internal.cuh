@@ -80,6 +80,7 @@ struct Level {
     uint8_t *color = nullptr;              // red-black colour of the cell on its own scale
     double *val64 = nullptr, *diag64 = nullptr;  // finest level only (FP64 residual)
     double *bcw = nullptr;                 // finest level: Dirichlet coefficients [4 * n]
+    double *kappa = nullptr;               // implicit scheme: relative permittivity 1 + chi per cell
     float *x = nullptr, *b = nullptr, *t = nullptr;  // FP32 work vectors
     int64_t lat_n() const { return ((int64_t)nx0 << lmax) * ((int64_t)ny0 << lmax); }
 };
@@ -416,6 +417,7 @@ void mesh_build(pic_ctx *ctx, Instance &in, int nx0, int ny0, double h0, int64_t
                 const uint32_t *root, const uint32_t *morton, const uint8_t *level);
 void mesh_build_device(pic_ctx *ctx, Instance &in, int64_t n);  // from in.root/morton/lev
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]);
+void poisson_kappa(pic_ctx *ctx, Instance &in, const double walls[4]);  // implicit: operator of this step
 void cell_emag(pic_ctx *ctx, Instance &in, const double walls[4], double *out_dev);
 void batch_prepare_node_e(pic_ctx *ctx);
 void node_e_batch(pic_ctx *ctx);
@@ -434,7 +436,11 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
                     const double *y, const double *vx, const double *vy, const double *vz,
                     const double *w, const uint64_t *id);
 void deposit(pic_ctx *ctx, Instance &in, const double walls[4]);
-void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping = true);
+// The push passes of a step: the leapfrog, or the direct implicit scheme's predictor (drift by
+// the old velocity, no kick, no collisions) and corrector (kick, drift by the kick's increment,
+// then collisions).
+enum { PUSH_LEAPFROG = 0, PUSH_PREDICT = 1, PUSH_CORRECT = 2 };
+void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping = true, int mode = PUSH_LEAPFROG);
 void particle_bookkeeping(Instance &in);  // host-side bounds after a step's launches
 void particles_read(pic_ctx *ctx, Instance &in, int s, double *x, double *y, double *vx,
                     double *vy, double *vz, double *w, uint64_t *id, uint32_t *leaf);

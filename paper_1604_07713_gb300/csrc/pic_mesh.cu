@@ -141,10 +141,14 @@ __global__ void k_check_balance(int64_t n, LatView L, int32_t *__restrict__ err)
 //   same level: g = 1 toward the neighbour;  coarse next to a fine pair: 4/3 toward the pair
 //   average; fine next to coarse N with sibling S: (2/3)((phi_c + phi_S)/2 - phi_N);
 //   Dirichlet wall: 2 toward the wall value; Neumann: nothing.
+// kappa (may be null: 1 everywhere) is the direct implicit scheme's relative permittivity
+// 1 + chi per cell: each face's conductance is multiplied by the face's kappa, the mean of
+// its two sides (at a coarse-fine face the coarse cell and the mean of the fine pair, the
+// same value in all three rows, so the operator stays conservative).
 __global__ void k_assemble(int64_t n, LatView L, int bcx, int bcy, int32_t *__restrict__ col,
                            float *__restrict__ val, float *__restrict__ dinv, double *__restrict__ val64,
                            double *__restrict__ diag64, double *__restrict__ bcw, uint8_t *__restrict__ color,
-                           int32_t *__restrict__ err) {
+                           int32_t *__restrict__ err, const double *__restrict__ kappa) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     {
@@ -159,22 +163,49 @@ __global__ void k_assemble(int64_t n, LatView L, int bcx, int bcy, int32_t *__re
     for (int d = 0; d < 4; ++d) {
         const Face f = face_of(L, (int32_t)c, d);
         const int bc = d < 2 ? bcx : bcy;
+        if (!kappa) {
+            switch (f.type) {
+            case FB:
+                if (bc == PIC_BC_DIRICHLET) { diag += 2.0; wall[d] = 2.0; }
+                break;
+            case FS:
+                diag += 1.0; cc[k] = f.n1; vv[k++] = -1.0;
+                break;
+            case FF:
+                diag += 4.0 / 3.0;
+                cc[k] = f.n1; vv[k++] = -2.0 / 3.0;
+                cc[k] = f.n2; vv[k++] = -2.0 / 3.0;
+                break;
+            case FC:
+                diag += 1.0 / 3.0;
+                cc[k] = f.sib; vv[k++] = 1.0 / 3.0;
+                cc[k] = f.n1; vv[k++] = -2.0 / 3.0;
+                break;
+            default:
+                atomicExch(err, 5);
+            }
+            continue;
+        }
+        double kf;
         switch (f.type) {
         case FB:
-            if (bc == PIC_BC_DIRICHLET) { diag += 2.0; wall[d] = 2.0; }
+            if (bc == PIC_BC_DIRICHLET) { diag += 2.0 * kappa[c]; wall[d] = 2.0 * kappa[c]; }
             break;
         case FS:
-            diag += 1.0; cc[k] = f.n1; vv[k++] = -1.0;
+            kf = 0.5 * (kappa[c] + kappa[f.n1]);
+            diag += kf; cc[k] = f.n1; vv[k++] = -kf;
             break;
         case FF:
-            diag += 4.0 / 3.0;
-            cc[k] = f.n1; vv[k++] = -2.0 / 3.0;
-            cc[k] = f.n2; vv[k++] = -2.0 / 3.0;
+            kf = 0.5 * (kappa[c] + 0.5 * (kappa[f.n1] + kappa[f.n2]));
+            diag += 4.0 / 3.0 * kf;
+            cc[k] = f.n1; vv[k++] = -2.0 / 3.0 * kf;
+            cc[k] = f.n2; vv[k++] = -2.0 / 3.0 * kf;
             break;
         case FC:
-            diag += 1.0 / 3.0;
-            cc[k] = f.sib; vv[k++] = 1.0 / 3.0;
-            cc[k] = f.n1; vv[k++] = -2.0 / 3.0;
+            kf = 0.5 * (kappa[f.n1] + 0.5 * (kappa[c] + kappa[f.sib]));
+            diag += 1.0 / 3.0 * kf;
+            cc[k] = f.sib; vv[k++] = 1.0 / 3.0 * kf;
+            cc[k] = f.n1; vv[k++] = -2.0 / 3.0 * kf;
             break;
         default:
             atomicExch(err, 5);
@@ -384,9 +415,39 @@ void assemble_level(pic_ctx *ctx, Instance &in, Level &g, bool finest, int32_t *
     g.x = dalloc<float>(A, g.n);
     g.b = dalloc<float>(A, g.n);
     g.t = dalloc<float>(A, g.n);
+    g.kappa = in.cfg.implicit ? dalloc<double>(A, g.n) : nullptr;  // set per step (poisson_kappa)
     k_assemble<<<blocks_for(g.n), kT, 0, ctx->stream>>>(g.n, view_of(in, g), in.cfg.bc_x, in.cfg.bc_y, g.col,
-                                                        g.val, g.dinv, g.val64, g.diag64, g.bcw, g.color, d_err);
+                                                        g.val, g.dinv, g.val64, g.diag64, g.bcw, g.color, d_err,
+                                                        nullptr);
     count_launch(ctx);
+}
+
+// A coarse cell's kappa: the mean over its children.
+__global__ void k_kappa_restrict(int64_t nc, const int32_t *__restrict__ child4, const double *__restrict__ kf,
+                                 double *__restrict__ kc) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nc) return;
+    double s = 0.0;
+    int m = 0;
+    for (int k = 0; k < 4; ++k) {
+        const int32_t i = child4[4 * p + k];
+        if (i >= 0) { s += kf[i]; ++m; }
+    }
+    kc[p] = m ? s / (double)m : 1.0;
+}
+
+// b = (charge + rho_bg h^2) / eps0 + sum_walls bcw phi_wall (the deposit's right-hand side,
+// formed again once the walls' coefficients carry kappa).
+__global__ void k_rhs(int64_t n, const double *__restrict__ charge, const uint8_t *__restrict__ lev, int lmax,
+                      double hf, double rho_bg, double inv_eps0, const double *__restrict__ bcw, double w0, double w1,
+                      double w2, double w3, double *__restrict__ b) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= n) return;
+    const double h = (double)(1 << (lmax - lev[L])) * hf;
+    const double wall[4] = {w0, w1, w2, w3};
+    double bl = (charge[L] + rho_bg * h * h) * inv_eps0;
+    for (int k = 0; k < 4; ++k) bl += bcw[4 * L + k] * wall[k];
+    b[L] = bl;
 }
 
 void fill_map(pic_ctx *ctx, Instance &in, Level &g) {
@@ -591,6 +652,30 @@ void node_e_batch(pic_ctx *ctx) {
         k_node_e_batch<float><<<(unsigned)t.nchunks, kT, 0, ctx->stream>>>((const NodeEEntry<float> *)t.tab, t.chunks);
     count_launch(ctx);
     check_launch("node_e_batch");
+}
+
+// The direct implicit scheme's operator for this step: kappa of the finest level (written by
+// the deposit) restricted to every coarser level, every level assembled again with it, and
+// the right-hand side formed with the new wall coefficients.
+void poisson_kappa(pic_ctx *ctx, Instance &in, const double walls[4]) {
+    cudaStream_t st = ctx->stream;
+    for (size_t g = 1; g < in.lv.size(); ++g) {
+        Level &C = in.lv[g];
+        k_kappa_restrict<<<blocks_for(C.n), kT, 0, st>>>(C.n, C.child4, in.lv[g - 1].kappa, C.kappa);
+        count_launch(ctx);
+    }
+    for (size_t g = 0; g < in.lv.size(); ++g) {
+        Level &L = in.lv[g];
+        k_assemble<<<blocks_for(L.n), kT, 0, st>>>(L.n, view_of(in, L), in.cfg.bc_x, in.cfg.bc_y, L.col, L.val,
+                                                   L.dinv, L.val64, L.diag64, L.bcw, L.color, in.d_err, L.kappa);
+        count_launch(ctx);
+    }
+    const Level &F = in.lv[0];
+    k_rhs<<<blocks_for(F.n), kT, 0, st>>>(F.n, in.charge, F.lev, in.lmax, in.h0 / (double)(1 << in.lmax),
+                                          in.cfg.rho_background, 1.0 / in.cfg.eps0, F.bcw, walls[0], walls[1],
+                                          walls[2], walls[3], in.bvec);
+    count_launch(ctx);
+    check_launch("poisson_kappa");
 }
 
 void node_e(pic_ctx *ctx, Instance &in, const double walls[4]) {

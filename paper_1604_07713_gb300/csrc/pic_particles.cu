@@ -98,6 +98,8 @@ struct DepositArgs {
     double wall[4];
     const double *wall_dev;  // non-null: the wall potentials are read from here (captured steps)
     double *charge, *b;
+    double *kappa;           // implicit scheme: 1 + chi per leaf, chi = sum_s chi[s] W_s / h^2 (else null)
+    double chi[2];           // dt^2 q_s^2 / (m_s eps0)
 };
 
 template <typename R>
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = warp; L < a.nleaf; L += nw) {
-        double total = 0.0;
+        double total = 0.0, chi = 0.0;
         for (int s = 0; s < a.nsp; ++s) {
             const int32_t p0 = a.start[s][L], p1 = a.end[s][L];
             const R *w = (const R *)a.w[s];
@@ -120,10 +122,13 @@ __global__ void __launch_bounds__(kT) k_deposit(DepositArgs a) {
             }
             R hi = sum, lo = -c;
             warp_two_sum(hi, lo);
-            total += a.q[s] * ((double)hi + (double)lo);
+            const double Ws = (double)hi + (double)lo;
+            total += a.q[s] * Ws;
+            chi += a.chi[s] * Ws;
         }
         if (lane == 0) {
             const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
+            if (a.kappa) a.kappa[L] = 1.0 + chi / (h * h);
             a.charge[L] = total;
             double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
             for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * (a.wall_dev ? a.wall_dev[k] : a.wall[k]);
@@ -146,9 +151,15 @@ template <typename R> __device__ __forceinline__ double leaf_weight(const LeafSu
 template <typename R>
 __device__ __forceinline__ void deposit_sums_leaf(const DepositArgs &a, const LeafSums &w0, const LeafSums &w1,
                                                   int64_t L) {
-    double total = a.q[0] * leaf_weight<R>(w0, L);
-    if (a.nsp > 1) total += a.q[1] * leaf_weight<R>(w1, L);
+    const double W0 = leaf_weight<R>(w0, L), W1 = a.nsp > 1 ? leaf_weight<R>(w1, L) : 0.0;
+    double total = a.q[0] * W0;
+    if (a.nsp > 1) total += a.q[1] * W1;
     const double h = (double)(1 << (a.lmax - a.lev[L])) * a.hf;
+    if (a.kappa) {
+        double chi = a.chi[0] * W0;
+        if (a.nsp > 1) chi += a.chi[1] * W1;
+        a.kappa[L] = 1.0 + chi / (h * h);
+    }
     a.charge[L] = total;
     double bl = (total + a.rho_bg * h * h) * a.inv_eps0;
     for (int k = 0; k < 4; ++k) bl += a.bcw[4 * L + k] * (a.wall_dev ? a.wall_dev[k] : a.wall[k]);
@@ -238,6 +249,7 @@ template <typename R> struct PushArgs {
     int self_wrap;        // some leaf spans a whole periodic direction (a particle may wrap back)
     // collisions
     int mcc, species;
+    int drift_kick;  // the implicit scheme's corrector: drift by the kick's increment only
     R ng_dt, sig_el, sig_iz0, eps_th, half_m_over_qe, two_qe_over_m, two_m_over_mn;
     R vt_gas;       // neutral thermal speed sqrt(T qe / M)
     R red_a, red_m, red_mn;  // ions: M / (m + M), m / (m + M), M / (m + M)
@@ -518,10 +530,12 @@ __device__ __forceinline__ void push_leaves(const PushArgs<R> &a, Queue<R> &q, c
                     ex = Bx[0] + u * Bx[1] + v * (Bx[2] + u * Bx[3]);
                     ey = By[0] + u * By[1] + v * (By[2] + u * By[3]);
                 }
-                // leapfrog kick and drift in leaf units
-                vx += a.qm_dt * ex;
-                vy += a.qm_dt * ey;
-                const R un = u + vx * dth, vn = v + vy * dth;
+                // leapfrog kick and drift in leaf units (the implicit scheme's predictor has no
+                // kick; its corrector drifts by the kick's increment)
+                const R dvx = a.qm_dt * ex, dvy = a.qm_dt * ey;
+                vx += dvx;
+                vy += dvy;
+                const R un = u + (a.drift_kick ? dvx : vx) * dth, vn = v + (a.drift_kick ? dvy : vy) * dth;
                 if (un >= (R)0 && un < (R)1 && vn >= (R)0 && vn < (R)1) {
                     stays = true;
                     u = un; v = vn;
@@ -1234,8 +1248,14 @@ template <typename R> PushArgs<R> push_args(Instance &in, int s, int64_t step) {
 
 // The push of species s in a step: with ionization the electrons count their spawns per leaf
 // and put the spawned ions into the ion lists.
-template <typename R> PushArgs<R> step_push_args(Instance &in, int s, int64_t step) {
+template <typename R> PushArgs<R> step_push_args(Instance &in, int s, int64_t step, int mode = PUSH_LEAPFROG) {
     PushArgs<R> a = push_args<R>(in, s, step);
+    if (mode == PUSH_PREDICT) {  // drift by the old velocity, no kick, no collisions
+        a.qm_dt = (R)0;
+        a.mcc = 0;
+        return a;
+    }
+    a.drift_kick = mode == PUSH_CORRECT ? 1 : 0;
     const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     if (s == 0 && ionize) {
         a.spawn = in.sp[0].spawn;
@@ -1249,10 +1269,10 @@ template <typename R> PushArgs<R> step_push_args(Instance &in, int s, int64_t st
 
 // The entering sort of species s in a step (spawned records get their ids; the entering
 // weight sums feed the next deposit).
-template <typename R> SortArgs step_sort_args(Instance &in, int s) {
+template <typename R> SortArgs step_sort_args(Instance &in, int s, int mode = PUSH_LEAPFROG) {
     Species &sp = in.sp[s];
     SortArgs a = sort_args<R>(in, sp);
-    if (in.cfg.mcc && in.cfg.sigma_iz0 > 0.0) {
+    if (mode != PUSH_PREDICT && in.cfg.mcc && in.cfg.sigma_iz0 > 0.0) {
         a.span = sp.rank0 + in.nleaf;  // the species total before the step
         a.spawn_base = in.sp[0].spawn_base;
     }
@@ -1278,7 +1298,7 @@ __global__ void k_step_reset(int64_t nl, int32_t *__restrict__ fill, int32_t *__
     }
 }
 
-template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
+template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step, int mode) {
     cudaStream_t st = ctx->stream;
     const int nsp = in.cfg.n_species;
     const int64_t nl = in.nleaf;
@@ -1313,7 +1333,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     // share of the GPU lets several instances' pushes run side by side
     const unsigned full = (unsigned)(bps * sms);
     const unsigned pb = std::min<unsigned>(wb, ctx->capturing ? std::max(1u, full / (unsigned)std::max(1, ctx->tune.graph_div)) : full);
-    const bool ionize = in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
+    const bool ionize = mode != PUSH_PREDICT && in.cfg.mcc && in.cfg.sigma_iz0 > 0.0;
     Species &e = in.sp[0];
     {
         Phase ph(ctx, PIC_PHASE_LISTS);
@@ -1328,7 +1348,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
     {
         Phase ph(ctx, PIC_PHASE_MOVE);
         for (int s = 0; s < nsp; ++s) {
-            PushArgs<R> a = step_push_args<R>(in, s, step);
+            PushArgs<R> a = step_push_args<R>(in, s, step, mode);
             if (ctx->capturing) a.step_dev = ctx->d_step;  // a captured step reads its number on the device
             if (cic) {
                 if (nt == 128) k_push<R, 128, true><<<pb, 128, push_smem, st>>>(a);
@@ -1349,7 +1369,7 @@ template <typename R> void step_impl(pic_ctx *ctx, Instance &in, int64_t step) {
         Phase ph(ctx, PIC_PHASE_SORT);
         for (int s = 0; s < nsp; ++s) {
             Species &sp = in.sp[s];
-            sort_lists<R>(ctx, step_sort_args<R>(in, s), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
+            sort_lists<R>(ctx, step_sort_args<R>(in, s, mode), soa<R>(sp, sp.cur), soa<R>(sp, sp.cur ^ 1));
             sp.sums_valid = true;
         }
         if (ionize) {
@@ -1506,8 +1526,10 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
         a.end[a.nsp] = in.sp[s].end;
         a.w[a.nsp] = in.sp[s].arr[in.sp[s].cur][5];
         a.q[a.nsp] = in.cfg.q[s];
+        a.chi[a.nsp] = in.cfg.dt * in.cfg.dt * in.cfg.q[s] * in.cfg.q[s] / (in.cfg.m[s] * in.cfg.eps0);
         ++a.nsp;
     }
+    a.kappa = in.cfg.implicit ? in.lv[0].kappa : nullptr;
     a.lev = in.lv[0].lev;
     a.lmax = in.lmax;
     a.hf = in.h0 / (double)(1 << in.lmax);
@@ -1535,6 +1557,7 @@ void deposit(pic_ctx *ctx, Instance &in, const double walls[4]) {
         k_deposit<float><<<warp_blocks(in.nleaf), kT, 0, ctx->stream>>>(a);
     count_launch(ctx);
     check_launch("deposit");
+    if (in.cfg.implicit) poisson_kappa(ctx, in, walls);  // the operator with this step's susceptibility
 }
 
 // Make sure a step cannot overflow the particle buffers: the electron count can at most
@@ -1576,10 +1599,10 @@ void ensure_slots(pic_ctx *ctx, Instance &in, int s, int64_t slots) {
     grow_species(ctx, in, s, std::max<int64_t>(slots + slots / 2, 2 * sp.cap));
 }
 
-void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping) {
-    if (in.cfg.precision == PIC_FP64) step_impl<double>(ctx, in, step);
-    else step_impl<float>(ctx, in, step);
-    if (bookkeeping) particle_bookkeeping(in);
+void particle_step(pic_ctx *ctx, Instance &in, int64_t step, bool bookkeeping, int mode) {
+    if (in.cfg.precision == PIC_FP64) step_impl<double>(ctx, in, step, mode);
+    else step_impl<float>(ctx, in, step, mode);
+    if (bookkeeping && mode != PUSH_PREDICT) particle_bookkeeping(in);  // the predictor spawns nothing
 }
 
 // Upper bounds of the populations after a step: every electron may have ionized once.

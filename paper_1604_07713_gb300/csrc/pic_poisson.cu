@@ -945,7 +945,8 @@ SmallDesc small_desc(const Instance &in, int g0) {
         SmallLevel &S = D.lv[k];
         S.n = (int32_t)L.n; S.col = L.col; S.val = L.val; S.dinv = L.dinv; S.color = L.color;
         S.child4 = L.child4; S.parent = L.parent; S.off = off;
-        S.uniform = L.lmax == 0 ? 1 : 0;
+        // (the implicit scheme's levels carry kappa in their ELL rows: no matrix-free stencil)
+        S.uniform = L.lmax == 0 && !in.cfg.implicit ? 1 : 0;
         S.nx = L.nx0;
         S.ny = L.ny0;
         // multiply-high reciprocal: floor(i * m / 2^32) == floor(i / nx) for the i < n used here
@@ -1114,7 +1115,9 @@ void poisson_setup(pic_ctx *ctx, Instance &in) {
     // coarsest-level CG needs three extra vectors: give it its own buffers
     Level &c = in.lv.back();
     c.t = dalloc<float>(A, 3 * c.n + 16);
-    in.coarse_inv = coarse_inverse(ctx, in, in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC);
+    // (the implicit scheme's coarsest operator changes every step: the CG solves it)
+    in.coarse_inv = in.cfg.implicit ? nullptr
+                                    : coarse_inverse(ctx, in, in.cfg.bc_x == PIC_BC_PERIODIC && in.cfg.bc_y == PIC_BC_PERIODIC);
     // meshes whose every level fits one block: the whole solve is one block's work item
     in.small_item = nullptr;
     if (small_from(in) == 0) {

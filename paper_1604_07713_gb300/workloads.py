@@ -36,7 +36,7 @@ def base_config(**kw) -> dict:
         phi_left_freq=0.0, phi_right=0.0, rho_background=0.0, ppc_target=32, ppc_min=8,
         ppc_max=128, adapt_every=0, e_ref=1.0, refine_field=1.5, coarsen_field=1.2,
         refine_count=128, coarsen_count=32, mg_rel_tol=1e-10, mg_max_cycles=40,
-        particle_capacity=0, instance=0, shape=0,
+        particle_capacity=0, instance=0, shape=0, implicit=0,
     )
     cfg.update(kw)
     return cfg
