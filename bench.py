@@ -36,7 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
-WORKLOADS = ("ccp", "streamer", "ensemble")
+WORKLOADS = ("ccp", "streamer", "ensemble", "ccp_implicit")
 
 
 def _dist():
@@ -49,15 +49,23 @@ PRECISION = {"fp32": 0, "fp64": 1}
 
 
 def _workload(seed, name="ccp", n_particles=50_000_000, precision="fp32"):
+    """The workload's config, mesh and particles; a name ending in '_implicit' selects the
+    direct implicit scheme (§3 DIPIC) on the same inputs."""
     from paper_1604_07713_gb300 import workloads as W
-    if name == "streamer":
-        return W.streamer_snapshot(n_particles=n_particles, seed=seed, precision=PRECISION[precision])
-    cfg, mesh, parts = W.ccp(seed=seed, precision=PRECISION[precision])
-    cfg["mg_rel_tol"] = 1e-8
+    implicit = name.endswith("_implicit")
+    base = name[:-len("_implicit")] if implicit else name
+    if base == "streamer":
+        cfg, mesh, parts = W.streamer_snapshot(n_particles=n_particles, seed=seed, precision=PRECISION[precision])
+    else:
+        cfg, mesh, parts = W.ccp(seed=seed, precision=PRECISION[precision])
+        cfg["mg_rel_tol"] = 1e-8
+    cfg["implicit"] = 1 if implicit else 0
     return cfg, mesh, parts
 
 
 def _config_json(ws, name="ccp", extra=None, precision="fp32"):
+    implicit = name.endswith("_implicit")
+    name = name[:-len("_implicit")] if implicit else name
     if name == "ensemble":
         d = {"workload": "ccp-ensemble-256-fp32", "instances": 256,
              "cells": "per instance 64-512 x 16 uniform leaves (multiples of 16 in x)",
@@ -77,6 +85,10 @@ def _config_json(ws, name="ccp", extra=None, precision="fp32"):
              "species": 2, "precision": "fp32 particle state, fp64 Poisson residual",
              "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
              "poisson_rel_tol": 1e-8}
+    if implicit:
+        d["workload"] += "-implicit"
+        d["scheme"] = ("direct implicit (§3 DIPIC): predictor push, Poisson with the susceptibility "
+                       "1 + (omega_p dt)^2, corrector push")
     if extra:
         d.update(extra)
     return d
@@ -167,7 +179,7 @@ def _oracle_sim(seed, name="ccp"):
         sim.fields()
         sim.adapt()
         return sim
-    cfg, mesh, parts = _workload(seed)
+    cfg, mesh, parts = _workload(seed, name)
     M = O.Mesh(mesh["nx0"], mesh["ny0"], mesh["h0"], 0, cfg["bc_x"], cfg["bc_y"])
     sim = O.Sim(cfg, M)
     for s in sorted(parts):
@@ -446,6 +458,8 @@ def run_gpu(args):
     rs = 8 if args.precision == "fp64" else 4
     move_ms, move_launches = phases["move"]
     push_label = f"k_push<{'double' if rs == 8 else 'float'}> in-place push (both species)"
+    if name.endswith("_implicit"):
+        push_label += ", the implicit scheme's predictor and corrector passes"
     graph_ms = phases.get("graph", (0.0, 0))[0]
     if ensemble and move_ms > 0.0 and graph_ms > 0.0:
         # the batched step's replays time their phases inside the graph (event nodes)
@@ -456,7 +470,8 @@ def run_gpu(args):
         move_ms = phases["graph"][0]
         push_label = "whole step (graph replay; push bytes over step time: a lower bound)"
     move_s = move_ms * 1e-3
-    alg_bytes = (11 * rs + 4) * particle_steps + leaf_steps * 2 * (10 * rs + 12)
+    passes = 2 if name.endswith("_implicit") else 1  # the implicit scheme's predictor and corrector
+    alg_bytes = passes * ((11 * rs + 4) * particle_steps + leaf_steps * 2 * (10 * rs + 12))
     achieved = alg_bytes / move_s / 1e9 if move_s > 0 else 0.0
     tr = _traffic_record(name) if args.precision == "fp32" else None
     # with phases timed inside graph replays, the replay's total is not a phase of its own
