@@ -685,10 +685,11 @@ struct SortArgs {
     int32_t *err;
 };
 
-__device__ __forceinline__ uint32_t spawn_id(const SortArgs &a, uint32_t span, uint32_t key, uint32_t aux,
-                                             uint32_t id) {
+// `nid` is *a.next_id, read once per warp (it holds still during the sorts).
+__device__ __forceinline__ uint32_t spawn_id(const SortArgs &a, uint32_t span, unsigned long long nid, uint32_t key,
+                                             uint32_t aux, uint32_t id) {
     if (key < span) return id;
-    return (uint32_t)(*a.next_id + 2ull * ((unsigned long long)a.spawn_base[aux] + id) + a.ion_bit);
+    return (uint32_t)(nid + 2ull * ((unsigned long long)a.spawn_base[aux] + id) + a.ion_bit);
 }
 
 // Entering region of leaf L, or k < 0 when it cannot be (an aborted re-layout).
@@ -704,15 +705,19 @@ __device__ __forceinline__ void entering_region(const SortArgs &a, int64_t L, in
 }
 
 constexpr int kSortSmem = 512;  // per-warp shared-memory sort capacity (keys + slots)
+constexpr int kSortRegs = 160;  // entering regions up to this long sort in registers
 
 // Sort the k <= 32 P entries at [b0, b0 + k) into [q0, q0 + k) in registers (one warp): lane
 // j holds records b0 + j + 32 m; a record's rank is the number of smaller keys (keys are
 // distinct), counted against every key broadcast by shuffles.  Every record is in registers
-// before any is stored (the region and its destination may overlap).
+// before any is stored (the region and its destination may overlap).  Each record's key,
+// aux word and payload are loaded together (the aux word serves spawned records only), and
+// `nid` is the list's next id, read once by the caller.  With `wr` non-null the weights are
+// also written there in key order (wr[rank]) for the caller's entering sum.
 template <typename R, int P>
-__device__ __forceinline__ void sort_region_regs(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0,
-                                                 int lane, const SoA<R> &d) {
-    uint32_t key[P], id[P];
+__device__ __forceinline__ void sort_region_regs(const SortArgs &a, uint32_t span, unsigned long long nid, int32_t b0,
+                                                 int32_t k, int32_t q0, int lane, const SoA<R> &d, R *wr) {
+    uint32_t key[P], aux[P], id[P];
     int rank[P];
     R u[P], v[P], vx[P], vy[P], vz[P], w[P];
 #pragma unroll
@@ -720,18 +725,25 @@ __device__ __forceinline__ void sort_region_regs(const SortArgs &a, uint32_t spa
         const int32_t i = lane + 32 * m;
         const int32_t p = b0 + i;
         const bool act = i < k;
-        key[m] = act ? a.key[p] : 0xFFFFFFFFu;
+        key[m] = 0xFFFFFFFFu;
+        aux[m] = 0;
         rank[m] = 0;
         u[m] = v[m] = vx[m] = vy[m] = vz[m] = w[m] = (R)0;
         id[m] = 0;
         if (act) {
+            key[m] = a.key[p]; aux[m] = a.aux[p];
             u[m] = d.u[p]; v[m] = d.v[p]; vx[m] = d.vx[p]; vy[m] = d.vy[p]; vz[m] = d.vz[p]; w[m] = d.w[p];
-            id[m] = spawn_id(a, span, key[m], key[m] >= span ? a.aux[p] : 0u, d.id[p]);
+            id[m] = d.id[p];
         }
     }
 #pragma unroll
+    for (int m = 0; m < P; ++m)
+        if (key[m] >= span && lane + 32 * m < k)
+            id[m] = (uint32_t)(nid + 2ull * ((unsigned long long)a.spawn_base[aux[m]] + id[m]) + a.ion_bit);
+#pragma unroll
     for (int mm = 0; mm < P; ++mm) {
         const int nj = min(32, k - 32 * mm);  // keys of column mm (warp-uniform)
+#pragma unroll 4
         for (int j = 0; j < nj; ++j) {
             const uint32_t o = __shfl_sync(0xFFFFFFFFu, key[mm], j);
 #pragma unroll
@@ -745,20 +757,23 @@ __device__ __forceinline__ void sort_region_regs(const SortArgs &a, uint32_t spa
             const int32_t q = q0 + rank[m];
             d.u[q] = u[m]; d.v[q] = v[m]; d.vx[q] = vx[m]; d.vy[q] = vy[m]; d.vz[q] = vz[m]; d.w[q] = w[m];
             d.id[q] = id[m];
+            if (wr) wr[rank[m]] = w[m];
         }
     __syncwarp();
 }
 
-// Sort the k entries at [b0, b0 + k) into [q0, q0 + k) (one warp).  Up to 160 entries sort
-// in registers; up to 512 by a bitonic network on (key, slot) pairs in the warp's shared
-// memory followed by a gather through the scratch buffer `t`.
+// Sort the k entries at [b0, b0 + k) into [q0, q0 + k) (one warp).  Up to kSortRegs entries
+// sort in registers (their weights also go to `wr` in key order when it is non-null); up to
+// 512 by a bitonic network on (key, slot) pairs in the warp's shared memory followed by a
+// gather through the scratch buffer `t`.
 template <typename R>
-__device__ void sort_region(const SortArgs &a, uint32_t span, int32_t b0, int32_t k, int32_t q0, int lane, SoA<R> d,
-                            SoA<R> t, unsigned long long *wsm) {
-    if (k <= 32) { sort_region_regs<R, 1>(a, span, b0, k, q0, lane, d); return; }
-    if (k <= 64) { sort_region_regs<R, 2>(a, span, b0, k, q0, lane, d); return; }
-    if (k <= 96) { sort_region_regs<R, 3>(a, span, b0, k, q0, lane, d); return; }
-    if (k <= 160) { sort_region_regs<R, 5>(a, span, b0, k, q0, lane, d); return; }
+__device__ void sort_region(const SortArgs &a, uint32_t span, unsigned long long nid, int32_t b0, int32_t k, int32_t q0,
+                            int lane, SoA<R> d, SoA<R> t, unsigned long long *wsm, R *wr) {
+    if (k <= 32) { sort_region_regs<R, 1>(a, span, nid, b0, k, q0, lane, d, wr); return; }
+    if (k <= 64) { sort_region_regs<R, 2>(a, span, nid, b0, k, q0, lane, d, wr); return; }
+    if (k <= 96) { sort_region_regs<R, 3>(a, span, nid, b0, k, q0, lane, d, wr); return; }
+    if (k <= 128) { sort_region_regs<R, 4>(a, span, nid, b0, k, q0, lane, d, wr); return; }
+    if (k <= kSortRegs) { sort_region_regs<R, 5>(a, span, nid, b0, k, q0, lane, d, wr); return; }
     // copy the region to the scratch buffer
     for (int32_t p = b0 + lane; p < b0 + k; p += 32) {
         t.u[p] = d.u[p]; t.v[p] = d.v[p]; t.vx[p] = d.vx[p]; t.vy[p] = d.vy[p];
@@ -787,7 +802,7 @@ __device__ void sort_region(const SortArgs &a, uint32_t span, int32_t b0, int32_
         const uint32_t kk = (uint32_t)(wsm[r] >> 32);
         d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
         d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
-        d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
+        d.id[q] = spawn_id(a, span, nid, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
     }
     __syncwarp();
 }
@@ -801,6 +816,7 @@ template <typename R>
 __device__ __forceinline__ void sort_big_leaves(const SortArgs &a, const SoA<R> &d, const SoA<R> &t, int32_t first,
                                                 int32_t stride, unsigned long long *bk, R *red_hi, R *red_lo) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
+    const unsigned long long nid = a.span ? *a.next_id : 0ull;
     const int32_t nbig = a.big[a.nleaf];
     for (int32_t li = first; li < nbig; li += stride) {
         const int32_t L = a.big[li];
@@ -835,7 +851,7 @@ __device__ __forceinline__ void sort_big_leaves(const SortArgs &a, const SoA<R> 
                 const uint32_t kk = (uint32_t)(bk[r] >> 32);
                 d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
                 d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
-                d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
+                d.id[q] = spawn_id(a, span, nid, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
             }
         } else {
             for (int32_t p = b0 + threadIdx.x; p < b0 + k; p += blockDim.x) {
@@ -845,7 +861,7 @@ __device__ __forceinline__ void sort_big_leaves(const SortArgs &a, const SoA<R> 
                 const int32_t q = q0 + rank;
                 d.u[q] = t.u[p]; d.v[q] = t.v[p]; d.vx[q] = t.vx[p]; d.vy[q] = t.vy[p];
                 d.vz[q] = t.vz[p]; d.w[q] = t.w[p];
-                d.id[q] = spawn_id(a, span, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
+                d.id[q] = spawn_id(a, span, nid, kk, kk >= span ? a.taux[p] : 0u, t.id[p]);
             }
         }
         __syncthreads();
@@ -878,16 +894,6 @@ __global__ void __launch_bounds__(512) k_sort_big(SortArgs a, SoA<R> d, SoA<R> t
 
 constexpr int kSortLane = 8;  // entering regions up to this long are sorted by a leaf's 8-lane group
 
-// The entering weights of a leaf in order (a few entering particles: one lane, Kahan), as the
-// (sum, -compensation) pair that the next deposit combines.
-template <typename R> __device__ __forceinline__ void entering_weight_seq(const SortArgs &a, int64_t L, SoA<R> d,
-                                                                          int32_t q0, int32_t k) {
-    R sum = 0, c = 0;
-    for (int32_t q = q0; q < q0 + k; ++q) kahan_add(sum, c, d.w[q]);
-    ((R *)a.ent_hi)[L] = sum;
-    ((R *)a.ent_lo)[L] = -c;
-}
-
 // Entering regions of every leaf, 8 lanes per leaf (4 leaves per warp pass): a short region
 // (k <= kSortLane records) is sorted by its leaf's lane group, lane i holding record b0 + i,
 // so that each of the record's arrays is read and written in one contiguous access per leaf;
@@ -900,6 +906,7 @@ template <typename R>
 __device__ __forceinline__ void sort_entering_groups(const SortArgs &a, const SoA<R> &d, const SoA<R> &t,
                                                      int64_t first, int64_t last, int64_t stride) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
+    const unsigned long long nid = a.span ? *a.next_id : 0ull;
     const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
     for (int64_t W = first; W * 4 < last; W += stride) {
         const int64_t L = W * 4 + g;
@@ -918,7 +925,7 @@ __device__ __forceinline__ void sort_entering_groups(const SortArgs &a, const So
             u = d.u[p]; v = d.v[p]; vx = d.vx[p]; vy = d.vy[p]; vz = d.vz[p]; w = d.w[p];
             id = d.id[p];
             key = a.key[p];
-            id = spawn_id(a, span, key, key >= span ? a.aux[p] : 0u, id);
+            id = spawn_id(a, span, nid, key, key >= span ? a.aux[p] : 0u, id);
         }
         // rank among the group's keys (keys are distinct)
         int r = 0;
@@ -962,27 +969,50 @@ __global__ void __launch_bounds__(kT) k_sort_entering(SortArgs a, SoA<R> d, SoA<
 }
 
 // Medium entering regions (kSortLane < k <= kSortSmem): one warp per listed leaf; the warp
-// takes the list entries first, first + stride, ... below last.
+// takes the list entries first, first + stride, ... below last.  Lane 0 fetches the next
+// entry's leaf and region words while the current region is sorted.  A region sorted in
+// registers leaves its weights in key order in the warp's shared memory, from which the
+// entering sum is taken (the same order and arithmetic as from the sorted list).
 template <typename R>
 __device__ __forceinline__ void sort_medium_leaves(const SortArgs &a, const SoA<R> &d, const SoA<R> &t, int64_t first,
                                                    int64_t last, int64_t stride, unsigned long long *wsm) {
     const uint32_t span = a.span ? (uint32_t)*a.span : 0xFFFFFFFFu;
+    const unsigned long long nid = a.span ? *a.next_id : 0ull;
     const int lane = threadIdx.x & 31;
     const int64_t nmed = min((int64_t)a.med[a.nleaf], last);
+    int32_t nL = 0, nb0 = 0, nk = 0, nq0 = 0, nlim = 0;  // lane 0: the next entry's words
+    auto fetch = [&](int64_t i) {
+        if (lane == 0 && i < nmed) {
+            nL = a.med[i];
+            nb0 = a.end[nL]; nk = a.fill[nL]; nq0 = a.start[nL] + a.stay[nL]; nlim = a.lim[nL];
+        }
+    };
+    fetch(first);
+    R *wr = reinterpret_cast<R *>(wsm);
     for (int64_t i = first; i < nmed; i += stride) {
-        const int64_t L = a.med[i];
-        int32_t b0, k, q0;
-        if (lane == 0) entering_region(a, L, b0, k, q0);
+        int32_t L = nL, b0 = nb0, k = nk, q0 = nq0;
+        if (lane == 0 && (b0 + k > nlim || q0 > b0)) {  // an aborted re-layout
+            k = -1;
+            atomicExch(a.err, 1);
+        }
+        L = __shfl_sync(0xFFFFFFFFu, L, 0);
         b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
-        sort_region<R>(a, span, b0, k, q0, lane, d, t, wsm);
+        fetch(i + stride);
+        const bool staged = a.ent_hi && k <= kSortRegs;
+        sort_region<R>(a, span, nid, b0, k, q0, lane, d, t, wsm, staged ? wr : nullptr);
         if (a.ent_hi) {
             if (k <= 16) {
-                if (lane == 0) entering_weight_seq<R>(a, L, d, q0, k);
+                if (lane == 0) {
+                    R sum = 0, c = 0;
+                    for (int32_t r = 0; r < k; ++r) kahan_add(sum, c, wr[r]);
+                    ((R *)a.ent_hi)[L] = sum;
+                    ((R *)a.ent_lo)[L] = -c;
+                }
             } else {
                 R sum = 0, c = 0;
-                for (int32_t q = q0 + lane; q < q0 + k; q += 32) kahan_add(sum, c, d.w[q]);
+                for (int32_t r = lane; r < k; r += 32) kahan_add(sum, c, staged ? wr[r] : d.w[q0 + r]);
                 R hi = sum, lo = -c;
                 warp_two_sum(hi, lo);
                 if (lane == 0) {
@@ -992,6 +1022,7 @@ __device__ __forceinline__ void sort_medium_leaves(const SortArgs &a, const SoA<
             }
         }
         if (lane == 0) a.end[L] = q0 + k;
+        __syncwarp();  // the staged weights are read before the next region overwrites them
     }
 }
 
