@@ -6,6 +6,7 @@
 #include <cstring>
 #include <array>
 #include <exception>
+#include <iterator>
 #include <new>
 
 #include "pic_internal.cuh"
@@ -94,7 +95,16 @@ void BlockCache::put(void *p) {
     }
     idle.emplace(it->second, p);
     idle_bytes += it->second;
-    if (idle_bytes > kCacheMaxIdle) trim();
+    // over the limit: the largest idle blocks go back to the driver first, so that a growth
+    // of the particle buffers does not also evict the mesh's many small blocks (which the
+    // next adaptation would then have to cudaMalloc again)
+    while (idle_bytes > kCacheMaxIdle && !idle.empty()) {
+        auto big = std::prev(idle.end());
+        cudaFree(big->second);
+        cls.erase(big->second);
+        idle_bytes -= big->first;
+        idle.erase(big);
+    }
 }
 void BlockCache::trim() {
     for (auto &e : idle) {

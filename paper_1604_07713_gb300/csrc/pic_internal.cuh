@@ -44,7 +44,7 @@ struct BlockCache {
     size_t idle_bytes = 0;
     int64_t fail_after = -1;  // injected fault: this many more blocks succeed, then one fails
     void *get(size_t bytes);
-    void put(void *p);
+    void put(void *p);  // over the idle limit, the largest idle blocks are freed first
     void trim();  // cudaFree every cached block
 };
 
