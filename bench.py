@@ -539,7 +539,9 @@ def run_gpu(args):
                                               "note": "the first instances of the ensemble, each alone, same steps"}
     # end to end through the C ABI with host buffers: load (H2D) + one step + read phi (D2H)
     if not args.no_e2e and not ensemble:
-        host = {s: {k: np.ascontiguousarray(v) for k, v in parts[s].items()} for s in parts}
+        # the step's inputs in pinned host memory (numpy views of page-locked tensors)
+        host = {s: {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in parts[s].items()}
+                for s in parts}
         h2d = sum(v.nbytes for s in host for v in host[s].values())
         e2e_steps = 3 if streamer else max(3, min(args.steps, 10))
         t_e2e = 0.0

@@ -408,6 +408,9 @@ pic_status pic_destroy(pic_ctx *ctx) {
     ctx->batch_mem.release_all();
     graph_release(ctx);
     for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
+    if (ctx->load_side) cudaStreamDestroy(ctx->load_side);
+    for (auto ev : ctx->load_ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto st : ctx->fork) cudaStreamDestroy(st);
     for (auto ev : ctx->fork_ev) cudaEventDestroy(ev);
     if (ctx->d_step) cudaFree(ctx->d_step);

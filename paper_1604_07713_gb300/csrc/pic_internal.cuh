@@ -291,6 +291,8 @@ struct pic_ctx {
     int64_t graph_nodes = 0;         // kernel launches of one replay
     std::vector<cudaStream_t> fork;  // branches of the captured step
     std::vector<cudaEvent_t> fork_ev;
+    cudaStream_t load_side = nullptr;              // particle loads: copies beside the context's stream
+    cudaEvent_t load_ev[2] = {nullptr, nullptr};
     void *report_dev = nullptr, *report_host = nullptr;  // end-of-call report, one entry per instance
     void *report_tab = nullptr;      // device table the report kernel reads
     int64_t report_epoch = -1;

@@ -635,12 +635,23 @@ void species_leaf_arrays(pic_ctx *ctx, Instance &in, int s, int64_t nl) {
         if (p) A.release(p);
 }
 
-// Buffers of one species with `cap` slots each, and its per-leaf arrays (no records).
+// Buffers of one species with `cap` slots each, and its per-leaf arrays (no records).  A
+// species that already holds buffers of `cap` slots keeps them (a reload of the same
+// population size costs no allocation): only their contents are dropped.
 void species_alloc(pic_ctx *ctx, Instance &in, int s, int64_t cap) {
     ++ctx->lists_epoch;
     Species &sp = in.sp[s];
     DeviceArena &A = in.part_mem[s];
+    if (sp.flags && sp.cap == cap && !A.blocks.empty()) {  // (a growth hands the old blocks over first)
+        GB_CUDA(cudaMemsetAsync(sp.flags, 0, 8 * 4, ctx->stream));
+        species_leaf_arrays(ctx, in, s, in.nleaf);
+        sp.cur = 0;
+        sp.n = 0;
+        sp.n_upper = 0;
+        return;
+    }
     A.release_all();
+    sp.flags = nullptr;
     sp.start = sp.end = sp.lim = sp.rank0 = sp.start_new = sp.stay = sp.inc = sp.fill = sp.big = sp.moved = nullptr;
     sp.spawn = sp.spawn_base = nullptr;
     sp.stay_hi = sp.stay_lo = nullptr;

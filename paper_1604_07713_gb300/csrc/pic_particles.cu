@@ -1116,27 +1116,45 @@ __global__ void k_locate_load(int64_t n, const double *__restrict__ x, const dou
     slot[i] = atomicAdd(cnt + l, 1);
 }
 
-template <typename R>
-__global__ void k_place_load(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                             const double *__restrict__ vx, const double *__restrict__ vy,
-                             const double *__restrict__ vz, const double *__restrict__ w,
-                             const unsigned long long *__restrict__ id, unsigned long long id0, double hf, int lmax,
-                             const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
-                             const uint8_t *__restrict__ lev, const int32_t *__restrict__ leaf,
-                             const int32_t *__restrict__ slot, const int32_t *__restrict__ start, SoA<R> d,
-                             uint32_t *__restrict__ key) {
+// The loaded record i goes to slot q = start[leaf[i]] + slot[i] of its list: perm[q] = i
+// (perm spans every slot of the lists, free ones included).
+__global__ void k_load_perm(int64_t n, const int32_t *__restrict__ leaf, const int32_t *__restrict__ slot,
+                            const int32_t *__restrict__ start, int32_t *__restrict__ perm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t l = leaf[i];
-    const int32_t q = start[l] + slot[i];
-    const double h = (double)(1 << (lmax - lev[l])) * hf;
-    R u = (R)((x[i] - (double)ix[l] * hf) / h), v = (R)((y[i] - (double)iy[l] * hf) / h);
-    u = u < (R)0 ? (R)0 : (u >= (R)1 ? below_one<R>() : u);
-    v = v < (R)0 ? (R)0 : (v >= (R)1 ? below_one<R>() : v);
-    d.u[q] = u; d.v[q] = v;
-    d.vx[q] = (R)vx[i]; d.vy[q] = (R)vy[i]; d.vz[q] = (R)vz[i]; d.w[q] = (R)w[i];
-    d.id[q] = (uint32_t)(id ? id[i] : id0 + (unsigned long long)i);
-    key[q] = (uint32_t)i;
+    if (i < n) perm[start[leaf[i]] + slot[i]] = (int32_t)i;
+}
+
+// One warp per leaf: the leaf's cnt[L] loaded records, gathered from the input through perm,
+// written to [start[L], start[L] + cnt[L]) with their offsets in the leaf, FP32 or FP64
+// payload, id (given, or id0 + input index) and the input index as the order key.  Every
+// array is written in contiguous runs; the input is read at the permuted indices.
+template <typename R>
+__global__ void k_gather_load(int64_t nleaf, const int32_t *__restrict__ start, const int32_t *__restrict__ cnt,
+                              const int32_t *__restrict__ perm, const double *__restrict__ x,
+                              const double *__restrict__ y, const double *__restrict__ vx,
+                              const double *__restrict__ vy, const double *__restrict__ vz,
+                              const double *__restrict__ w, const unsigned long long *__restrict__ id,
+                              unsigned long long id0, double hf, int lmax, const int32_t *__restrict__ ix,
+                              const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, SoA<R> d,
+                              uint32_t *__restrict__ key) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t L = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; L < nleaf; L += nw) {
+        const int32_t q0 = start[L], k = cnt[L];
+        if (k == 0) continue;
+        const double h = (double)(1 << (lmax - lev[L])) * hf;
+        const double cx = (double)ix[L], cy = (double)iy[L];
+        for (int32_t r = lane; r < k; r += 32) {
+            const int32_t q = q0 + r, i = perm[q];
+            R u = (R)((x[i] - cx * hf) / h), v = (R)((y[i] - cy * hf) / h);
+            u = u < (R)0 ? (R)0 : (u >= (R)1 ? below_one<R>() : u);
+            v = v < (R)0 ? (R)0 : (v >= (R)1 ? below_one<R>() : v);
+            d.u[q] = u; d.v[q] = v;
+            d.vx[q] = (R)vx[i]; d.vy[q] = (R)vy[i]; d.vz[q] = (R)vz[i]; d.w[q] = (R)w[i];
+            d.id[q] = (uint32_t)(id ? id[i] : id0 + (unsigned long long)i);
+            key[q] = (uint32_t)i;
+        }
+    }
 }
 
 // Read-back: absolute FP64 positions and leaf index per particle, at the particle's rank in
@@ -1479,16 +1497,27 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     DeviceArena tmp(&ctx->cache);
     double *d[6];
     const double *h[6] = {x, y, vx, vy, vz, w};
-    for (int k = 0; k < 6; ++k) {
-        d[k] = dalloc<double>(tmp, n);
-        if (n) GB_CUDA(cudaMemcpyAsync(d[k], h[k], n * 8, cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < 6; ++k) d[k] = dalloc<double>(tmp, n);
+    unsigned long long *did = id && n ? dalloc<unsigned long long>(tmp, n) : nullptr;
+    // x and y on the context's stream, the rest on a side stream: the location and the list
+    // layout run while the velocities, weights and ids are still copied
+    if (!ctx->load_side) {
+        GB_CUDA(cudaStreamCreateWithFlags(&ctx->load_side, cudaStreamNonBlocking));
+        for (auto &ev : ctx->load_ev) GB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
-    unsigned long long *did = nullptr;
-    if (id && n) {
-        did = dalloc<unsigned long long>(tmp, n);
-        GB_CUDA(cudaMemcpyAsync(did, id, n * 8, cudaMemcpyHostToDevice, st));
+    cudaStream_t side = ctx->load_side;
+    GB_CUDA(cudaEventRecord(ctx->load_ev[0], st));  // the side copies follow what the stream has queued
+    GB_CUDA(cudaStreamWaitEvent(side, ctx->load_ev[0], 0));
+    if (n) {
+        for (int k = 0; k < 2; ++k) GB_CUDA(cudaMemcpyAsync(d[k], h[k], n * 8, cudaMemcpyHostToDevice, st));
+        for (int k = 2; k < 6; ++k) GB_CUDA(cudaMemcpyAsync(d[k], h[k], n * 8, cudaMemcpyHostToDevice, side));
+        if (did) GB_CUDA(cudaMemcpyAsync(did, id, n * 8, cudaMemcpyHostToDevice, side));
     }
+    GB_CUDA(cudaEventRecord(ctx->load_ev[1], side));
     int32_t *leaf = dalloc<int32_t>(tmp, n), *slot = dalloc<int32_t>(tmp, n);
+    // perm is indexed by list slot (free slots included, below cap): the scratch buffer's
+    // id array holds cap words and is free until the entering sort
+    int32_t *perm = reinterpret_cast<int32_t *>(sp.id[1]);
     int32_t *err = dalloc<int32_t>(tmp, 1);
     GB_CUDA(cudaMemsetAsync(err, 0, 4, st));
     GB_CUDA(cudaMemsetAsync(sp.fill, 0, (nl + 1) * 4, st));
@@ -1504,6 +1533,7 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     GB_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
     if (herr) {
+        GB_CUDA(cudaStreamSynchronize(side));  // no copy may still write a released block
         tmp.release_all();
         fail(PIC_EINVAL, "particle position outside the domain");
     }
@@ -1514,14 +1544,20 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     GB_CUDA(cudaMemcpyAsync(sp.end, sp.start, nl * 4, cudaMemcpyDeviceToDevice, st));
     const unsigned long long id0 = id ? 0ull : next_id;
     if (n) {
+        k_load_perm<<<blocks_for(n), kT, 0, st>>>(n, leaf, slot, sp.start, perm);
+        count_launch(ctx);
+    }
+    GB_CUDA(cudaStreamWaitEvent(st, ctx->load_ev[1], 0));  // every input array is on the device
+    if (n) {
+        const unsigned gb = (unsigned)std::min<int64_t>((nl + kT / 32 - 1) / (kT / 32), 152 * 64);
         if (in.cfg.precision == PIC_FP64)
-            k_place_load<double><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], did, id0, hf,
-                                                               in.lmax, g.ix, g.iy, g.lev, leaf, slot, sp.start,
-                                                               soa<double>(sp, 0), sp.key);
+            k_gather_load<double><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, d[0], d[1], d[2], d[3], d[4], d[5],
+                                                     did, id0, hf, in.lmax, g.ix, g.iy, g.lev, soa<double>(sp, 0),
+                                                     sp.key);
         else
-            k_place_load<float><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], did, id0, hf,
-                                                              in.lmax, g.ix, g.iy, g.lev, leaf, slot, sp.start,
-                                                              soa<float>(sp, 0), sp.key);
+            k_gather_load<float><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, d[0], d[1], d[2], d[3], d[4], d[5],
+                                                    did, id0, hf, in.lmax, g.ix, g.iy, g.lev, soa<float>(sp, 0),
+                                                    sp.key);
         count_launch(ctx);
     }
     if (in.cfg.precision == PIC_FP64)

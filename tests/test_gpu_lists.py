@@ -128,3 +128,36 @@ def test_long_entering_regions_and_long_loaded_lists_keep_the_oracle_order(nb):
     _check(res, W.FP64)
     g, _ = res[0]
     assert np.bincount(g[0]["leaf"].astype(np.int64), minlength=16).max() >= 0.45 * nb
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32])
+def test_repeated_loads_into_one_context_round_trip(precision):
+    # loads of either species in any order, a species loaded again with the same size (its
+    # buffers are kept) and with another size: every read-back equals its input by id, and
+    # the per-leaf counts are the histogram of the input positions
+    cfg, mesh, parts = W.ccp(nx=32, ny=8, ppc=40, seed=5, precision=precision, te=30.0, ng=3e21)
+    rng = np.random.default_rng(7)
+    small = {k: v[: v.size // 3].copy() for k, v in parts[0].items()}
+    small["x"] = small["x"][rng.permutation(small["x"].size)]
+    h0, nx, ny = mesh["h0"], mesh["nx0"], mesh["ny0"]
+
+    def check(ctx, s, p):
+        g = ctx.particles(s)
+        assert g["x"].size == p["x"].size
+        ids = g["id"].astype(np.int64)
+        o = np.argsort(ids)
+        assert np.array_equal(ids[o], np.arange(ids.size) + ids.min())  # id = first id + input index
+        tol = 0.0 if precision == W.FP64 else 1e-6
+        for k in ("x", "y", "vx", "vy", "vz", "w"):
+            a, b = g[k][o], p[k]
+            assert np.abs(a - b).max() <= tol * max(1e-300, np.abs(b).max()) + (1e-15 * h0 if k in "xy" else 0), (s, k)
+        hist = np.zeros(nx * ny)
+        np.add.at(hist, np.floor(p["y"] / h0).astype(int) * nx + np.floor(p["x"] / h0).astype(int), 1)
+        cnt = ctx.fields(G.PIC_FIELD_COUNT_E if s == 0 else G.PIC_FIELD_COUNT_I)
+        assert np.array_equal(np.sort(cnt), np.sort(hist))
+
+    with G.Context(cfg) as ctx:
+        ctx.set_mesh_dict(mesh)
+        for s, p in ((1, parts[1]), (0, parts[0]), (0, parts[0]), (1, parts[1]), (0, small), (0, parts[0])):
+            ctx.load(s, **p)
+            check(ctx, s, p)
