@@ -543,7 +543,7 @@ def run_gpu(args):
         host = {s: {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in parts[s].items()}
                 for s in parts}
         h2d = sum(v.nbytes for s in host for v in host[s].values())
-        e2e_steps = 3 if streamer else max(3, min(args.steps, 10))
+        e2e_steps = 6 if streamer else max(3, min(args.steps, 10))
         t_e2e = 0.0
         n_e2e = 0
         for k in range(e2e_steps + 1):

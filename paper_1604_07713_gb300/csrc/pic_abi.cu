@@ -50,7 +50,7 @@ size_t size_class(size_t b) {
     return (b + g - 1) / g * g;
 }
 constexpr size_t kCacheMaxBlock = (size_t)512 << 20;  // larger blocks are freed, not cached
-constexpr size_t kCacheMaxIdle = (size_t)4 << 30;     // idle bytes kept at most
+constexpr size_t kCacheMaxIdle = (size_t)8 << 30;     // idle bytes kept at most
 
 void *raw_alloc(size_t bytes) {
     void *p = nullptr;

@@ -17,38 +17,75 @@ namespace gbpic {
 
 namespace {
 constexpr int kT = 256;
-inline unsigned warp_blocks(int64_t nw) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((nw + kT / 32 - 1) / (kT / 32), 1 << 20));
-}
 
-// Per leaf: W, W / h^2, sum w v (3) and sum w v^2 (3) of one species' records (FP64 lanes,
-// lanes combined by a fixed shuffle tree).
+// The electrons' moments for the explicit-PIC limits, in two passes.  Pass 1, a fixed grid of
+// kMomBlocks blocks (warps over leaves, grid-stride): per leaf the weight sum W_L (one warp
+// reduction), its maximum and the maximum density W_L / h_L^2 over the warp's leaves; the
+// weighted velocity sums (w v, w v^2 per component) per lane across all its leaves, reduced
+// once at the end (FP64 lanes, fixed shuffle trees).  Each warp writes kMomWords words:
+// {max W_L, max density, sum W_L, 3 x sum w v, 3 x sum w v^2}.  Pass 2, one block,
+// combines the warps' words in a fixed tree (maxima for the first two).  The grid, the leaf
+// assignment and both trees are fixed, so the result does not depend on scheduling.
+constexpr int kMomBlocks = 152 * 4;
+constexpr int kMomWarps = kMomBlocks * (kT / 32);
+constexpr int kMomWords = 9;
 template <typename R>
-__global__ void k_leaf_moments(int64_t nl, const int32_t *__restrict__ start, const int32_t *__restrict__ end,
-                               const uint8_t *__restrict__ lev, int lmax, double hf, SoA<R> d,
-                               double *__restrict__ out) {
+__global__ void __launch_bounds__(kT) k_leaf_moments(int64_t nl, const int32_t *__restrict__ start,
+                                                     const int32_t *__restrict__ end, const uint8_t *__restrict__ lev,
+                                                     int lmax, double hf, SoA<R> d, double *__restrict__ part) {
     const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t L = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; L < nl; L += nw) {
-        double m[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    double w_max = 0.0, n_max = 0.0, w_tot = 0.0;
+    for (int64_t L = warp; L < nl; L += kMomWarps) {
+        double wl = 0.0;
         for (int32_t p = start[L] + lane; p < end[L]; p += 32) {
             const double w = (double)d.w[p], vx = (double)d.vx[p], vy = (double)d.vy[p], vz = (double)d.vz[p];
-            m[0] += w;
-            m[1] += w * vx; m[2] += w * vy; m[3] += w * vz;
-            m[4] += w * vx * vx; m[5] += w * vy * vy; m[6] += w * vz * vz;
+            wl += w;
+            const double a = w * vx, b = w * vy, c = w * vz;
+            m[0] += a; m[1] += b; m[2] += c;
+            m[3] += a * vx; m[4] += b * vy; m[5] += c * vz;
         }
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xFFFFFFFFu, m[k], o);
-        if (lane == 0) {
-            const double h = (double)(1 << (lmax - lev[L])) * hf;
-            double *o = out + 8 * L;
-            o[0] = m[0];
-            o[1] = m[0] / (h * h);
-            for (int k = 1; k < 7; ++k) o[k + 1] = m[k];
-        }
+        for (int o = 16; o > 0; o >>= 1) wl += __shfl_xor_sync(0xFFFFFFFFu, wl, o);
+        const double h = (double)(1 << (lmax - lev[L])) * hf;
+        w_max = fmax(w_max, wl);
+        n_max = fmax(n_max, wl / (h * h));
+        w_tot += wl;
     }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xFFFFFFFFu, m[k], o);
+    if (lane == 0) {
+        double *o = part + kMomWords * warp;
+        o[0] = w_max; o[1] = n_max; o[2] = w_tot;
+        for (int k = 0; k < 6; ++k) o[3 + k] = m[k];
+    }
+}
+
+constexpr int kMomThreads = 512;
+__global__ void __launch_bounds__(kMomThreads) k_moments_reduce(const double *__restrict__ part,
+                                                                 double *__restrict__ out) {
+    __shared__ double acc[kMomWords][kMomThreads];
+    double a[kMomWords] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int wp = threadIdx.x; wp < kMomWarps; wp += kMomThreads) {
+        const double *o = part + kMomWords * wp;
+        a[0] = fmax(a[0], o[0]);
+        a[1] = fmax(a[1], o[1]);
+        for (int k = 2; k < kMomWords; ++k) a[k] += o[k];
+    }
+    for (int k = 0; k < kMomWords; ++k) acc[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int h = kMomThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int k = 0; k < kMomWords; ++k) {
+                const double b = acc[k][threadIdx.x + h];
+                acc[k][threadIdx.x] = k < 2 ? fmax(acc[k][threadIdx.x], b) : acc[k][threadIdx.x] + b;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kMomWords) out[threadIdx.x] = acc[threadIdx.x][0];
 }
 
 pic_status limits(const pic_config &c, double n_max, double w_max, double t_e_ev, double *dx_ld, double *wdt) {
@@ -72,29 +109,24 @@ pic_status stability_check(pic_ctx *ctx, Instance &in, double *dx_ld, double *wd
         return limits(in.cfg, 0.0, 0.0, 0.0, dx_ld, wdt);
     }
     DeviceArena T(&ctx->cache);
-    double *mom = dalloc<double>(T, 8 * nl);
+    double *part = dalloc<double>(T, (size_t)kMomWords * kMomWarps + kMomWords);
+    double *tot = part + (size_t)kMomWords * kMomWarps;
     const Level &g = in.lv[0];
     const double hf = in.h0 / (double)(1 << in.lmax);
     if (in.cfg.precision == PIC_FP64)
-        k_leaf_moments<double><<<warp_blocks(nl), kT, 0, ctx->stream>>>(nl, sp.start, sp.end, g.lev, in.lmax, hf,
-                                                                         soa<double>(sp, sp.cur), mom);
+        k_leaf_moments<double><<<kMomBlocks, kT, 0, ctx->stream>>>(nl, sp.start, sp.end, g.lev, in.lmax, hf,
+                                                                   soa<double>(sp, sp.cur), part);
     else
-        k_leaf_moments<float><<<warp_blocks(nl), kT, 0, ctx->stream>>>(nl, sp.start, sp.end, g.lev, in.lmax, hf,
-                                                                       soa<float>(sp, sp.cur), mom);
-    count_launch(ctx);
+        k_leaf_moments<float><<<kMomBlocks, kT, 0, ctx->stream>>>(nl, sp.start, sp.end, g.lev, in.lmax, hf,
+                                                                  soa<float>(sp, sp.cur), part);
+    k_moments_reduce<<<1, kMomThreads, 0, ctx->stream>>>(part, tot);
+    count_launch(ctx, 2);
     check_launch("stability_check");
-    std::vector<double> h((size_t)8 * nl);
-    GB_CUDA(cudaMemcpyAsync(h.data(), mom, 8 * 8 * nl, cudaMemcpyDeviceToHost, ctx->stream));
+    double r[kMomWords];
+    GB_CUDA(cudaMemcpyAsync(r, tot, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     T.release_all();
-    double w_max = 0.0, n_max = 0.0, W = 0.0, mv[3] = {0, 0, 0}, mv2[3] = {0, 0, 0};
-    for (int64_t L = 0; L < nl; ++L) {
-        const double *o = h.data() + 8 * L;
-        w_max = std::max(w_max, o[0]);
-        n_max = std::max(n_max, o[1]);
-        W += o[0];
-        for (int k = 0; k < 3; ++k) { mv[k] += o[2 + k]; mv2[k] += o[5 + k]; }
-    }
+    const double w_max = r[0], n_max = r[1], W = r[2], *mv = r + 3, *mv2 = r + 6;
     double var = 0.0;
     if (W > 0.0)
         for (int k = 0; k < 3; ++k) var += std::max(0.0, mv2[k] / W - (mv[k] / W) * (mv[k] / W));

@@ -1124,33 +1124,59 @@ __global__ void k_load_perm(int64_t n, const int32_t *__restrict__ leaf, const i
     if (i < n) perm[start[leaf[i]] + slot[i]] = (int32_t)i;
 }
 
-// One warp per leaf: the leaf's cnt[L] loaded records, gathered from the input through perm,
-// written to [start[L], start[L] + cnt[L]) with their offsets in the leaf, FP32 or FP64
-// payload, id (given, or id0 + input index) and the input index as the order key.  Every
-// array is written in contiguous runs; the input is read at the permuted indices.
+// The loaded records in input order, converted to the list's precision with their offsets
+// in their leaf, packed so that the gather below reads few sectors per record: FP32 as
+// (u, v, vx, vy) in 16 bytes and (vz, w) in 8, FP64 as three 16-byte pairs.
+template <typename R> struct LoadPack {
+    void *a, *b, *c;
+};
+template <typename R>
+__global__ void k_pack_load(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                            const double *__restrict__ vx, const double *__restrict__ vy,
+                            const double *__restrict__ vz, const double *__restrict__ w,
+                            const int32_t *__restrict__ leaf, double hf, int lmax, const int32_t *__restrict__ ix,
+                            const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, LoadPack<R> pk) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t l = leaf[i];
+    const double h = (double)(1 << (lmax - lev[l])) * hf;
+    R u = (R)((x[i] - (double)ix[l] * hf) / h), v = (R)((y[i] - (double)iy[l] * hf) / h);
+    u = u < (R)0 ? (R)0 : (u >= (R)1 ? below_one<R>() : u);
+    v = v < (R)0 ? (R)0 : (v >= (R)1 ? below_one<R>() : v);
+    if constexpr (sizeof(R) == 4) {
+        ((float4 *)pk.a)[i] = make_float4(u, v, (float)vx[i], (float)vy[i]);
+        ((float2 *)pk.b)[i] = make_float2((float)vz[i], (float)w[i]);
+    } else {
+        ((double2 *)pk.a)[i] = make_double2(u, v);
+        ((double2 *)pk.b)[i] = make_double2(vx[i], vy[i]);
+        ((double2 *)pk.c)[i] = make_double2(vz[i], w[i]);
+    }
+}
+
+// One warp per leaf: the leaf's cnt[L] loaded records, gathered from the packed input
+// through perm, written to [start[L], start[L] + cnt[L]) with their id (given, or id0 +
+// input index) and the input index as the order key.  Every array is written in
+// contiguous runs.
 template <typename R>
 __global__ void k_gather_load(int64_t nleaf, const int32_t *__restrict__ start, const int32_t *__restrict__ cnt,
-                              const int32_t *__restrict__ perm, const double *__restrict__ x,
-                              const double *__restrict__ y, const double *__restrict__ vx,
-                              const double *__restrict__ vy, const double *__restrict__ vz,
-                              const double *__restrict__ w, const unsigned long long *__restrict__ id,
-                              unsigned long long id0, double hf, int lmax, const int32_t *__restrict__ ix,
-                              const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, SoA<R> d,
+                              const int32_t *__restrict__ perm, LoadPack<R> pk,
+                              const unsigned long long *__restrict__ id, unsigned long long id0, SoA<R> d,
                               uint32_t *__restrict__ key) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t L = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; L < nleaf; L += nw) {
         const int32_t q0 = start[L], k = cnt[L];
-        if (k == 0) continue;
-        const double h = (double)(1 << (lmax - lev[L])) * hf;
-        const double cx = (double)ix[L], cy = (double)iy[L];
         for (int32_t r = lane; r < k; r += 32) {
             const int32_t q = q0 + r, i = perm[q];
-            R u = (R)((x[i] - cx * hf) / h), v = (R)((y[i] - cy * hf) / h);
-            u = u < (R)0 ? (R)0 : (u >= (R)1 ? below_one<R>() : u);
-            v = v < (R)0 ? (R)0 : (v >= (R)1 ? below_one<R>() : v);
-            d.u[q] = u; d.v[q] = v;
-            d.vx[q] = (R)vx[i]; d.vy[q] = (R)vy[i]; d.vz[q] = (R)vz[i]; d.w[q] = (R)w[i];
+            if constexpr (sizeof(R) == 4) {
+                const float4 A = __ldg((const float4 *)pk.a + i);
+                const float2 B = __ldg((const float2 *)pk.b + i);
+                d.u[q] = A.x; d.v[q] = A.y; d.vx[q] = A.z; d.vy[q] = A.w; d.vz[q] = B.x; d.w[q] = B.y;
+            } else {
+                const double2 A = __ldg((const double2 *)pk.a + i), B = __ldg((const double2 *)pk.b + i),
+                              C = __ldg((const double2 *)pk.c + i);
+                d.u[q] = A.x; d.v[q] = A.y; d.vx[q] = B.x; d.vy[q] = B.y; d.vz[q] = C.x; d.w[q] = C.y;
+            }
             d.id[q] = (uint32_t)(id ? id[i] : id0 + (unsigned long long)i);
             key[q] = (uint32_t)i;
         }
@@ -1550,15 +1576,20 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     GB_CUDA(cudaStreamWaitEvent(st, ctx->load_ev[1], 0));  // every input array is on the device
     if (n) {
         const unsigned gb = (unsigned)std::min<int64_t>((nl + kT / 32 - 1) / (kT / 32), 152 * 64);
-        if (in.cfg.precision == PIC_FP64)
-            k_gather_load<double><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, d[0], d[1], d[2], d[3], d[4], d[5],
-                                                     did, id0, hf, in.lmax, g.ix, g.iy, g.lev, soa<double>(sp, 0),
+        if (in.cfg.precision == PIC_FP64) {
+            LoadPack<double> pk{dalloc<double>(tmp, 2 * n), dalloc<double>(tmp, 2 * n), dalloc<double>(tmp, 2 * n)};
+            k_pack_load<double><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], leaf, hf, in.lmax,
+                                                              g.ix, g.iy, g.lev, pk);
+            k_gather_load<double><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, pk, did, id0, soa<double>(sp, 0),
                                                      sp.key);
-        else
-            k_gather_load<float><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, d[0], d[1], d[2], d[3], d[4], d[5],
-                                                    did, id0, hf, in.lmax, g.ix, g.iy, g.lev, soa<float>(sp, 0),
+        } else {
+            LoadPack<float> pk{dalloc<float>(tmp, 4 * n), dalloc<float>(tmp, 2 * n), nullptr};
+            k_pack_load<float><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], leaf, hf, in.lmax,
+                                                             g.ix, g.iy, g.lev, pk);
+            k_gather_load<float><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, pk, did, id0, soa<float>(sp, 0),
                                                     sp.key);
-        count_launch(ctx);
+        }
+        count_launch(ctx, 2);
     }
     if (in.cfg.precision == PIC_FP64)
         sort_lists<double>(ctx, sort_args<double>(in, sp), soa<double>(sp, 0), soa<double>(sp, 1));
