@@ -546,6 +546,7 @@ def run_gpu(args):
         e2e_steps = 6 if streamer else max(3, min(args.steps, 10))
         t_e2e = 0.0
         n_e2e = 0
+        iter_ms = []
         for k in range(e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -557,8 +558,9 @@ def run_gpu(args):
             if k > 0:
                 t_e2e += t1 - t0
                 n_e2e += sum(host[s]["x"].size for s in host)
+                iter_ms.append(round((t1 - t0) * 1e3, 3))
         line["e2e"] = {"value": n_e2e / t_e2e, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
-                       "d2h_bytes_per_step": int(phi.nbytes)}
+                       "d2h_bytes_per_step": int(phi.nbytes), "iter_ms": iter_ms}
     ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.seed, steps=args.cpu_steps, name=name)

@@ -49,7 +49,7 @@ size_t size_class(size_t b) {
     const size_t g = e >= 3 ? (size_t)1 << (e - 3) : 1;
     return (b + g - 1) / g * g;
 }
-constexpr size_t kCacheMaxBlock = (size_t)512 << 20;  // larger blocks are freed, not cached
+constexpr size_t kCacheMaxBlock = (size_t)2 << 30;    // larger blocks are freed, not cached
 constexpr size_t kCacheMaxIdle = (size_t)8 << 30;     // idle bytes kept at most
 
 void *raw_alloc(size_t bytes) {

@@ -1125,17 +1125,15 @@ __global__ void k_load_perm(int64_t n, const int32_t *__restrict__ leaf, const i
 }
 
 // The loaded records in input order, converted to the list's precision with their offsets
-// in their leaf, packed so that the gather below reads few sectors per record: FP32 as
-// (u, v, vx, vy) in 16 bytes and (vz, w) in 8, FP64 as three 16-byte pairs.
-template <typename R> struct LoadPack {
-    void *a, *b, *c;
-};
+// in their leaf, one aligned record of 8 words per particle, (u, v, vx, vy, vz, w) and two
+// words of padding (32 bytes in FP32, 64 in FP64), so that the gather below reads one (FP32)
+// or two (FP64) DRAM sectors per record.
 template <typename R>
 __global__ void k_pack_load(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                             const double *__restrict__ vx, const double *__restrict__ vy,
                             const double *__restrict__ vz, const double *__restrict__ w,
                             const int32_t *__restrict__ leaf, double hf, int lmax, const int32_t *__restrict__ ix,
-                            const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, LoadPack<R> pk) {
+                            const int32_t *__restrict__ iy, const uint8_t *__restrict__ lev, R *__restrict__ rec) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t l = leaf[i];
@@ -1144,12 +1142,14 @@ __global__ void k_pack_load(int64_t n, const double *__restrict__ x, const doubl
     u = u < (R)0 ? (R)0 : (u >= (R)1 ? below_one<R>() : u);
     v = v < (R)0 ? (R)0 : (v >= (R)1 ? below_one<R>() : v);
     if constexpr (sizeof(R) == 4) {
-        ((float4 *)pk.a)[i] = make_float4(u, v, (float)vx[i], (float)vy[i]);
-        ((float2 *)pk.b)[i] = make_float2((float)vz[i], (float)w[i]);
+        float4 *o = reinterpret_cast<float4 *>(rec + 8 * i);
+        o[0] = make_float4(u, v, (float)vx[i], (float)vy[i]);
+        o[1] = make_float4((float)vz[i], (float)w[i], 0.0f, 0.0f);
     } else {
-        ((double2 *)pk.a)[i] = make_double2(u, v);
-        ((double2 *)pk.b)[i] = make_double2(vx[i], vy[i]);
-        ((double2 *)pk.c)[i] = make_double2(vz[i], w[i]);
+        double2 *o = reinterpret_cast<double2 *>(rec + 8 * i);
+        o[0] = make_double2(u, v);
+        o[1] = make_double2(vx[i], vy[i]);
+        o[2] = make_double2(vz[i], w[i]);
     }
 }
 
@@ -1159,7 +1159,7 @@ __global__ void k_pack_load(int64_t n, const double *__restrict__ x, const doubl
 // contiguous runs.
 template <typename R>
 __global__ void k_gather_load(int64_t nleaf, const int32_t *__restrict__ start, const int32_t *__restrict__ cnt,
-                              const int32_t *__restrict__ perm, LoadPack<R> pk,
+                              const int32_t *__restrict__ perm, const R *__restrict__ rec,
                               const unsigned long long *__restrict__ id, unsigned long long id0, SoA<R> d,
                               uint32_t *__restrict__ key) {
     const int lane = threadIdx.x & 31;
@@ -1169,12 +1169,12 @@ __global__ void k_gather_load(int64_t nleaf, const int32_t *__restrict__ start, 
         for (int32_t r = lane; r < k; r += 32) {
             const int32_t q = q0 + r, i = perm[q];
             if constexpr (sizeof(R) == 4) {
-                const float4 A = __ldg((const float4 *)pk.a + i);
-                const float2 B = __ldg((const float2 *)pk.b + i);
+                const float4 *o = reinterpret_cast<const float4 *>(rec + 8 * (int64_t)i);
+                const float4 A = __ldg(o), B = __ldg(o + 1);
                 d.u[q] = A.x; d.v[q] = A.y; d.vx[q] = A.z; d.vy[q] = A.w; d.vz[q] = B.x; d.w[q] = B.y;
             } else {
-                const double2 A = __ldg((const double2 *)pk.a + i), B = __ldg((const double2 *)pk.b + i),
-                              C = __ldg((const double2 *)pk.c + i);
+                const double2 *o = reinterpret_cast<const double2 *>(rec + 8 * (int64_t)i);
+                const double2 A = __ldg(o), B = __ldg(o + 1), C = __ldg(o + 2);
                 d.u[q] = A.x; d.v[q] = A.y; d.vx[q] = B.x; d.vy[q] = B.y; d.vz[q] = C.x; d.w[q] = C.y;
             }
             d.id[q] = (uint32_t)(id ? id[i] : id0 + (unsigned long long)i);
@@ -1577,16 +1577,16 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     if (n) {
         const unsigned gb = (unsigned)std::min<int64_t>((nl + kT / 32 - 1) / (kT / 32), 152 * 64);
         if (in.cfg.precision == PIC_FP64) {
-            LoadPack<double> pk{dalloc<double>(tmp, 2 * n), dalloc<double>(tmp, 2 * n), dalloc<double>(tmp, 2 * n)};
+            double *rec = dalloc<double>(tmp, 8 * n);
             k_pack_load<double><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], leaf, hf, in.lmax,
-                                                              g.ix, g.iy, g.lev, pk);
-            k_gather_load<double><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, pk, did, id0, soa<double>(sp, 0),
+                                                              g.ix, g.iy, g.lev, rec);
+            k_gather_load<double><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, rec, did, id0, soa<double>(sp, 0),
                                                      sp.key);
         } else {
-            LoadPack<float> pk{dalloc<float>(tmp, 4 * n), dalloc<float>(tmp, 2 * n), nullptr};
+            float *rec = dalloc<float>(tmp, 8 * n);
             k_pack_load<float><<<blocks_for(n), kT, 0, st>>>(n, d[0], d[1], d[2], d[3], d[4], d[5], leaf, hf, in.lmax,
-                                                             g.ix, g.iy, g.lev, pk);
-            k_gather_load<float><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, pk, did, id0, soa<float>(sp, 0),
+                                                             g.ix, g.iy, g.lev, rec);
+            k_gather_load<float><<<gb, kT, 0, st>>>(nl, sp.start, sp.fill, perm, rec, did, id0, soa<float>(sp, 0),
                                                     sp.key);
         }
         count_launch(ctx, 2);
