@@ -196,7 +196,7 @@ template <typename R> void read_species(pic_ctx *ctx, Instance &in, int s, Reade
     const pic_config &c = in.cfg;
     if (c.particle_capacity > 0 && c.particle_capacity < n) fail(PIC_ECAPACITY, "particle_capacity below the checkpoint's population");
     const int64_t cap = c.particle_capacity > 0 ? slots_for(c.particle_capacity, nl)
-                                                : std::max<int64_t>(slots_for(2 * n + (1 << 16), nl), 1 << 20);
+                                                : load_slots(n, nl);
     if (cap >= (1ll << 31) - 1) fail(PIC_ECAPACITY, "particle slots beyond 2^31");
     Species &sp = in.sp[s];
     species_alloc(ctx, in, s, cap);

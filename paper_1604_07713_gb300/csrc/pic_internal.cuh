@@ -96,6 +96,15 @@ struct Level {
 __host__ __device__ inline int32_t list_slack(int32_t c) { return 16 + (c >> 2); }
 // Slots that lists of n records over nl leaves need, free slots included.
 inline int64_t slots_for(int64_t n, int64_t nl) { return n + n / 4 + 16 * nl + 64; }
+// Slots of a species loaded with n records (particle_capacity unset): room for the
+// population to double (every electron ionizing once) before a regrow, plus a tail of about
+// the population's size for the leaves whose free slots run out (each takes a fresh segment
+// there; a re-layout, which copies every record twice, compacts the lists when the tail is
+// used up).
+inline int64_t load_slots(int64_t n, int64_t nl) {
+    const int64_t s = slots_for(3 * n + (1 << 16), nl);
+    return s > (1 << 20) ? s : (1 << 20);
+}
 
 // One species: SoA records (offsets u, v in [0,1) of the leaf, velocity, weight:
 // precision R; id: u32) in three buffers of `cap` slots: the lists (arr[cur]), a scratch

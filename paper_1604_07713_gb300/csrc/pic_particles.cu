@@ -1512,9 +1512,7 @@ void particles_load(pic_ctx *ctx, Instance &in, int s, int64_t n, const double *
     GB_CUDA(cudaStreamSynchronize(st));
     if (in.cfg.particle_capacity > 0 && in.cfg.particle_capacity < n)
         fail(PIC_ECAPACITY, "particle_capacity below the loaded population");
-    // room for the population to double (every electron ionizing once) before a regrow
-    const int64_t cap = in.cfg.particle_capacity > 0 ? slots_for(in.cfg.particle_capacity, nl)
-                                                     : std::max<int64_t>(slots_for(2 * n + (1 << 16), nl), 1 << 20);
+    const int64_t cap = in.cfg.particle_capacity > 0 ? slots_for(in.cfg.particle_capacity, nl) : load_slots(n, nl);
     if (cap >= (1ll << 31) - 1) fail(PIC_ECAPACITY, "particle slots beyond 2^31");
     if (id)
         for (int64_t i = 0; i < n; ++i)
