@@ -1162,10 +1162,17 @@ void poisson_batch_items(pic_ctx *ctx, const std::vector<Instance *> &list) {
         ctx->batch_mem.release_all();
         ctx->batch_items = ctx->batch_mem.alloc(list.size() * sizeof(SmallSolve));
         ctx->batch_smem = 0;
+        // largest meshes first: the blocks start in this order, one per SM (each reserves the
+        // largest instance's shared memory), so the longest solves begin in the first wave
+        // and the short ones fill in behind them (every item writes only its own instance)
+        std::vector<size_t> order(list.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t a, size_t b) { return list[a]->lv[0].n > list[b]->lv[0].n; });
         for (size_t k = 0; k < list.size(); ++k) {
-            GB_CUDA(cudaMemcpyAsync((SmallSolve *)ctx->batch_items + k, list[k]->small_item, sizeof(SmallSolve),
+            GB_CUDA(cudaMemcpyAsync((SmallSolve *)ctx->batch_items + k, list[order[k]]->small_item, sizeof(SmallSolve),
                                     cudaMemcpyDeviceToDevice, ctx->stream));
-            ctx->batch_smem = std::max(ctx->batch_smem, list[k]->small_smem);
+            ctx->batch_smem = std::max(ctx->batch_smem, list[order[k]]->small_smem);
         }
         ctx->batch_epoch = ctx->mesh_epoch;
         ctx->batch_n = (int)list.size();
