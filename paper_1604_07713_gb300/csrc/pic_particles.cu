@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(kT) k_sort_entering_batch(const SortEntry<R> *
 // Block b: the entries [c.y, c.z) of the medium-region list of entry c.x (the list can hold
 // every leaf; blocks past its length return at once).
 template <typename R>
-__global__ void __launch_bounds__(kT, 3) k_sort_medium_batch(const SortEntry<R> *__restrict__ tab,
+__global__ void __launch_bounds__(kT, 4) k_sort_medium_batch(const SortEntry<R> *__restrict__ tab,
                                                           const int4 *__restrict__ chunks) {
     __shared__ unsigned long long sm_keys[kWarpsPerBlock][kSortSmem];
     __shared__ SortEntry<R> se;
